@@ -1,0 +1,192 @@
+/*
+ * kep.h - C ABI of the GB300 k-th eigenpair library.
+ *
+ * Problem (Section 1, Eq. 1.1): A x = lambda B x with n x n sparse symmetric A and symmetric
+ * positive definite B sharing one sparsity pattern (Section 4.1); eigenvalues ascending,
+ * k 1-based.  The library's hot path is the numeric phase of the sparse LDL^T factorization
+ * P Q (A - sigma B) Q^T P^T = L D L^T (Algorithm 1', the factorization step), which gives the
+ * Sylvester inertia count nu_sigma(A, B) = nu_0(D, I) (Section 2.1) and the shifted solves of
+ * the shift-and-invert Lanczos stage (Eq. 2.5).
+ *
+ * Conventions for every call:
+ *  - All floating point is IEEE double (FP64).  Integers are int64_t unless stated.
+ *  - Inputs are caller-owned and only read.  kep_analyze copies what it needs; after it returns
+ *    the caller may free its arrays.  Outputs go to caller-allocated buffers.
+ *  - The context owns every device allocation it makes (factors, fronts, workspaces) and frees
+ *    them in kep_destroy.  One context serves one host thread at a time; it is not thread-safe.
+ *  - Errors are returned as kep_status codes; nothing aborts, traps or throws across the ABI.
+ *    After an error the context stays usable unless the code is KEP_ERR_CUDA.
+ *  - ptr_kind selects where a vector argument lives: KEP_HOST (pageable or pinned host memory;
+ *    the call copies in and out and synchronises) or KEP_DEVICE (device memory on the context's
+ *    device; the call is ordered on the context's stream and synchronises before returning).
+ */
+#ifndef KEP_H
+#define KEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kep_ctx kep_ctx;
+
+typedef enum {
+  KEP_OK = 0,
+  KEP_ERR_INVALID = 1,        /* bad argument: null pointer, index out of range, duplicate entry */
+  KEP_ERR_NOT_SPD = 2,        /* B is not positive definite (its inertia at 0 is not (0, 0, n)) */
+  KEP_ERR_SINGULAR = 3,       /* an exact zero pivot: sigma is an eigenvalue; inertia still filled */
+  KEP_ERR_NOT_CONVERGED = 4,  /* an iteration hit its limit */
+  KEP_ERR_CLUSTER = 5,        /* Algorithm 3 could not validate the interval (clustered/multiple) */
+  KEP_ERR_POOL = 6,           /* delayed pivots exceeded the front slack (internal re-plan failed) */
+  KEP_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+  KEP_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+  KEP_ERR_NONFINITE = 9,      /* a NaN or Inf appeared in a pivot */
+  KEP_ERR_NOMEM = 10          /* device or host allocation failed */
+} kep_status;
+
+enum { KEP_HOST = 0, KEP_DEVICE = 1 };
+
+/* kep_analyze flags */
+enum {
+  KEP_PATTERN_FULL = 0,       /* CSR holds both triangles */
+  KEP_PATTERN_LOWER = 1,      /* CSR holds the lower triangle (col <= row) only */
+  KEP_ORDER_GRAPH = 2         /* ignore coords; order by graph breadth-first levels */
+};
+
+/* Inertia of a factored matrix: counts of negative, zero and positive eigenvalues of D, and the
+ * number of pivots that were passed from a front to its parent ("delayed"). */
+typedef struct {
+  int64_t neg, zero, pos, delayed;
+} kep_inertia;
+
+/* Symbolic-analysis facts (Section 4.3: #nzf predicts the run time). */
+typedef struct {
+  int64_t n, nnz;             /* order, stored entries of the full symmetric pattern */
+  int64_t nfronts, nlevels;   /* fronts of the assembly tree, tree height + 1 */
+  int64_t max_front;          /* largest symbolic front order m */
+  int64_t nnz_factor;         /* #nzf: entries of L and D (symbolic, without delays) */
+  double flops_factor;        /* multiply-add = 2 flops, symbolic count for one factorization */
+  int64_t front_bytes;        /* device bytes of one factor slot's front storage */
+} kep_info;
+
+/* Parameters of Algorithm 4 (Section 3.4) and of the stage-3 iteration. */
+typedef struct {
+  int64_t m_max;              /* Algorithm 1' stop: nu_u - nu_l <= m_max (paper: 20) */
+  double tau_res;             /* Algorithm 3 relative residual 2-norm tolerance (paper: 1e-10) */
+  double tau_diff;            /* Algorithm 3 relative difference 2-norm tolerance (paper: 1e-10) */
+  int64_t max_lanczos;        /* Algorithm 2 iteration limit */
+  int64_t max_si;             /* Algorithm 3 iteration limit */
+  const double* start_vectors;/* optional host array of 2n: v_1 (Algorithm 2) then v~_1
+                                 (Algorithm 3); NULL draws them from a counter-based generator */
+  uint64_t seed;              /* seed of that generator */
+} kep_params;
+
+/* Report of kep_kth_eigenpair. */
+typedef struct {
+  double lambda;              /* lambda_k */
+  double eta;                 /* error bound of Proposition 3 for lambda_k */
+  double rel_res;             /* ||(A - lambda B) x||_2 / ||x||_2, computed explicitly */
+  double rel_res_normwise;    /* ||A x - lambda B x||_2 / (||A||_inf ||x||_2) */
+  double sigma_lo, sigma_hi;  /* interval after Algorithm 1' */
+  int64_t nu_lo, nu_hi;       /* its inertia counts */
+  double init_lo, init_hi;    /* interval from Algorithm 2 */
+  int64_t init_nu_lo, init_nu_hi;
+  int64_t n_factor;           /* numeric factorizations (B included) */
+  int64_t n_lanczos;          /* Algorithm 2 iterations */
+  int64_t n_bisect;           /* Algorithm 1' iterations */
+  int64_t n_si_iter;          /* Algorithm 3 iterations */
+  int64_t si_iter_bound;      /* first Algorithm 3 iteration with inclusion and disjointness */
+  double t_stage[3];          /* seconds spent in stages 1, 2, 3 */
+} kep_report;
+
+void kep_default_params(kep_params* p);
+
+/*
+ * kep_analyze - symbolic phase (Section 3.3: "fill-reducing ordering Q and symbolic
+ * factorization ... recycled for other shifted matrices"; task (i) of Section 4.3).
+ *
+ * n        order of A and B (n >= 1).
+ * rowptr   n+1 row offsets into colind (int64, rowptr[0] = 0), CSR of the common pattern.
+ * colind   column indices (int32, 0 <= c < n); no duplicates within a row.
+ * a_val, b_val  values of A and B on that pattern (double, rowptr[n] each).  Both must be
+ *          symmetric; with KEP_PATTERN_LOWER only entries with colind <= row are given.
+ * flags    KEP_PATTERN_FULL / KEP_PATTERN_LOWER, optionally | KEP_ORDER_GRAPH.
+ * coords   optional 3n doubles (x, y, z of the atom owning each row; an ordering hint only).
+ * out      receives the new context.
+ * Computes the nested-dissection ordering, the assembly tree, front structures and index maps
+ * on the host, and uploads them and the values to the current CUDA device.  Errors:
+ * KEP_ERR_INVALID for a malformed pattern, KEP_ERR_NOMEM, KEP_ERR_CUDA.
+ */
+kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                       const double* a_val, const double* b_val, int flags,
+                       const double* coords, kep_ctx** out);
+
+/* Fill *info with the symbolic facts of ctx. */
+kep_status kep_get_info(const kep_ctx* ctx, kep_info* info);
+
+/*
+ * kep_set_stream - order all of ctx's device work on the given cudaStream_t (NULL: the legacy
+ * default stream).  The stream must belong to the context's device.
+ */
+kep_status kep_set_stream(kep_ctx* ctx, void* stream);
+
+/*
+ * kep_factor - numeric LDL^T of A - sigma*B (Algorithm 1', lines "LDL^H <- PQ(A - sigma B)Q^T P^T"
+ * and "nu := nu_0(D, I)"), and its inertia.
+ *
+ * The factor stays in ctx for kep_solve until the next kep_factor.  out->neg is nu_sigma(A, B),
+ * the number of eigenvalues below sigma.  Returns KEP_ERR_SINGULAR (with *out filled) when an
+ * exact zero pivot occurs, i.e. sigma is an eigenvalue; KEP_ERR_NONFINITE on NaN/Inf input.
+ */
+kep_status kep_factor(kep_ctx* ctx, double sigma, kep_inertia* out);
+
+/*
+ * kep_factor_pencil - as kep_factor for the matrix ca*A + cb*B (kep_factor(sigma) is
+ * ca = 1, cb = -sigma; ca = 0, cb = 1 factors B, task (ii) of Section 4.3).
+ */
+kep_status kep_factor_pencil(kep_ctx* ctx, double ca, double cb, kep_inertia* out);
+
+/*
+ * kep_solve - x = (ca*A + cb*B)^{-1} rhs with the last factorization (the solves of Eq. 2.5 and,
+ * with the B factor, of Eq. 2.2): x = P^T Q^T L^{-T} D^{-1} L^{-1} Q P rhs.
+ *
+ * rhs, x   n*nrhs doubles, column-major (column i at offset i*n); may alias.
+ * ptr_kind KEP_HOST or KEP_DEVICE for both rhs and x.
+ * Returns KEP_ERR_INVALID if no factorization is present, KEP_ERR_SINGULAR if it had a zero pivot.
+ */
+kep_status kep_solve(kep_ctx* ctx, const double* rhs, double* x, int64_t nrhs, int ptr_kind);
+
+/*
+ * kep_spmv - ax = A x and bx = B x (the products of Eqs. 2.2 and 2.5), original numbering.
+ * x, ax, bx: n doubles each; ax or bx may be NULL to skip it.
+ */
+kep_status kep_spmv(kep_ctx* ctx, const double* x, double* ax, double* bx, int ptr_kind);
+
+/*
+ * kep_kth_eigenpair - Algorithm 4 (Section 3.4): Algorithm 2 (initial interval from Ritz
+ * values), Algorithm 1' (bisection to at most m_max eigenvalues), Algorithm 3 (shift-and-invert
+ * Lanczos with modified Ritz vectors x_{i,2}, Proposition 3 bounds, index validation).
+ *
+ * k        target index, 1 <= k <= n.
+ * params   NULL for the paper's settings (m_max 20, tau_res = tau_diff = 1e-10).
+ * lambda   receives lambda_k.
+ * x        optional host array of n doubles: x_k, B-normalized (x^T B x = 1).
+ * report   optional.
+ * Returns KEP_ERR_CLUSTER when Algorithm 3 cannot validate the interval within max_si
+ * iterations (multiple or clustered eigenvalues, Section 3.4), KEP_ERR_NOT_SPD if B's
+ * factorization shows B is not positive definite.
+ */
+kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, double* lambda,
+                             double* x, kep_report* report);
+
+/* Release every resource of ctx (NULL is accepted). */
+void kep_destroy(kep_ctx* ctx);
+
+/* Static description of a status code. */
+const char* kep_status_str(kep_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KEP_H */

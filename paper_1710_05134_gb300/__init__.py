@@ -1,0 +1,6 @@
+"""GB300-native k-th eigenpair library: sparse LDL^T inertia counts, shifted solves and the
+three-stage method of Lee, Hoshi, Sogabe, Miyatake and Zhang, on hand-written sm_103a kernels.
+
+The compute path is libkep.so (C ABI in include/kep.h); ``kep`` is its thin Python binding."""
+from .kep import (FactorResult, KepError, Problem, lib, status_str, EXPORTED,  # noqa: F401
+                  KEP_OK, KEP_ERR_SINGULAR, KEP_ERR_CLUSTER, KEP_ERR_NOT_SPD)

@@ -1,0 +1,344 @@
+// C ABI of the kep library: context lifecycle, symbolic analysis upload, factor, solve, SpMV.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kep_ctx.h"
+
+using namespace kep;
+
+namespace kep {
+
+template <typename T>
+static kep_status dev_upload(kep_ctx* c, T** out, const std::vector<T>& v) {
+  *out = nullptr;
+  size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return KEP_ERR_NOMEM;
+  c->allocs.push_back(p);
+  if (!v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  *out = static_cast<T*>(p);
+  return KEP_OK;
+}
+
+template <typename T>
+static kep_status dev_alloc(kep_ctx* c, T** out, size_t count) {
+  *out = nullptr;
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return KEP_ERR_NOMEM;
+  c->allocs.push_back(p);
+  *out = static_cast<T*>(p);
+  return KEP_OK;
+}
+
+#define KEP_TRY(x) do { kep_status _s = (x); if (_s != KEP_OK) return _s; } while (0)
+
+static kep_status alloc_slot(kep_ctx* c, int i) {
+  if (c->slot_ready[i]) return KEP_OK;
+  const Plan& P = c->plan;
+  FactorSlot& S = c->slot[i];
+  KEP_TRY(dev_alloc(c, &S.F, P.front_total));
+  KEP_TRY(dev_alloc(c, &S.rowvar, P.vec_total));
+  KEP_TRY(dev_alloc(c, &S.apos, P.vec_total));
+  KEP_TRY(dev_alloc(c, &S.Dd, P.piv_total));
+  KEP_TRY(dev_alloc(c, &S.De, P.piv_total));
+  KEP_TRY(dev_alloc(c, &S.piv, P.piv_total));
+  KEP_TRY(dev_alloc(c, &S.d_in, P.nfronts));
+  KEP_TRY(dev_alloc(c, &S.nelim, P.nfronts));
+  KEP_TRY(dev_alloc(c, &S.d_out, P.nfronts));
+  KEP_TRY(dev_alloc(c, &S.cnt, 3 * static_cast<size_t>(P.nfronts)));
+  KEP_TRY(dev_alloc(c, &S.status, 2));
+  S.valid = false;
+  c->slot_ready[i] = true;
+  return KEP_OK;
+}
+
+kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out) {
+  KEP_TRY(alloc_slot(c, slot));
+  FactorSlot& S = c->slot[slot];
+  S.valid = false;
+  FactorLaunch F;
+  F.plan = &c->plan;
+  F.T = c->T;
+  F.S = S;
+  F.cbpool = c->d_cbpool;
+  F.W = c->W;
+  F.d_level_fronts = c->d_level_fronts;
+  F.h_done = c->h_done;
+  F.d_red = c->d_red;
+  F.h_red = c->h_red;
+  F.stream = c->stream;
+  F.num_sms = c->num_sms;
+  int bits = 0;
+  kep_inertia in{0, 0, 0, 0};
+  kep_status st = run_factor(F, ca, cb, &in, &bits);
+  if (st != KEP_OK) return st;
+  S.ca = ca; S.cb = cb;
+  c->slot_status[slot] = bits;
+  if (out) *out = in;
+  if (bits & ST_POOL) return KEP_ERR_POOL;
+  if (bits & ST_NONFINITE) return KEP_ERR_NONFINITE;
+  if (in.neg + in.zero + in.pos != c->plan.n) return KEP_ERR_POOL;
+  S.valid = true;
+  c->slot_zero[slot] = in.zero;
+  if (in.zero > 0) return KEP_ERR_SINGULAR;
+  return KEP_OK;
+}
+
+kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x) {
+  FactorSlot& S = c->slot[slot];
+  if (!c->slot_ready[slot] || !S.valid) return KEP_ERR_INVALID;
+  if (c->slot_zero[slot] > 0) return KEP_ERR_SINGULAR;
+  SolveLaunch L;
+  L.plan = &c->plan;
+  L.T = c->T;
+  L.S = S;
+  L.d_level_fronts = c->d_level_fronts;
+  L.d_perm = c->d_perm;
+  L.vasm = c->d_vasm;
+  L.vfac = c->d_vfac;
+  L.bnew = c->d_bnew;
+  L.xnew = c->d_xnew;
+  L.stream = c->stream;
+  L.num_sms = c->num_sms;
+  return run_solve(L, b, x);
+}
+
+kep_status ctx_spmv_dev(kep_ctx* c, const double* x, double* ax, double* bx) {
+  return run_spmv(c->plan.n, c->d_rp, c->d_ci, c->d_a, c->d_b, x, ax, bx, c->stream, c->num_sms);
+}
+
+}  // namespace kep
+
+extern "C" {
+
+void kep_default_params(kep_params* p) {
+  if (!p) return;
+  p->m_max = 20;
+  p->tau_res = 1e-10;
+  p->tau_diff = 1e-10;
+  p->max_lanczos = 200;
+  p->max_si = 300;
+  p->start_vectors = nullptr;
+  p->seed = 0x5eed;
+}
+
+const char* kep_status_str(kep_status s) {
+  switch (s) {
+    case KEP_OK: return "ok";
+    case KEP_ERR_INVALID: return "invalid argument or state";
+    case KEP_ERR_NOT_SPD: return "B is not positive definite";
+    case KEP_ERR_SINGULAR: return "exact zero pivot (shift is an eigenvalue)";
+    case KEP_ERR_NOT_CONVERGED: return "iteration limit reached";
+    case KEP_ERR_CLUSTER: return "interval eigenpairs could not be validated (cluster)";
+    case KEP_ERR_POOL: return "delayed pivots exceeded the front slack";
+    case KEP_ERR_TIMEOUT: return "device wait timed out";
+    case KEP_ERR_CUDA: return "CUDA runtime error";
+    case KEP_ERR_NONFINITE: return "non-finite pivot";
+    case KEP_ERR_NOMEM: return "out of memory";
+  }
+  return "unknown status";
+}
+
+kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* a_val,
+                       const double* b_val, int flags, const double* coords, kep_ctx** out) {
+  if (!out) return KEP_ERR_INVALID;
+  *out = nullptr;
+  if (n < 1 || n > INT32_MAX - 1 || !rowptr || !colind || !a_val || !b_val) return KEP_ERR_INVALID;
+  if (rowptr[0] != 0) return KEP_ERR_INVALID;
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return KEP_ERR_INVALID;
+  const int64_t nnz_in = rowptr[n];
+  const bool lower = flags & KEP_PATTERN_LOWER;
+  // full symmetric pattern, sorted rows
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      int64_t j = colind[e];
+      if (j < 0 || j >= n) return KEP_ERR_INVALID;
+      if (lower) {
+        if (j > i) return KEP_ERR_INVALID;
+        cnt[i + 1]++;
+        if (j != i) cnt[j + 1]++;
+      } else {
+        cnt[i + 1]++;
+      }
+    }
+  for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  const int64_t nnz = cnt[n];
+  std::vector<int32_t> ci(nnz);
+  std::vector<double> av(nnz), bv(nnz);
+  {
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        int64_t j = colind[e];
+        int64_t o = fill[i]++;
+        ci[o] = static_cast<int32_t>(j); av[o] = a_val[e]; bv[o] = b_val[e];
+        if (lower && j != i) {
+          int64_t o2 = fill[j]++;
+          ci[o2] = static_cast<int32_t>(i); av[o2] = a_val[e]; bv[o2] = b_val[e];
+        }
+      }
+  }
+  (void)nnz_in;
+  std::vector<int64_t> idx;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t e0 = cnt[i], e1 = cnt[i + 1];
+    bool sorted = true;
+    for (int64_t e = e0 + 1; e < e1; ++e) if (ci[e] <= ci[e - 1]) { sorted = false; break; }
+    if (sorted) continue;
+    idx.resize(e1 - e0);
+    for (int64_t e = e0; e < e1; ++e) idx[e - e0] = e;
+    std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return ci[x] < ci[y]; });
+    std::vector<int32_t> c2(e1 - e0); std::vector<double> a2(e1 - e0), b2(e1 - e0);
+    for (int64_t k = 0; k < e1 - e0; ++k) { c2[k] = ci[idx[k]]; a2[k] = av[idx[k]]; b2[k] = bv[idx[k]]; }
+    for (int64_t k = 0; k < e1 - e0; ++k) { ci[e0 + k] = c2[k]; av[e0 + k] = a2[k]; bv[e0 + k] = b2[k]; }
+    for (int64_t e = e0 + 1; e < e1; ++e) if (ci[e] == ci[e - 1]) return KEP_ERR_INVALID;
+  }
+  kep_ctx* c = new (std::nothrow) kep_ctx();
+  if (!c) return KEP_ERR_NOMEM;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return KEP_ERR_CUDA; }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  std::string err;
+  kep_status st = build_plan(n, cnt, ci, av, bv, coords, (flags & KEP_ORDER_GRAPH) != 0, 8, c->plan, err);
+  if (st != KEP_OK) { delete c; return st; }
+  const Plan& P = c->plan;
+#define UP(dst, vec) do { st = dev_upload(c, &dst, vec); if (st != KEP_OK) { kep_destroy(c); return st; } } while (0)
+  int32_t *first, *p_sym, *m_sym, *m_alloc, *parent, *child_ptr, *child_idx, *struct_var, *relmap, *ent_r, *ent_c;
+  int64_t *struct_ptr, *relmap_ptr, *ent_ptr, *front_off, *cb_off, *vec_off, *piv_off, *p21_off;
+  double *ent_a, *ent_b;
+  UP(first, P.first); UP(p_sym, P.p_sym); UP(m_sym, P.m_sym); UP(m_alloc, P.m_alloc);
+  UP(parent, P.parent); UP(child_ptr, P.child_ptr); UP(child_idx, P.child_idx);
+  UP(struct_ptr, P.struct_ptr); UP(struct_var, P.struct_var);
+  UP(relmap_ptr, P.relmap_ptr); UP(relmap, P.relmap);
+  UP(ent_ptr, P.ent_ptr); UP(ent_r, P.ent_r); UP(ent_c, P.ent_c); UP(ent_a, P.ent_a); UP(ent_b, P.ent_b);
+  UP(front_off, P.front_off); UP(cb_off, P.cb_off); UP(vec_off, P.vec_off); UP(piv_off, P.piv_off);
+  UP(p21_off, P.p21_off);
+  UP(c->d_level_fronts, P.level_fronts);
+  UP(c->d_perm, P.perm);
+  UP(c->d_iperm, P.iperm);
+  UP(c->d_rp, cnt); UP(c->d_ci, ci); UP(c->d_a, av); UP(c->d_b, bv);
+#undef UP
+  FrontTables& T = c->T;
+  T.nfronts = P.nfronts;
+  T.first = first; T.p_sym = p_sym; T.m_sym = m_sym; T.m_alloc = m_alloc; T.parent = parent;
+  T.child_ptr = child_ptr; T.child_idx = child_idx; T.struct_ptr = struct_ptr; T.struct_var = struct_var;
+  T.relmap_ptr = relmap_ptr; T.relmap = relmap; T.ent_ptr = ent_ptr; T.ent_r = ent_r; T.ent_c = ent_c;
+  T.ent_a = ent_a; T.ent_b = ent_b; T.front_off = front_off; T.cb_off = cb_off; T.vec_off = vec_off;
+  T.piv_off = piv_off;
+  // workspaces
+  const int64_t ent = std::max<int32_t>(P.max_level_width, 1);
+  LargeWork& W = c->W;
+  W.cap = static_cast<int32_t>(ent);
+  W.p21_off = p21_off;
+  W.list = nullptr;
+#define AL(dst, count) do { st = dev_alloc(c, &dst, count); if (st != KEP_OK) { kep_destroy(c); return st; } } while (0)
+  AL(W.k, ent); AL(W.w, ent); AL(W.q, ent); AL(W.fails, ent); AL(W.done, ent);
+  AL(W.L11, ent * kPanel * kPanel); AL(W.Dblk, ent * 2 * kPanel); AL(W.pi, ent * kPanel);
+  AL(W.pt, ent * kPanel); AL(W.colmax, ent * kPanel);
+  AL(W.P21, std::max<int64_t>(P.max_large_rows, 1) * kPanel);
+  AL(c->d_cbpool, P.cb_total);
+  AL(c->d_red, 8);
+  AL(c->d_vasm, P.vec_total); AL(c->d_vfac, P.vec_total);
+  AL(c->d_bnew, P.n); AL(c->d_xnew, P.n);
+  AL(c->d_io0, P.n); AL(c->d_io1, P.n); AL(c->d_io2, P.n);
+#undef AL
+  if (cudaMallocHost(reinterpret_cast<void**>(&c->h_done), sizeof(int32_t) * ent) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(long long) * 8) != cudaSuccess) {
+    kep_destroy(c);
+    return KEP_ERR_NOMEM;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { kep_destroy(c); return KEP_ERR_CUDA; }
+  *out = c;
+  return KEP_OK;
+}
+
+kep_status kep_get_info(const kep_ctx* c, kep_info* info) {
+  if (!c || !info) return KEP_ERR_INVALID;
+  const Plan& P = c->plan;
+  info->n = P.n;
+  info->nnz = P.nnz;
+  info->nfronts = P.nfronts;
+  info->nlevels = P.nlevels;
+  info->max_front = P.max_front;
+  info->nnz_factor = P.nnz_factor;
+  info->flops_factor = P.flops;
+  info->front_bytes = P.front_total * 8;
+  return KEP_OK;
+}
+
+kep_status kep_set_stream(kep_ctx* c, void* stream) {
+  if (!c) return KEP_ERR_INVALID;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return KEP_OK;
+}
+
+kep_status kep_factor(kep_ctx* c, double sigma, kep_inertia* out) {
+  return kep_factor_pencil(c, 1.0, -sigma, out);
+}
+
+kep_status kep_factor_pencil(kep_ctx* c, double ca, double cb, kep_inertia* out) {
+  if (!c) return KEP_ERR_INVALID;
+  if (!std::isfinite(ca) || !std::isfinite(cb)) return KEP_ERR_INVALID;
+  return ctx_factor(c, 0, ca, cb, out);
+}
+
+kep_status kep_solve(kep_ctx* c, const double* rhs, double* x, int64_t nrhs, int ptr_kind) {
+  if (!c || !rhs || !x || nrhs < 0) return KEP_ERR_INVALID;
+  const int64_t n = c->plan.n;
+  for (int64_t r = 0; r < nrhs; ++r) {
+    const double* b = rhs + r * n;
+    double* xr = x + r * n;
+    kep_status st;
+    if (ptr_kind == KEP_DEVICE) {
+      st = ctx_solve_dev(c, 0, b, xr);
+    } else {
+      if (cudaMemcpyAsync(c->d_io0, b, n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return KEP_ERR_CUDA;
+      st = ctx_solve_dev(c, 0, c->d_io0, c->d_io1);
+      if (st == KEP_OK &&
+          cudaMemcpyAsync(xr, c->d_io1, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return KEP_ERR_CUDA;
+    }
+    if (st != KEP_OK) return st;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  return KEP_OK;
+}
+
+kep_status kep_spmv(kep_ctx* c, const double* x, double* ax, double* bx, int ptr_kind) {
+  if (!c || !x || (!ax && !bx)) return KEP_ERR_INVALID;
+  const int64_t n = c->plan.n;
+  kep_status st;
+  if (ptr_kind == KEP_DEVICE) {
+    st = ctx_spmv_dev(c, x, ax, bx);
+  } else {
+    if (cudaMemcpyAsync(c->d_io0, x, n * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    st = ctx_spmv_dev(c, c->d_io0, ax ? c->d_io1 : nullptr, bx ? c->d_io2 : nullptr);
+    if (st != KEP_OK) return st;
+    if (ax && cudaMemcpyAsync(ax, c->d_io1, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    if (bx && cudaMemcpyAsync(bx, c->d_io2, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+      return KEP_ERR_CUDA;
+  }
+  if (st != KEP_OK) return st;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  return KEP_OK;
+}
+
+void kep_destroy(kep_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_done) cudaFreeHost(c->h_done);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  c->driver_release();
+  delete c;
+}
+
+}  // extern "C"

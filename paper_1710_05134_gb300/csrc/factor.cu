@@ -1,0 +1,700 @@
+// Numeric multifrontal LDL^T of ca*A + cb*B on the GPU (Algorithm 1', the factorization and
+// inertia steps; task (iv)-(vi) of Section 4.3).
+//
+// Fronts are processed level by level (leaves first).  All fronts of a level form a batch and
+// advance in lock step; every kernel reads its front's dynamic state (delays received, pivots
+// eliminated so far) from device memory, so no host synchronisation is needed inside a level.
+//
+// Per front:
+//   assembly   zero the storage, scatter the original entries ca*a + cb*b, extend-add the
+//              children's contribution blocks (their delayed columns first);
+//   pivoting   a posteriori threshold pivoting on blocks of kPanel fully-summed columns:
+//              Bunch-Kaufman (alpha = (1+sqrt 17)/8) inside the diagonal block, then every row
+//              below solves against that block and the largest |l| of each column is tested
+//              against 1/u; the accepted leading pivots are kept, the rest of the block is
+//              restored and retried in the next block; a front whose block fails entirely passes
+//              its remaining fully-summed columns to the parent (delayed pivots);
+//   update     Schur complement of the trailing matrix with the accepted pivots, FP64 FMA tiles;
+//   inertia    the sign rule for 1x1 and 2x2 pivots of D, summed per front.
+#include <cmath>
+#include <cstdio>
+
+#include "kep_device.cuh"
+
+namespace kep {
+
+namespace {
+
+constexpr int kTile = 64;          // Schur-update tile edge
+constexpr int kRowTile = 64;       // rows per CTA in the row-parallel kernels
+
+struct Batch {
+  const int32_t* lf;   // fronts of the level
+  int32_t e0;          // first entry of this batch within the level
+};
+
+KEP_D int32_t children_delays(const FrontTables& T, const FactorSlot& S, int32_t t, bool& bad) {
+  int32_t d = 0;
+  for (int32_t c = T.child_ptr[t]; c < T.child_ptr[t + 1]; ++c) {
+    int32_t ch = T.child_idx[c];
+    if (S.d_in[ch] < 0) bad = true;
+    d += S.d_out[ch];
+  }
+  return d;
+}
+
+// ------------------------------------------------------------------------------------------
+// assembly
+// ------------------------------------------------------------------------------------------
+__global__ void lf_init_kernel(FrontTables T, FactorSlot S, double* cbpool, LargeWork W, Batch B) {
+  const int32_t b = B.e0 + blockIdx.y;
+  const int32_t t = B.lf[b];
+  bool bad = false;
+  const int32_t d_in = children_delays(T, S, t, bad);
+  if (d_in > T.m_alloc[t] - T.m_sym[t]) bad = true;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.d_in[t] = bad ? -1 : d_in;
+    S.nelim[t] = 0;
+    S.d_out[t] = 0;
+    S.cnt[3 * t] = S.cnt[3 * t + 1] = S.cnt[3 * t + 2] = 0;
+    W.k[b] = 0; W.q[b] = 0; W.w[b] = 0; W.fails[b] = 0; W.done[b] = bad ? 1 : 0;
+    if (bad) {
+      atomicOr(&S.status[0], ST_POOL);
+      atomicCAS(&S.status[1], -1, t);
+    }
+  }
+  if (bad) return;
+  const FrontView v = front_view(T, S, cbpool, t, d_in);
+  for (int32_t j = blockIdx.x; j < v.p; j += gridDim.x) {
+    double* col = v.L + static_cast<int64_t>(j) * v.ldL;
+    for (int32_t i = j + threadIdx.x; i < v.m; i += blockDim.x) col[i] = 0.0;
+  }
+  for (int32_t j = blockIdx.x; j < v.c; j += gridDim.x) {
+    double* col = v.C + static_cast<int64_t>(j) * v.c;
+    for (int32_t i = j + threadIdx.x; i < v.c; i += blockDim.x) col[i] = 0.0;
+  }
+  int32_t* rv = S.rowvar + T.vec_off[t];
+  int32_t* ap = S.apos + T.vec_off[t];
+  const int32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int32_t i = gt; i < v.m; i += gs) {
+    ap[i] = i;
+    if (i >= d_in) rv[i] = T.struct_var[T.struct_ptr[t] + (i - d_in)];
+  }
+  if (blockIdx.x == 0) {
+    int32_t off = 0;
+    for (int32_t c = T.child_ptr[t]; c < T.child_ptr[t + 1]; ++c) {
+      int32_t ch = T.child_idx[c];
+      int32_t dout = S.d_out[ch], nel = S.nelim[ch];
+      const int32_t* crv = S.rowvar + T.vec_off[ch];
+      for (int32_t q = threadIdx.x; q < dout; q += blockDim.x) rv[off + q] = crv[nel + q];
+      off += dout;
+    }
+  }
+}
+
+__global__ void lf_scatter_kernel(FrontTables T, FactorSlot S, double* cbpool, Batch B,
+                                  double ca, double cb) {
+  const int32_t t = B.lf[B.e0 + blockIdx.y];
+  const int32_t d_in = S.d_in[t];
+  if (d_in < 0) return;
+  const FrontView v = front_view(T, S, cbpool, t, d_in);
+  const int64_t e0 = T.ent_ptr[t], e1 = T.ent_ptr[t + 1];
+  for (int64_t e = e0 + blockIdx.x * blockDim.x + threadIdx.x; e < e1;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int32_t r = T.ent_r[e] + d_in, c = T.ent_c[e] + d_in;
+    v.L[static_cast<int64_t>(c) * v.ldL + r] = ca * T.ent_a[e] + cb * T.ent_b[e];
+  }
+}
+
+// Extend-add of the s-th child of every front in the batch (one launch per child slot keeps
+// the additions of different children to one parent entry in a fixed order).
+__global__ void lf_extend_kernel(FrontTables T, FactorSlot S, double* cbpool, Batch B, int32_t s) {
+  const int32_t t = B.lf[B.e0 + blockIdx.y];
+  const int32_t d_in = S.d_in[t];
+  if (d_in < 0) return;
+  const int32_t c0 = T.child_ptr[t];
+  if (s >= T.child_ptr[t + 1] - c0) return;
+  int32_t off = 0;
+  for (int32_t u = 0; u < s; ++u) off += S.d_out[T.child_idx[c0 + u]];
+  const int32_t ch = T.child_idx[c0 + s];
+  const ChildCB cv = child_cb(T, S, cbpool, ch);
+  const int32_t nc = cv.size();
+  const FrontView v = front_view(T, S, cbpool, t, d_in);
+  for (int32_t qj = blockIdx.x; qj < nc; qj += gridDim.x) {
+    const int32_t Pj = parent_pos(T, ch, qj, cv.dout, off, d_in);
+    for (int32_t qi = qj + threadIdx.x; qi < nc; qi += blockDim.x) {
+      const int32_t Pi = parent_pos(T, ch, qi, cv.dout, off, d_in);
+      *v.at(Pi, Pj) += cv.get(qi, qj);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// pivoting panel: Bunch-Kaufman on the w x w diagonal block (one warp)
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) lf_panel_kernel(FrontTables T, FactorSlot S, LargeWork W,
+                                                      Batch B) {
+  __shared__ double Bk[kPanel][kPanel + 1];
+  __shared__ int32_t perm[kPanel];
+  __shared__ double dd[kPanel], de[kPanel];
+  __shared__ int8_t pt[kPanel];
+  const int32_t b = B.e0 + blockIdx.x;
+  const int32_t lane = threadIdx.x;
+  if (W.done[b]) return;
+  const int32_t t = B.lf[b];
+  const int32_t d_in = S.d_in[t];
+  const int32_t p = T.p_sym[t] + d_in;
+  const int32_t k = W.k[b] + W.q[b];
+  __syncwarp();
+  if (lane == 0) { W.k[b] = k; W.q[b] = 0; }
+  if (k >= p) {
+    if (lane == 0) { W.done[b] = 1; S.nelim[t] = k; S.d_out[t] = p - k; W.w[b] = 0; }
+    return;
+  }
+  const int32_t w = min(kPanel, p - k);
+  const double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  for (int32_t c = 0; c < w; ++c) {
+    double val = 0.0;
+    if (lane >= c && lane < w) val = L[static_cast<int64_t>(k + c) * ld + k + lane];
+    if (lane < w && lane >= c) { Bk[lane][c] = val; Bk[c][lane] = val; }
+  }
+  perm[lane] = lane;
+  __syncwarp();
+  int32_t kk = 0;
+  while (kk < w) {
+    // column kk below the diagonal: largest magnitude and its row
+    double v = (lane > kk && lane < w) ? fabs(Bk[lane][kk]) : -1.0;
+    double lam = warp_max(v);
+    unsigned ball = __ballot_sync(0xffffffffu, v == lam && lane > kk && lane < w);
+    int32_t r = ball ? __ffs(ball) - 1 : -1;
+    if (lam < 0) lam = 0.0;
+    double akk = fabs(Bk[kk][kk]);
+    int32_t kind = 1, piv = kk;          // kind 1: 1x1 at piv; kind 2: 2x2 (kk, piv)
+    if (lam == 0.0 || akk >= kBKAlpha * lam) {
+      kind = 1; piv = kk;
+    } else {
+      double vr = (lane >= kk && lane < w && lane != r) ? fabs(Bk[lane][r]) : -1.0;
+      double sig = warp_max(vr);
+      if (sig < 0) sig = 0.0;
+      if (akk * sig >= kBKAlpha * lam * lam) { kind = 1; piv = kk; }
+      else if (fabs(Bk[r][r]) >= kBKAlpha * sig) { kind = 1; piv = r; }
+      else { kind = 2; piv = r; }
+    }
+    const int32_t dst = kind == 1 ? kk : kk + 1;
+    if (piv != dst) {   // symmetric interchange of dst and piv in the full block copy
+      if (lane < w) { double tmp = Bk[lane][dst]; Bk[lane][dst] = Bk[lane][piv]; Bk[lane][piv] = tmp; }
+      __syncwarp();
+      if (lane < w) { double tmp = Bk[dst][lane]; Bk[dst][lane] = Bk[piv][lane]; Bk[piv][lane] = tmp; }
+      if (lane == 0) { int32_t tp = perm[dst]; perm[dst] = perm[piv]; perm[piv] = tp; }
+      __syncwarp();
+    }
+    if (kind == 1) {
+      const double d = Bk[kk][kk];
+      double la = 0.0;
+      if (lane > kk && lane < w) la = d != 0.0 ? Bk[lane][kk] / d : 0.0;
+      __syncwarp();
+      if (lane > kk && lane < w)
+        for (int32_t c = kk + 1; c < w; ++c) Bk[lane][c] -= la * Bk[c][kk];
+      __syncwarp();
+      if (lane > kk && lane < w) { Bk[lane][kk] = la; Bk[kk][lane] = la; }
+      if (lane == 0) { dd[kk] = d; de[kk] = 0.0; pt[kk] = 1; }
+      __syncwarp();
+      kk += 1;
+    } else {
+      const double a = Bk[kk][kk], bb = Bk[kk + 1][kk], c2 = Bk[kk + 1][kk + 1];
+      const double det = a * c2 - bb * bb;
+      double l0 = 0.0, l1 = 0.0;
+      if (lane > kk + 1 && lane < w) {
+        double w0 = Bk[lane][kk], w1 = Bk[lane][kk + 1];
+        l0 = (c2 * w0 - bb * w1) / det;
+        l1 = (a * w1 - bb * w0) / det;
+      }
+      __syncwarp();
+      if (lane > kk + 1 && lane < w)
+        for (int32_t c = kk + 2; c < w; ++c) Bk[lane][c] -= l0 * Bk[c][kk] + l1 * Bk[c][kk + 1];
+      __syncwarp();
+      if (lane > kk + 1 && lane < w) {
+        Bk[lane][kk] = l0; Bk[kk][lane] = l0;
+        Bk[lane][kk + 1] = l1; Bk[kk + 1][lane] = l1;
+      }
+      if (lane == 0) {
+        dd[kk] = a; dd[kk + 1] = c2; de[kk] = bb; de[kk + 1] = 0.0;
+        pt[kk] = 2; pt[kk + 1] = 0;
+      }
+      __syncwarp();
+      kk += 2;
+    }
+  }
+  __syncwarp();
+  double* L11 = W.L11 + static_cast<int64_t>(b) * kPanel * kPanel;
+  for (int32_t c = 0; c < w; ++c) {
+    double val = 0.0;
+    if (lane > c && lane < w) val = (pt[c] == 2 && lane == c + 1) ? 0.0 : Bk[lane][c];
+    if (lane < w) L11[c * kPanel + lane] = (lane == c) ? 1.0 : (lane > c ? val : 0.0);
+  }
+  if (lane < w) {
+    W.Dblk[b * 2 * kPanel + lane] = dd[lane];
+    W.Dblk[b * 2 * kPanel + kPanel + lane] = de[lane];
+    W.pt[b * kPanel + lane] = pt[lane];
+    W.pi[b * kPanel + lane] = perm[lane];
+    W.colmax[b * kPanel + lane] = 0ull;
+  }
+  if (lane == 0) W.w[b] = w;
+}
+
+// ------------------------------------------------------------------------------------------
+// L21 rows and column maxima: row i solves y L11^T = f (f: row i of the permuted block columns),
+// then l = y D^{-1}
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, FactorSlot S, LargeWork W,
+                                                          Batch B) {
+  __shared__ double L11s[kPanel][kPanel + 1];
+  __shared__ double dd[kPanel], de[kPanel];
+  __shared__ int8_t pt[kPanel];
+  __shared__ int32_t pi[kPanel];
+  __shared__ double red[kRowTile / 32][kPanel];
+  const int32_t b = B.e0 + blockIdx.y;
+  if (W.done[b]) return;
+  const int32_t t = B.lf[b];
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in;
+  const int32_t k = W.k[b], w = W.w[b];
+  const int32_t rows = m - k - w;
+  const int32_t ntile = (rows + kRowTile - 1) / kRowTile;
+  if (blockIdx.x >= ntile) return;
+  const double* L11 = W.L11 + static_cast<int64_t>(b) * kPanel * kPanel;
+  for (int32_t e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x)
+    L11s[e % kPanel][e / kPanel] = L11[e];
+  if (threadIdx.x < kPanel) {
+    dd[threadIdx.x] = W.Dblk[b * 2 * kPanel + threadIdx.x];
+    de[threadIdx.x] = W.Dblk[b * 2 * kPanel + kPanel + threadIdx.x];
+    pt[threadIdx.x] = W.pt[b * kPanel + threadIdx.x];
+    pi[threadIdx.x] = W.pi[b * kPanel + threadIdx.x];
+  }
+  __syncthreads();
+  const double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  double* P21 = W.P21 + W.p21_off[t];
+  const int64_t ldp = T.m_alloc[t];
+  double cm[kPanel];
+#pragma unroll
+  for (int32_t c = 0; c < kPanel; ++c) cm[c] = 0.0;
+  for (int32_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int32_t ii = tile * kRowTile + threadIdx.x;     // row index below the block
+    const bool valid = ii < rows;
+    const int32_t i = k + w + ii;
+    double f[kPanel];
+#pragma unroll
+    for (int32_t c = 0; c < kPanel; ++c)
+      f[c] = (valid && c < w) ? L[static_cast<int64_t>(k + pi[c]) * ld + i] : 0.0;
+    // forward substitution with the unit lower L11 (y L11^T = f)
+#pragma unroll
+    for (int32_t c = 0; c < kPanel; ++c) {
+#pragma unroll
+      for (int32_t a = c + 1; a < kPanel; ++a) f[a] -= f[c] * L11s[a][c];
+    }
+    // l = y D^{-1}
+#pragma unroll
+    for (int32_t c = 0; c < kPanel; ++c) {
+      if (c < w) {
+        if (pt[c] == 1) {
+          const double d = dd[c];
+          f[c] = d != 0.0 ? f[c] / d : (f[c] == 0.0 ? 0.0 : INFINITY);
+        } else if (pt[c] == 2 && c + 1 < kPanel) {
+          const double a = dd[c], c2 = dd[c + 1], bb = de[c];
+          const double det = a * c2 - bb * bb;
+          const double y0 = f[c], y1 = f[c + 1];
+          f[c] = (y0 * c2 - y1 * bb) / det;
+          f[c + 1] = (y1 * a - y0 * bb) / det;
+        }
+      }
+    }
+    if (valid) {
+#pragma unroll
+      for (int32_t c = 0; c < kPanel; ++c)
+        if (c < w) {
+          P21[ii + c * ldp] = f[c];
+          double af = fabs(f[c]);
+          if (!(af <= cm[c])) cm[c] = af;   // NaN propagates as "larger"
+        }
+    }
+  }
+  // reduce column maxima over the CTA, then atomically into the batch entry
+  const int32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+  for (int32_t c = 0; c < kPanel; ++c) {
+    double v = cm[c];
+    for (int o = 16; o > 0; o >>= 1) {
+      double u = __shfl_xor_sync(0xffffffffu, v, o);
+      if (!(u <= v)) v = u;
+    }
+    if (lane == 0) red[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < w) {
+    double v = 0.0;
+    for (int32_t q = 0; q < kRowTile / 32; ++q) {
+      double u = red[q][threadIdx.x];
+      if (!(u <= v)) v = u;
+    }
+    if (v != v) v = INFINITY;
+    atomicMax(&W.colmax[b * kPanel + threadIdx.x], static_cast<unsigned long long>(__double_as_longlong(v)));
+  }
+}
+
+// Number of leading pivots of the block whose L columns pass |l| <= 1/u.
+KEP_D int32_t accepted_count(const LargeWork& W, int32_t b, int32_t w) {
+  const double lim = 1.0 / kThresholdU;
+  int32_t c = 0, q = 0;
+  while (c < w) {
+    const int8_t pt = W.pt[b * kPanel + c];
+    const double m0 = __longlong_as_double(static_cast<long long>(W.colmax[b * kPanel + c]));
+    if (pt == 2) {
+      const double m1 = __longlong_as_double(static_cast<long long>(W.colmax[b * kPanel + c + 1]));
+      if (m0 <= lim && m1 <= lim) { c += 2; q = c; } else break;
+    } else {
+      if (m0 <= lim) { c += 1; q = c; } else break;
+    }
+  }
+  return q;
+}
+
+// ------------------------------------------------------------------------------------------
+// apply: permute the block, write accepted L columns and D, restore rejected columns
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot S, LargeWork W,
+                                                       Batch B) {
+  __shared__ double Bo[kPanel][kPanel + 1];
+  __shared__ double Fo[kPanel][kRowTile + 1];
+  __shared__ int32_t pi[kPanel];
+  __shared__ int32_t rvo[kPanel], apo[kPanel];
+  const int32_t b = B.e0 + blockIdx.y;
+  if (W.done[b]) return;
+  const int32_t t = B.lf[b];
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in, p = T.p_sym[t] + d_in;
+  const int32_t k = W.k[b], w = W.w[b];
+  int32_t q = accepted_count(W, b, w);
+  if (q == 0 && T.parent[t] < 0) {
+    // a root has no parent to pass columns to: take the block's Bunch-Kaufman pivots as they are
+    q = w;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&S.status[0], ST_ROOT_FORCED);
+  }
+  if (q == 0) {
+    // no pivot of this block passes the threshold: the remaining fully-summed columns go to
+    // the parent (delayed pivots)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      W.done[b] = 1;
+      S.nelim[t] = k;
+      S.d_out[t] = p - k;
+    }
+    return;
+  }
+  if (threadIdx.x < kPanel) pi[threadIdx.x] = W.pi[b * kPanel + threadIdx.x];
+  __syncthreads();
+  double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  const int32_t nA = (k + 31) / 32;
+  const int32_t rows = m - k - w;
+  const int32_t nB = (rows + kRowTile - 1) / kRowTile;
+  const double* L11 = W.L11 + static_cast<int64_t>(b) * kPanel * kPanel;
+  const double* P21 = W.P21 + W.p21_off[t];
+  const int64_t ldp = T.m_alloc[t];
+  for (int32_t item = blockIdx.x; item < 1 + nA + nB; item += gridDim.x) {
+    if (item == 0) {
+      // the diagonal block
+      for (int32_t e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int32_t a = e % w, c = e / w;
+        if (a >= c) {
+          double val = L[static_cast<int64_t>(k + c) * ld + k + a];
+          Bo[a][c] = val; Bo[c][a] = val;
+        }
+      }
+      int32_t* rv = S.rowvar + T.vec_off[t];
+      int32_t* ap = S.apos + T.vec_off[t];
+      if (threadIdx.x < w) { rvo[threadIdx.x] = rv[k + threadIdx.x]; apo[threadIdx.x] = ap[k + threadIdx.x]; }
+      __syncthreads();
+      for (int32_t e = threadIdx.x; e < w * w; e += blockDim.x) {
+        int32_t a = e % w, c = e / w;
+        if (a < c) continue;
+        double val;
+        if (c < q) {
+          const int8_t ptc = W.pt[b * kPanel + c];
+          if (a == c) val = W.Dblk[b * 2 * kPanel + c];
+          else if (ptc == 2 && a == c + 1) val = W.Dblk[b * 2 * kPanel + kPanel + c];
+          else val = L11[c * kPanel + a];
+        } else {
+          val = Bo[pi[a]][pi[c]];
+        }
+        L[static_cast<int64_t>(k + c) * ld + k + a] = val;
+      }
+      if (threadIdx.x < w) { rv[k + threadIdx.x] = rvo[pi[threadIdx.x]]; ap[k + threadIdx.x] = apo[pi[threadIdx.x]]; }
+      const int64_t po = T.piv_off[t];
+      if (threadIdx.x < q) {
+        S.Dd[po + k + threadIdx.x] = W.Dblk[b * 2 * kPanel + threadIdx.x];
+        S.De[po + k + threadIdx.x] = W.Dblk[b * 2 * kPanel + kPanel + threadIdx.x];
+        S.piv[po + k + threadIdx.x] = W.pt[b * kPanel + threadIdx.x];
+      }
+      if (threadIdx.x == 0) {
+        int32_t neg = 0, zero = 0, pos = 0;
+        bool finite = true;
+        for (int32_t c = 0; c < q;) {
+          const double a = W.Dblk[b * 2 * kPanel + c];
+          if (W.pt[b * kPanel + c] == 2) {
+            const double c2 = W.Dblk[b * 2 * kPanel + c + 1], bb = W.Dblk[b * 2 * kPanel + kPanel + c];
+            finite = finite && isfinite(a) && isfinite(c2) && isfinite(bb);
+            count_pivot2(a, bb, c2, neg, zero, pos);
+            c += 2;
+          } else {
+            finite = finite && isfinite(a);
+            count_pivot1(a, neg, zero, pos);
+            c += 1;
+          }
+        }
+        S.cnt[3 * t] += neg; S.cnt[3 * t + 1] += zero; S.cnt[3 * t + 2] += pos;
+        if (!finite) { atomicOr(&S.status[0], ST_NONFINITE); atomicCAS(&S.status[1], -1, t); }
+        W.q[b] = q;
+      }
+      __syncthreads();
+    } else if (item <= nA) {
+      // rows k .. k+w of the earlier L columns follow the block permutation
+      const int32_t warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+      const int32_t j0 = (item - 1) * 32;
+      for (int32_t j = j0 + warp; j < min(k, j0 + 32); j += blockDim.x / 32) {
+        double* col = L + static_cast<int64_t>(j) * ld + k;
+        double val = lane < w ? col[pi[lane]] : 0.0;
+        __syncwarp();
+        if (lane < w) col[lane] = val;
+      }
+    } else {
+      // rows below the block: accepted columns take L21, rejected ones their permuted originals
+      const int32_t ii = (item - 1 - nA) * kRowTile + (threadIdx.x % kRowTile);
+      const int32_t half = threadIdx.x / kRowTile;        // two threads per row: column halves
+      const bool active = ii < rows;
+      const int64_t i = k + w + ii;
+      for (int32_t c = half; c < w; c += 2)
+        if (active) Fo[c][threadIdx.x % kRowTile] = L[static_cast<int64_t>(k + c) * ld + i];
+      __syncthreads();
+      for (int32_t c = half; c < w; c += 2)
+        if (active)
+          L[static_cast<int64_t>(k + c) * ld + i] =
+              c < q ? P21[ii + c * ldp] : Fo[pi[c]][threadIdx.x % kRowTile];
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Schur update of the trailing matrix: C(i, j) -= sum_c L(i, c) (L D)(j, c) over the q accepted
+// pivots, for s = k + q <= j <= i < m.  64 x 64 tiles, 256 threads with 4 x 4 register tiles.
+// ------------------------------------------------------------------------------------------
+KEP_D void tile_bounds(int32_t bidx, int32_t nL, int32_t s, int32_t p, int32_t m, int32_t& lo,
+                       int32_t& hi) {
+  if (bidx < nL) { lo = s + bidx * kTile; hi = min(lo + kTile, p); }
+  else { lo = p + (bidx - nL) * kTile; hi = min(lo + kTile, m); }
+}
+
+__global__ void __launch_bounds__(256) lf_update_kernel(FrontTables T, FactorSlot S, double* cbpool,
+                                                        LargeWork W, Batch B) {
+  __shared__ double Ai[kPanel][kTile + 1];
+  __shared__ double Wj[kPanel][kTile + 1];
+  __shared__ double dd[kPanel], de[kPanel];
+  __shared__ int8_t pt[kPanel];
+  const int32_t b = B.e0 + blockIdx.y;
+  if (W.done[b]) return;
+  const int32_t q = W.q[b];
+  if (q == 0) return;
+  const int32_t t = B.lf[b];
+  const int32_t d_in = S.d_in[t];
+  const FrontView v = front_view(T, S, cbpool, t, d_in);
+  const int32_t k = W.k[b];
+  const int32_t s = k + q;
+  const int32_t nL = v.p > s ? (v.p - s + kTile - 1) / kTile : 0;
+  const int32_t nC = (v.c + kTile - 1) / kTile;
+  const int32_t nb = nL + nC;
+  const int32_t ntiles = nb * (nb + 1) / 2;
+  if (blockIdx.x >= ntiles) return;
+  const int64_t po = T.piv_off[t];
+  if (threadIdx.x < q) {
+    dd[threadIdx.x] = S.Dd[po + k + threadIdx.x];
+    de[threadIdx.x] = S.De[po + k + threadIdx.x];
+    pt[threadIdx.x] = S.piv[po + k + threadIdx.x];
+  }
+  const double* Lk = v.L + static_cast<int64_t>(k) * v.ldL;   // column k of L
+  const int32_t tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int32_t bi = static_cast<int32_t>((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
+    while (bi * (bi + 1) / 2 > tile) --bi;
+    while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
+    const int32_t bj = tile - bi * (bi + 1) / 2;
+    int32_t I0, I1, J0, J1;
+    tile_bounds(bi, nL, s, v.p, v.m, I0, I1);
+    tile_bounds(bj, nL, s, v.p, v.m, J0, J1);
+    __syncthreads();
+    // A_I = L(I, k..k+q) and W_J = L(J, k..k+q) D (a 2x2 block mixes its two columns)
+    for (int32_t e = threadIdx.x; e < kPanel * kTile; e += blockDim.x) {
+      const int32_t r = e % kTile, c = e / kTile;
+      double ai = 0.0, wj = 0.0;
+      if (c < q) {
+        if (I0 + r < I1) ai = Lk[static_cast<int64_t>(c) * v.ldL + I0 + r];
+        if (J0 + r < J1) {
+          const double x = Lk[static_cast<int64_t>(c) * v.ldL + J0 + r];
+          const int8_t ptc = pt[c];
+          if (ptc == 1) {
+            wj = x * dd[c];
+          } else if (ptc == 2) {
+            const double y = Lk[static_cast<int64_t>(c + 1) * v.ldL + J0 + r];
+            wj = x * dd[c] + y * de[c];
+          } else {
+            const double y = Lk[static_cast<int64_t>(c - 1) * v.ldL + J0 + r];
+            wj = y * de[c - 1] + x * dd[c];
+          }
+        }
+      }
+      Ai[c][r] = ai;
+      Wj[c][r] = wj;
+    }
+    __syncthreads();
+    double acc[4][4];
+#pragma unroll
+    for (int32_t x = 0; x < 4; ++x)
+#pragma unroll
+      for (int32_t y = 0; y < 4; ++y) acc[x][y] = 0.0;
+    for (int32_t c = 0; c < q; ++c) {
+      double a[4], wv[4];
+#pragma unroll
+      for (int32_t x = 0; x < 4; ++x) a[x] = Ai[c][ty + 16 * x];
+#pragma unroll
+      for (int32_t y = 0; y < 4; ++y) wv[y] = Wj[c][tx + 16 * y];
+#pragma unroll
+      for (int32_t x = 0; x < 4; ++x)
+#pragma unroll
+        for (int32_t y = 0; y < 4; ++y) acc[x][y] = fma(a[x], wv[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int32_t y = 0; y < 4; ++y) {
+      const int32_t j = J0 + tx + 16 * y;
+      if (j >= J1) continue;
+#pragma unroll
+      for (int32_t x = 0; x < 4; ++x) {
+        const int32_t i = I0 + ty + 16 * x;
+        if (i < I1 && i >= j) *v.at(i, j) -= acc[x][y];
+      }
+    }
+  }
+}
+
+__global__ void reduce_inertia_kernel(FactorSlot S, int32_t nfronts, long long* out) {
+  // out: neg, zero, pos, delayed (sum of d_out over roots is 0; delayed = sum of all d_out)
+  long long a = 0, z = 0, c = 0, d = 0;
+  for (int32_t t = threadIdx.x; t < nfronts; t += blockDim.x) {
+    a += S.cnt[3 * t]; z += S.cnt[3 * t + 1]; c += S.cnt[3 * t + 2]; d += S.d_out[t];
+  }
+  __shared__ long long red[4][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o); z += __shfl_xor_sync(0xffffffffu, z, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o); d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (lane == 0) { red[0][warp] = a; red[1][warp] = z; red[2][warp] = c; red[3][warp] = d; }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[threadIdx.x][w];
+    out[threadIdx.x] = s;
+  }
+  if (threadIdx.x == 0) { out[4] = S.status[0]; out[5] = S.status[1]; }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// host orchestration
+// ------------------------------------------------------------------------------------------
+
+
+static int grid_cap(int64_t want, int64_t cap) {
+  if (want < 1) want = 1;
+  return static_cast<int>(want < cap ? want : cap);
+}
+
+kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, int* status_bits) {
+  const Plan& P = *F.plan;
+  cudaStream_t st = F.stream;
+  int32_t init_status[2] = {0, -1};
+  if (cudaMemcpyAsync(F.S.status, init_status, sizeof(init_status), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  const int target = F.num_sms * 8;
+  for (int32_t l = 0; l < P.nlevels; ++l) {
+    const int32_t lb = P.level_ptr[l], le = P.level_ptr[l + 1];
+    const int32_t width = le - lb;
+    // batches: each front with a large order alone, the rest together (chunks of 65535)
+    int32_t e = 0;
+    while (e < width) {
+      int32_t t0 = P.level_fronts[lb + e];
+      int32_t e1;
+      if (P.m_alloc[t0] > 4096) e1 = e + 1;
+      else e1 = std::min<int32_t>(width, e + 65535);
+      const int32_t nb = e1 - e;
+      Batch B{F.d_level_fronts + lb, e};
+      int64_t max_m = 0, max_p = 0, max_c = 0, max_ent = 0;
+      for (int32_t i = e; i < e1; ++i) {
+        int32_t t = P.level_fronts[lb + i];
+        max_m = std::max<int64_t>(max_m, P.m_alloc[t]);
+        max_p = std::max<int64_t>(max_p, P.p_alloc[t]);
+        max_c = std::max<int64_t>(max_c, P.m_sym[t] - P.p_sym[t]);
+        max_ent = std::max<int64_t>(max_ent, P.ent_ptr[t + 1] - P.ent_ptr[t]);
+      }
+      const int gx_cols = grid_cap(std::max(max_p, max_c), std::max<int64_t>(1, (target + nb - 1) / nb));
+      lf_init_kernel<<<dim3(gx_cols, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B);
+      lf_scatter_kernel<<<dim3(grid_cap((max_ent + 255) / 256, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 256, 0, st>>>(
+          F.T, F.S, F.cbpool, B, ca, cb);
+      int32_t maxch = 0;
+      for (int32_t i = e; i < e1; ++i) {
+        int32_t t = P.level_fronts[lb + i];
+        maxch = std::max(maxch, P.child_ptr[t + 1] - P.child_ptr[t]);
+      }
+      for (int32_t s = 0; s < maxch; ++s)
+        lf_extend_kernel<<<dim3(grid_cap(max_m, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 128, 0, st>>>(
+            F.T, F.S, F.cbpool, B, s);
+      const int64_t rowtiles = (max_m + kRowTile - 1) / kRowTile;
+      const int gx_rows = grid_cap(rowtiles, std::max<int64_t>(1, (target + nb - 1) / nb));
+      const int gx_apply = grid_cap(rowtiles + max_p / 32 + 2, std::max<int64_t>(1, (target + nb - 1) / nb));
+      const int64_t tb = (max_m + kTile - 1) / kTile + 1;
+      const int gx_upd = grid_cap(tb * (tb + 1) / 2, std::max<int64_t>(1, (F.num_sms * 4 + nb - 1) / nb));
+      int64_t steps = (max_p + kPanel - 1) / kPanel + 1;
+      while (true) {
+        for (int64_t it = 0; it < steps; ++it) {
+          lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B);
+          lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B);
+          lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B);
+          lf_update_kernel<<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B);
+        }
+        // one more panel call finalises fronts whose last block was accepted
+        lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B);
+        if (cudaMemcpyAsync(F.h_done, F.W.done + e, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return KEP_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;
+        bool all = true;
+        for (int32_t i = 0; i < nb; ++i) all = all && F.h_done[i];
+        if (all) break;
+        steps = 8;   // partially accepted blocks need extra steps
+      }
+      e = e1;
+    }
+  }
+  reduce_inertia_kernel<<<1, 1024, 0, st>>>(F.S, P.nfronts, F.d_red);
+  if (cudaMemcpyAsync(F.h_red, F.d_red, 6 * sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return KEP_ERR_CUDA;
+  out->neg = F.h_red[0];
+  out->zero = F.h_red[1];
+  out->pos = F.h_red[2];
+  out->delayed = F.h_red[3];
+  *status_bits = static_cast<int>(F.h_red[4]);
+  return KEP_OK;
+}
+
+}  // namespace kep

@@ -1,0 +1,52 @@
+// The kep_ctx object behind the opaque C handle (library-internal).
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+#include "kep_internal.h"
+
+struct kep_ctx {
+  int device = 0;
+  int num_sms = 1;
+  cudaStream_t stream = nullptr;
+  kep::Plan plan;
+  std::vector<void*> allocs;        // every cudaMalloc of this context
+  kep::FrontTables T{};
+  int32_t* d_level_fronts = nullptr;
+  int32_t* d_perm = nullptr;
+  int32_t* d_iperm = nullptr;
+  // full symmetric CSR (original numbering) for the sparse products
+  int64_t* d_rp = nullptr;
+  int32_t* d_ci = nullptr;
+  double* d_a = nullptr;
+  double* d_b = nullptr;
+  // factorization slots: 0 = the public "last factor" (kep_factor / kep_solve),
+  // 1 = the factor of B kept by the eigenpair driver during stage 1
+  kep::FactorSlot slot[2]{};
+  bool slot_ready[2] = {false, false};
+  int slot_status[2] = {0, 0};
+  int64_t slot_zero[2] = {0, 0};
+  double* d_cbpool = nullptr;
+  kep::LargeWork W{};
+  long long* d_red = nullptr;
+  long long* h_red = nullptr;       // pinned
+  int32_t* h_done = nullptr;        // pinned
+  // solve workspaces
+  double* d_vasm = nullptr;
+  double* d_vfac = nullptr;
+  double* d_bnew = nullptr;
+  double* d_xnew = nullptr;
+  double* d_io0 = nullptr;
+  double* d_io1 = nullptr;
+  double* d_io2 = nullptr;
+  // eigenpair driver state (owned by driver.cu)
+  void* driver = nullptr;
+  void driver_release();
+};
+
+namespace kep {
+kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out);
+kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x);
+kep_status ctx_spmv_dev(kep_ctx* c, const double* x, double* ax, double* bx);
+}  // namespace kep

@@ -1,0 +1,179 @@
+// Internal declarations of the kep library (host analysis plan, device layout, kernel launchers).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/kep.h"
+
+namespace kep {
+
+// ---------------------------------------------------------------------------------------------
+// Tunables
+// ---------------------------------------------------------------------------------------------
+constexpr int kSmallMax = 128;      // fronts with m_alloc <= this are factored in shared memory
+constexpr int kPanel = 32;          // block width of the large-front pivoting panel
+constexpr double kBKAlpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
+constexpr double kThresholdU = 0.01;               // threshold pivoting parameter u
+
+// ---------------------------------------------------------------------------------------------
+// Host-side symbolic plan (built once by kep_analyze, Section 3.3)
+// ---------------------------------------------------------------------------------------------
+struct Plan {
+  int64_t n = 0, nnz = 0;
+  std::vector<int32_t> perm;    // perm[new] = old
+  std::vector<int32_t> iperm;   // iperm[old] = new
+  // assembly tree (fronts numbered in post-order: children before parents)
+  int32_t nfronts = 0;
+  std::vector<int32_t> first;       // first fully-summed variable (new numbering)
+  std::vector<int32_t> p_sym;       // fully-summed count
+  std::vector<int32_t> m_sym;       // front order without delays
+  std::vector<int32_t> parent;      // -1 for a root
+  std::vector<int32_t> child_ptr, child_idx;
+  std::vector<int64_t> struct_ptr;  // struct_var[struct_ptr[t] .. +m_sym): fs vars then sorted CB vars
+  std::vector<int32_t> struct_var;
+  std::vector<int64_t> relmap_ptr;  // relmap[relmap_ptr[t] .. +(m_sym - p_sym)): parent position of
+  std::vector<int32_t> relmap;      //   each symbolic CB row of t in the parent's symbolic struct
+  std::vector<int64_t> ent_ptr;     // original lower entries owned by front t
+  std::vector<int32_t> ent_r, ent_c;// symbolic (row, col) positions inside the front
+  std::vector<double> ent_a, ent_b; // A and B values of those entries
+  std::vector<int32_t> height;      // leaves 0
+  int32_t nlevels = 0;
+  std::vector<int32_t> level_ptr, level_fronts;   // fronts of each level, small ones first
+  std::vector<int32_t> level_nsmall;              // count of small fronts per level
+  // memory plan.  Each front has persistent L storage (m_alloc x p_alloc, column-major,
+  // ld = m_alloc: the fully-summed columns, later L and D) and a transient contribution block
+  // (c x c, c = m_sym - p_sym, column-major) in a pool that lives from the front's factorization
+  // until its parent's assembly.
+  std::vector<int32_t> slack, m_alloc, p_alloc;
+  std::vector<int64_t> front_off;   // doubles, L storage
+  std::vector<int64_t> cb_off;      // doubles, contribution block in the pool (-1: none)
+  std::vector<int64_t> vec_off;     // prefix of m_alloc (row lists, solve vectors)
+  std::vector<int64_t> piv_off;     // prefix of p_alloc (D storage)
+  int64_t front_total = 0, cb_total = 0, vec_total = 0, piv_total = 0;
+  int64_t max_large_rows = 0;       // max over levels of sum of m_alloc of large fronts
+  int32_t max_level_width = 0;
+  std::vector<int64_t> p21_off;     // per front: offset of its L21 panel in the level workspace
+  int32_t max_children = 0;
+  // statistics
+  int64_t max_front = 0, nnz_factor = 0;
+  double flops = 0;
+  double norm_a_inf = 0;            // ||A||_inf
+};
+
+// Build the plan from a full symmetric CSR pattern (both triangles, sorted, no duplicates).
+// coords: optional n*3. graph_order forces the coordinate-free ordering.
+kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                      const std::vector<double>& av, const std::vector<double>& bv,
+                      const double* coords, bool graph_order, int32_t slack_base, Plan& plan,
+                      std::string& err);
+
+// ---------------------------------------------------------------------------------------------
+// Device layout
+// ---------------------------------------------------------------------------------------------
+// Static per-front tables (uploaded once).
+struct FrontTables {
+  int32_t nfronts;
+  const int32_t* first;
+  const int32_t* p_sym;
+  const int32_t* m_sym;
+  const int32_t* m_alloc;
+  const int32_t* parent;
+  const int32_t* child_ptr;
+  const int32_t* child_idx;
+  const int64_t* struct_ptr;
+  const int32_t* struct_var;
+  const int64_t* relmap_ptr;
+  const int32_t* relmap;
+  const int64_t* ent_ptr;
+  const int32_t* ent_r;
+  const int32_t* ent_c;
+  const double* ent_a;
+  const double* ent_b;
+  const int64_t* front_off;
+  const int64_t* cb_off;
+  const int64_t* vec_off;
+  const int64_t* piv_off;
+};
+
+
+
+// One numeric factorization (a "slot"): dynamic per-front state + factor storage.
+struct FactorSlot {
+  double* F;            // fronts (column-major, ld = m_alloc), lower triangle meaningful
+  int32_t* rowvar;      // per front, m_alloc: variable (new numbering) at each factor position
+  int32_t* apos;        // per front, m_alloc: assembly position of each factor position
+  double* Dd;           // per front, p_alloc: diagonal of D
+  double* De;           // per front, p_alloc: off-diagonal of a 2x2 block (at its first index)
+  int8_t* piv;          // 1: 1x1, 2: first of a 2x2, 0: second of a 2x2
+  int32_t* d_in;        // delayed columns received from the children
+  int32_t* nelim;       // pivots eliminated in the front
+  int32_t* d_out;       // fully-summed columns passed to the parent
+  int32_t* cnt;         // per front: neg, zero, pos (3 ints)
+  int32_t* status;      // [0]: error bits, [1]: first failing front
+  double ca, cb;        // matrix factored: ca*A + cb*B
+  bool valid = false;
+};
+
+// status bits
+enum : int32_t {
+  ST_POOL = 1,          // delays exceeded a front's slack
+  ST_NONFINITE = 2,     // NaN/Inf pivot
+  ST_ROOT_FORCED = 4,   // a root block failed the threshold test and was accepted as is
+};
+
+// Large-front step workspace (per level batch).
+struct LargeWork {
+  int32_t* list;        // fronts in the batch
+  int32_t* k;           // eliminated so far
+  int32_t* w;           // current block width
+  int32_t* q;           // accepted in current block
+  int32_t* fails;       // consecutive failed blocks
+  int32_t* done;        // 1 when the front has finished
+  double* L11;          // per batch entry: kPanel*kPanel
+  double* Dblk;         // per batch entry: 2*kPanel (diag, offdiag)
+  int32_t* pi;          // per batch entry: kPanel local permutation
+  int8_t* pt;           // per batch entry: kPanel pivot types
+  unsigned long long* colmax;  // per batch entry: kPanel
+  double* P21;          // per batch entry: rows x kPanel (offset p21_off)
+  int64_t* p21_off;
+  int32_t cap;          // capacity (entries)
+};
+
+struct FactorLaunch {
+  const Plan* plan;
+  FrontTables T;
+  FactorSlot S;
+  double* cbpool;
+  LargeWork W;
+  const int32_t* d_level_fronts;
+  int32_t* h_done;          // pinned, >= max level width
+  long long* d_red;         // 6 entries
+  long long* h_red;         // pinned
+  cudaStream_t stream;
+  int num_sms;
+};
+
+struct SolveLaunch {
+  const Plan* plan;
+  FrontTables T;
+  FactorSlot S;
+  const int32_t* d_level_fronts;
+  const int32_t* d_perm;
+  double* vasm;
+  double* vfac;
+  double* bnew;
+  double* xnew;
+  cudaStream_t stream;
+  int num_sms;
+};
+
+kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, int* status_bits);
+kep_status run_solve(SolveLaunch& L, const double* b, double* x);
+kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
+                    const double* x, double* ya, double* yb, cudaStream_t st, int num_sms);
+
+}  // namespace kep

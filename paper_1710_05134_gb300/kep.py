@@ -1,0 +1,253 @@
+"""Thin Python binding of the kep C ABI (include/kep.h): argument marshalling only.
+
+Every computation runs in libkep.so's CUDA kernels.  If the library cannot be loaded this module
+raises; there is no CPU fallback.  Vectors may be numpy arrays (host) or CUDA torch tensors
+(device, float64, contiguous); device tensors are used in place on the context's stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+KEP_OK, KEP_ERR_INVALID, KEP_ERR_NOT_SPD, KEP_ERR_SINGULAR = 0, 1, 2, 3
+KEP_ERR_NOT_CONVERGED, KEP_ERR_CLUSTER, KEP_ERR_POOL, KEP_ERR_TIMEOUT = 4, 5, 6, 7
+KEP_ERR_CUDA, KEP_ERR_NONFINITE, KEP_ERR_NOMEM = 8, 9, 10
+KEP_HOST, KEP_DEVICE = 0, 1
+KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
+
+# symbols declared in include/kep.h
+EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
+            "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_destroy",
+            "kep_status_str"]
+
+
+class KepError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_str(code)} (code {code})")
+
+
+class Inertia(ctypes.Structure):
+    _fields_ = [("neg", ctypes.c_int64), ("zero", ctypes.c_int64), ("pos", ctypes.c_int64),
+                ("delayed", ctypes.c_int64)]
+
+    def astuple(self):
+        return (self.neg, self.zero, self.pos)
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nfronts", ctypes.c_int64),
+                ("nlevels", ctypes.c_int64), ("max_front", ctypes.c_int64),
+                ("nnz_factor", ctypes.c_int64), ("flops_factor", ctypes.c_double),
+                ("front_bytes", ctypes.c_int64)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m_max", ctypes.c_int64), ("tau_res", ctypes.c_double), ("tau_diff", ctypes.c_double),
+                ("max_lanczos", ctypes.c_int64), ("max_si", ctypes.c_int64),
+                ("start_vectors", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("eta", ctypes.c_double), ("rel_res", ctypes.c_double),
+                ("rel_res_normwise", ctypes.c_double), ("sigma_lo", ctypes.c_double),
+                ("sigma_hi", ctypes.c_double), ("nu_lo", ctypes.c_int64), ("nu_hi", ctypes.c_int64),
+                ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double),
+                ("init_nu_lo", ctypes.c_int64), ("init_nu_hi", ctypes.c_int64),
+                ("n_factor", ctypes.c_int64), ("n_lanczos", ctypes.c_int64),
+                ("n_bisect", ctypes.c_int64), ("n_si_iter", ctypes.c_int64),
+                ("si_iter_bound", ctypes.c_int64), ("t_stage", ctypes.c_double * 3)]
+
+    def asdict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_stage"}
+        d["lambda"] = d.pop("lambda_")
+        d["t_stage"] = list(self.t_stage)
+        return d
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building if needed) libkep.so; raises if it cannot be built or loaded."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB if os.path.exists(_build.LIB) else _build.build()
+        L = ctypes.CDLL(path)
+        P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        L.kep_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.kep_default_params.restype = None
+        L.kep_analyze.argtypes = [I64, P, P, P, P, I, P, ctypes.POINTER(P)]
+        L.kep_get_info.argtypes = [P, ctypes.POINTER(Info)]
+        L.kep_set_stream.argtypes = [P, P]
+        L.kep_factor.argtypes = [P, D, ctypes.POINTER(Inertia)]
+        L.kep_factor_pencil.argtypes = [P, D, D, ctypes.POINTER(Inertia)]
+        L.kep_solve.argtypes = [P, P, P, I64, I]
+        L.kep_spmv.argtypes = [P, P, P, P, I]
+        L.kep_kth_eigenpair.argtypes = [P, I64, ctypes.POINTER(Params), ctypes.POINTER(D), P,
+                                        ctypes.POINTER(Report)]
+        L.kep_destroy.argtypes = [P]
+        L.kep_destroy.restype = None
+        L.kep_status_str.argtypes = [I]
+        L.kep_status_str.restype = ctypes.c_char_p
+        for name in ["kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
+                     "kep_solve", "kep_spmv", "kep_kth_eigenpair"]:
+            getattr(L, name).restype = I
+        _LIB = L
+    return _LIB
+
+
+def status_str(code: int) -> str:
+    return lib().kep_status_str(code).decode()
+
+
+def _check(code: int, where: str, ok=(KEP_OK,)):
+    if code not in ok:
+        raise KepError(code, where)
+    return code
+
+
+def _is_device(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _dev_ptr(x) -> int:
+    import torch
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("device vectors must be contiguous float64 CUDA tensors")
+    return x.data_ptr()
+
+
+@dataclass
+class FactorResult:
+    neg: int
+    zero: int
+    pos: int
+    delayed: int
+    status: int
+
+    @property
+    def nu(self) -> int:
+        return self.neg
+
+
+class Problem:
+    """A pencil (A, B) analysed once (ordering, tree, maps) and factored for any shift."""
+
+    def __init__(self, n, rowptr, colind, a, b, coords=None, *, lower: bool = False,
+                 graph_order: bool = False):
+        L = lib()
+        self.n = int(n)
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colind = np.ascontiguousarray(colind, dtype=np.int32)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        cp = None
+        if coords is not None:
+            coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1)
+            if coords.size != 3 * self.n:
+                raise ValueError("coords must hold 3 values per row")
+            cp = coords.ctypes.data_as(ctypes.c_void_p)
+        flags = (KEP_PATTERN_LOWER if lower else KEP_PATTERN_FULL) | (KEP_ORDER_GRAPH if graph_order else 0)
+        h = ctypes.c_void_p()
+        _check(L.kep_analyze(self.n, rowptr.ctypes.data, colind.ctypes.data, a.ctypes.data,
+                             b.ctypes.data, flags, cp, ctypes.byref(h)), "kep_analyze")
+        self._h = h
+        self._stream = None
+
+    @classmethod
+    def from_pencil(cls, p, **kw):
+        return cls(p.n, p.rowptr, p.colind, p.a, p.b, p.coords, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def info(self) -> Info:
+        inf = Info()
+        _check(lib().kep_get_info(self._h, ctypes.byref(inf)), "kep_get_info")
+        return inf
+
+    def set_stream(self, stream):
+        """Order the context's work on a torch.cuda.Stream (or a raw cudaStream_t int)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._stream = stream
+        _check(lib().kep_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)), "kep_set_stream")
+
+    def factor(self, sigma: float, *, allow_singular: bool = True) -> FactorResult:
+        """LDL^T of A - sigma*B; .nu is the number of eigenvalues below sigma."""
+        return self.factor_pencil(1.0, -float(sigma), allow_singular=allow_singular)
+
+    def factor_pencil(self, ca: float, cb: float, *, allow_singular: bool = True) -> FactorResult:
+        inr = Inertia()
+        ok = (KEP_OK, KEP_ERR_SINGULAR) if allow_singular else (KEP_OK,)
+        code = _check(lib().kep_factor_pencil(self._h, float(ca), float(cb), ctypes.byref(inr)),
+                      "kep_factor_pencil", ok)
+        return FactorResult(inr.neg, inr.zero, inr.pos, inr.delayed, code)
+
+    def solve(self, rhs, out=None):
+        """x = M^{-1} rhs with the last factorization; rhs of shape (n,) or (nrhs, n)."""
+        if _is_device(rhs):
+            import torch
+            x = torch.empty_like(rhs) if out is None else out
+            nrhs = 1 if rhs.dim() == 1 else rhs.shape[0]
+            _check(lib().kep_solve(self._h, _dev_ptr(rhs), _dev_ptr(x), nrhs, KEP_DEVICE), "kep_solve")
+            return x
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.empty_like(rhs) if out is None else out
+        nrhs = 1 if rhs.ndim == 1 else rhs.shape[0]
+        _check(lib().kep_solve(self._h, rhs.ctypes.data, x.ctypes.data, nrhs, KEP_HOST), "kep_solve")
+        return x
+
+    def spmv(self, x):
+        """(A x, B x)."""
+        if _is_device(x):
+            import torch
+            ax, bx = torch.empty_like(x), torch.empty_like(x)
+            _check(lib().kep_spmv(self._h, _dev_ptr(x), _dev_ptr(ax), _dev_ptr(bx), KEP_DEVICE), "kep_spmv")
+            return ax, bx
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        ax, bx = np.empty_like(x), np.empty_like(x)
+        _check(lib().kep_spmv(self._h, x.ctypes.data, ax.ctypes.data, bx.ctypes.data, KEP_HOST), "kep_spmv")
+        return ax, bx
+
+    def kth_eigenpair(self, k: int, *, m_max: int = 20, tau_res: float = 1e-10, tau_diff: float = 1e-10,
+                      max_lanczos: int = 200, max_si: int = 300, start_vectors=None, seed: int = 0x5eed,
+                      want_vector: bool = True):
+        """Algorithm 4: (lambda_k, x_k (B-normalized), report dict)."""
+        prm = Params()
+        lib().kep_default_params(ctypes.byref(prm))
+        prm.m_max, prm.tau_res, prm.tau_diff = int(m_max), float(tau_res), float(tau_diff)
+        prm.max_lanczos, prm.max_si, prm.seed = int(max_lanczos), int(max_si), int(seed)
+        sv = None
+        if start_vectors is not None:
+            sv = np.ascontiguousarray(start_vectors, dtype=np.float64).reshape(-1)
+            if sv.size != 2 * self.n:
+                raise ValueError("start_vectors must hold 2n values")
+            prm.start_vectors = sv.ctypes.data
+        lam = ctypes.c_double()
+        x = np.empty(self.n) if want_vector else None
+        rep = Report()
+        _check(lib().kep_kth_eigenpair(self._h, int(k), ctypes.byref(prm), ctypes.byref(lam),
+                                       x.ctypes.data if x is not None else None, ctypes.byref(rep)),
+               "kep_kth_eigenpair")
+        return lam.value, x, rep.asdict()
