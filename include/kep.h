@@ -180,6 +180,27 @@ kep_status kep_spmv(kep_ctx* ctx, const double* x, double* ax, double* bx, int p
 kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, double* lambda,
                              double* x, kep_report* report);
 
+/*
+ * Kernel accounting.  Classes (index into the arrays): 0 assembly (zero, scatter, extend-add),
+ * 1 pivot panel, 2 L21 rows, 3 apply, 4 Schur update, 5 inertia reduction, 6 forward solve,
+ * 7 backward solve, 8 permutation, 9 SpMV, 10 vector operations of the eigenpair driver.
+ * launches[] always counts every kernel launch of ctx since the last reset.  ms[] sums the
+ * CUDA-event time of each launch (events recorded on ctx's stream around the launch) and is
+ * filled only while timing is enabled.
+ */
+#define KEP_NKCLASS 11
+typedef struct {
+  int64_t launches[KEP_NKCLASS];
+  double ms[KEP_NKCLASS];
+  int64_t total_launches;
+} kep_timing;
+
+/* Enable (1) or disable (0) per-launch event timing; synchronises ctx's stream. */
+kep_status kep_set_timing(kep_ctx* ctx, int enable);
+
+/* Copy the counters into *out; reset (1) zeroes them afterwards.  Synchronises ctx's stream. */
+kep_status kep_get_timing(kep_ctx* ctx, kep_timing* out, int reset);
+
 /* Release every resource of ctx (NULL is accepted). */
 void kep_destroy(kep_ctx* ctx);
 

@@ -263,6 +263,42 @@ struct ND {
 
 }  // namespace
 
+// Device memory plan for a given slack: L storage and D storage offsets per front, solve vectors,
+// and the per-level L21 panel workspace.  Leaves never receive delayed columns (no slack).
+void plan_memory(Plan& P, int32_t slack_base) {
+  const int32_t nt = P.nfronts;
+  P.slack.resize(nt); P.m_alloc.resize(nt); P.p_alloc.resize(nt);
+  P.front_off.assign(nt + 1, 0); P.vec_off.assign(nt + 1, 0); P.piv_off.assign(nt + 1, 0);
+  for (int32_t t = 0; t < nt; ++t) {
+    const bool leaf = P.child_ptr[t + 1] == P.child_ptr[t];
+    int32_t s = leaf ? 0 : slack_base + static_cast<int32_t>(static_cast<int64_t>(P.m_sym[t]) * slack_base / 128);
+    P.slack[t] = s;
+    P.m_alloc[t] = P.m_sym[t] + s;
+    P.p_alloc[t] = P.p_sym[t] + s;
+    int64_t sz = static_cast<int64_t>(P.m_alloc[t]) * P.p_alloc[t];
+    sz = (sz + 31) / 32 * 32;
+    P.front_off[t + 1] = P.front_off[t] + sz;
+    P.vec_off[t + 1] = P.vec_off[t] + P.m_alloc[t];
+    P.piv_off[t + 1] = P.piv_off[t] + P.p_alloc[t];
+  }
+  P.front_total = P.front_off[nt];
+  P.vec_total = P.vec_off[nt];
+  P.piv_total = P.piv_off[nt];
+  P.slack_base = slack_base;
+  P.p21_off.assign(nt, 0);
+  P.max_large_rows = 0;
+  if (P.level_ptr.size() != static_cast<size_t>(P.nlevels) + 1) return;
+  for (int32_t l = 0; l < P.nlevels; ++l) {
+    int64_t off = 0;
+    for (int64_t i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
+      int32_t t = P.level_fronts[i];
+      P.p21_off[t] = off;
+      off += static_cast<int64_t>(P.m_alloc[t]) * kPanel;
+    }
+    P.max_large_rows = std::max(P.max_large_rows, off / kPanel);
+  }
+}
+
 kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                       const std::vector<double>& av, const std::vector<double>& bv,
                       const double* coords, bool graph_order, int32_t slack_base, Plan& P,
@@ -409,23 +445,7 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
     for (int32_t c : kids[t]) P.height[t] = std::max(P.height[t], P.height[c] + 1);
   P.nlevels = 0;
   for (int32_t t = 0; t < nt; ++t) P.nlevels = std::max(P.nlevels, P.height[t] + 1);
-  // memory plan
-  P.slack.resize(nt); P.m_alloc.resize(nt); P.p_alloc.resize(nt);
-  P.front_off.assign(nt + 1, 0); P.vec_off.assign(nt + 1, 0); P.piv_off.assign(nt + 1, 0);
-  for (int32_t t = 0; t < nt; ++t) {
-    int32_t s = kids[t].empty() ? 0 : slack_base + P.m_sym[t] / 16;
-    P.slack[t] = s;
-    P.m_alloc[t] = P.m_sym[t] + s;
-    P.p_alloc[t] = P.p_sym[t] + s;
-    int64_t sz = static_cast<int64_t>(P.m_alloc[t]) * P.p_alloc[t];
-    sz = (sz + 31) / 32 * 32;
-    P.front_off[t + 1] = P.front_off[t] + sz;
-    P.vec_off[t + 1] = P.vec_off[t] + P.m_alloc[t];
-    P.piv_off[t + 1] = P.piv_off[t] + P.p_alloc[t];
-  }
-  P.front_total = P.front_off[nt];
-  P.vec_total = P.vec_off[nt];
-  P.piv_total = P.piv_off[nt];
+  plan_memory(P, slack_base);
   P.level_ptr.assign(P.nlevels + 1, 0);
   for (int32_t t = 0; t < nt; ++t) P.level_ptr[P.height[t] + 1]++;
   for (int32_t l = 0; l < P.nlevels; ++l) P.level_ptr[l + 1] += P.level_ptr[l];
@@ -445,10 +465,6 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
       for (int32_t t : small[l]) P.level_fronts[o++] = t;
       for (int32_t t : large[l]) P.level_fronts[o++] = t;
       P.level_nsmall[l] = static_cast<int32_t>(small[l].size());
-      int64_t rows = 0;
-      for (int32_t t : small[l]) rows += P.m_alloc[t];
-      for (int32_t t : large[l]) rows += P.m_alloc[t];
-      P.max_large_rows = std::max(P.max_large_rows, rows);
       P.max_level_width = std::max<int32_t>(P.max_level_width, P.level_ptr[l + 1] - P.level_ptr[l]);
     }
   }
@@ -501,16 +517,7 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
     }
     P.cb_total = std::max<int64_t>(peak, 32);
   }
-  // L21 panel workspace: every front of a level gets its own m_alloc x kPanel slice
-  P.p21_off.assign(nt, 0);
-  for (int32_t l = 0; l < P.nlevels; ++l) {
-    int64_t off = 0;
-    for (int64_t i = P.level_ptr[l]; i < P.level_ptr[l + 1]; ++i) {
-      int32_t t = P.level_fronts[i];
-      P.p21_off[t] = off;
-      off += static_cast<int64_t>(P.m_alloc[t]) * kPanel;
-    }
-  }
+  plan_memory(P, slack_base);   // again: level order is now known (panel workspace offsets)
   // statistics: #nzf and flops of the symbolic factorization
   for (int32_t t = 0; t < nt; ++t) {
     int64_t m = P.m_sym[t], p = P.p_sym[t];

@@ -7,6 +7,8 @@
 
 #include "kep_ctx.h"
 
+static_assert(KEP_NKCLASS == kep::KC_COUNT, "kernel class count");
+
 using namespace kep;
 
 namespace kep {
@@ -25,12 +27,23 @@ static kep_status dev_upload(kep_ctx* c, T** out, const std::vector<T>& v) {
 }
 
 template <typename T>
-static kep_status dev_alloc(kep_ctx* c, T** out, size_t count) {
+static kep_status dev_alloc(kep_ctx* c, T** out, size_t count, bool plan_dependent = false) {
   *out = nullptr;
   void* p = nullptr;
   if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return KEP_ERR_NOMEM;
-  c->allocs.push_back(p);
+  (plan_dependent ? c->mem_allocs : c->allocs).push_back(p);
   *out = static_cast<T*>(p);
+  return KEP_OK;
+}
+
+template <typename T>
+static kep_status dev_upload_mem(kep_ctx* c, const T** out, const std::vector<T>& v) {
+  T* p = nullptr;
+  kep_status st = dev_alloc(c, &p, v.size(), true);
+  if (st != KEP_OK) return st;
+  if (!v.empty() && cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  *out = p;
   return KEP_OK;
 }
 
@@ -40,24 +53,70 @@ static kep_status alloc_slot(kep_ctx* c, int i) {
   if (c->slot_ready[i]) return KEP_OK;
   const Plan& P = c->plan;
   FactorSlot& S = c->slot[i];
-  KEP_TRY(dev_alloc(c, &S.F, P.front_total));
-  KEP_TRY(dev_alloc(c, &S.rowvar, P.vec_total));
-  KEP_TRY(dev_alloc(c, &S.apos, P.vec_total));
-  KEP_TRY(dev_alloc(c, &S.Dd, P.piv_total));
-  KEP_TRY(dev_alloc(c, &S.De, P.piv_total));
-  KEP_TRY(dev_alloc(c, &S.piv, P.piv_total));
-  KEP_TRY(dev_alloc(c, &S.d_in, P.nfronts));
-  KEP_TRY(dev_alloc(c, &S.nelim, P.nfronts));
-  KEP_TRY(dev_alloc(c, &S.d_out, P.nfronts));
-  KEP_TRY(dev_alloc(c, &S.cnt, 3 * static_cast<size_t>(P.nfronts)));
-  KEP_TRY(dev_alloc(c, &S.status, 2));
+  KEP_TRY(dev_alloc(c, &S.F, P.front_total, true));
+  KEP_TRY(dev_alloc(c, &S.rowvar, P.vec_total, true));
+  KEP_TRY(dev_alloc(c, &S.apos, P.vec_total, true));
+  KEP_TRY(dev_alloc(c, &S.Dd, P.piv_total, true));
+  KEP_TRY(dev_alloc(c, &S.De, P.piv_total, true));
+  KEP_TRY(dev_alloc(c, &S.piv, P.piv_total, true));
+  KEP_TRY(dev_alloc(c, &S.d_in, P.nfronts, true));
+  KEP_TRY(dev_alloc(c, &S.nelim, P.nfronts, true));
+  KEP_TRY(dev_alloc(c, &S.d_out, P.nfronts, true));
+  KEP_TRY(dev_alloc(c, &S.cnt, 3 * static_cast<size_t>(P.nfronts), true));
+  KEP_TRY(dev_alloc(c, &S.status, 2, true));
   S.valid = false;
   c->slot_ready[i] = true;
   return KEP_OK;
 }
 
+// Upload the slack-dependent tables and allocate the slack-dependent workspaces.
+kep_status setup_memory(kep_ctx* c) {
+  const Plan& P = c->plan;
+  KEP_TRY(dev_upload_mem(c, &c->T.m_alloc, P.m_alloc));
+  KEP_TRY(dev_upload_mem(c, &c->T.front_off, P.front_off));
+  KEP_TRY(dev_upload_mem(c, &c->T.vec_off, P.vec_off));
+  KEP_TRY(dev_upload_mem(c, &c->T.piv_off, P.piv_off));
+  const int64_t* p21 = nullptr;
+  KEP_TRY(dev_upload_mem(c, &p21, P.p21_off));
+  c->W.p21_off = const_cast<int64_t*>(p21);
+  KEP_TRY(dev_alloc(c, &c->W.P21, std::max<int64_t>(P.max_large_rows, 1) * kPanel, true));
+  KEP_TRY(dev_alloc(c, &c->d_vasm, P.vec_total, true));
+  KEP_TRY(dev_alloc(c, &c->d_vfac, P.vec_total, true));
+  return KEP_OK;
+}
+
+void release_memory(kep_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  for (void* p : c->mem_allocs) cudaFree(p);
+  c->mem_allocs.clear();
+  for (int i = 0; i < 2; ++i) { c->slot_ready[i] = false; c->slot[i].valid = false; }
+}
+
+// Delayed pivots overflowed a front's slack: grow the slack of every non-leaf front and rebuild
+// the slack-dependent storage (the ordering, tree and index maps stay).
+static kep_status replan(kep_ctx* c, int32_t slack_base) {
+  release_memory(c);
+  plan_memory(c->plan, slack_base);
+  ++c->replans;
+  return setup_memory(c);
+}
+
+kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out, int* bits_out);
+
 kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out) {
-  KEP_TRY(alloc_slot(c, slot));
+  for (int attempt = 0;; ++attempt) {
+    KEP_TRY(alloc_slot(c, slot));
+    int bits = 0;
+    kep_status st = ctx_factor_once(c, slot, ca, cb, out, &bits);
+    if (st == KEP_ERR_POOL && (bits & ST_POOL) && attempt < 4) {
+      KEP_TRY(replan(c, c->plan.slack_base * 4));
+      continue;
+    }
+    return st;
+  }
+}
+
+kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out, int* bits_out) {
   FactorSlot& S = c->slot[slot];
   S.valid = false;
   FactorLaunch F;
@@ -72,9 +131,11 @@ kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* o
   F.h_red = c->h_red;
   F.stream = c->stream;
   F.num_sms = c->num_sms;
+  F.timer = &c->timer;
   int bits = 0;
   kep_inertia in{0, 0, 0, 0};
   kep_status st = run_factor(F, ca, cb, &in, &bits);
+  *bits_out = bits;
   if (st != KEP_OK) return st;
   S.ca = ca; S.cb = cb;
   c->slot_status[slot] = bits;
@@ -104,11 +165,12 @@ kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x) {
   L.xnew = c->d_xnew;
   L.stream = c->stream;
   L.num_sms = c->num_sms;
+  L.timer = &c->timer;
   return run_solve(L, b, x);
 }
 
 kep_status ctx_spmv_dev(kep_ctx* c, const double* x, double* ax, double* bx) {
-  return run_spmv(c->plan.n, c->d_rp, c->d_ci, c->d_a, c->d_b, x, ax, bx, c->stream, c->num_sms);
+  return run_spmv(c->plan.n, c->d_rp, c->d_ci, c->d_a, c->d_b, x, ax, bx, c->stream, c->num_sms, &c->timer);
 }
 
 }  // namespace kep
@@ -208,16 +270,15 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   if (st != KEP_OK) { delete c; return st; }
   const Plan& P = c->plan;
 #define UP(dst, vec) do { st = dev_upload(c, &dst, vec); if (st != KEP_OK) { kep_destroy(c); return st; } } while (0)
-  int32_t *first, *p_sym, *m_sym, *m_alloc, *parent, *child_ptr, *child_idx, *struct_var, *relmap, *ent_r, *ent_c;
-  int64_t *struct_ptr, *relmap_ptr, *ent_ptr, *front_off, *cb_off, *vec_off, *piv_off, *p21_off;
+  int32_t *first, *p_sym, *m_sym, *parent, *child_ptr, *child_idx, *struct_var, *relmap, *ent_r, *ent_c;
+  int64_t *struct_ptr, *relmap_ptr, *ent_ptr, *cb_off;
   double *ent_a, *ent_b;
-  UP(first, P.first); UP(p_sym, P.p_sym); UP(m_sym, P.m_sym); UP(m_alloc, P.m_alloc);
+  UP(first, P.first); UP(p_sym, P.p_sym); UP(m_sym, P.m_sym);
   UP(parent, P.parent); UP(child_ptr, P.child_ptr); UP(child_idx, P.child_idx);
   UP(struct_ptr, P.struct_ptr); UP(struct_var, P.struct_var);
   UP(relmap_ptr, P.relmap_ptr); UP(relmap, P.relmap);
   UP(ent_ptr, P.ent_ptr); UP(ent_r, P.ent_r); UP(ent_c, P.ent_c); UP(ent_a, P.ent_a); UP(ent_b, P.ent_b);
-  UP(front_off, P.front_off); UP(cb_off, P.cb_off); UP(vec_off, P.vec_off); UP(piv_off, P.piv_off);
-  UP(p21_off, P.p21_off);
+  UP(cb_off, P.cb_off);
   UP(c->d_level_fronts, P.level_fronts);
   UP(c->d_perm, P.perm);
   UP(c->d_iperm, P.iperm);
@@ -225,28 +286,26 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
 #undef UP
   FrontTables& T = c->T;
   T.nfronts = P.nfronts;
-  T.first = first; T.p_sym = p_sym; T.m_sym = m_sym; T.m_alloc = m_alloc; T.parent = parent;
+  T.first = first; T.p_sym = p_sym; T.m_sym = m_sym; T.parent = parent;
   T.child_ptr = child_ptr; T.child_idx = child_idx; T.struct_ptr = struct_ptr; T.struct_var = struct_var;
   T.relmap_ptr = relmap_ptr; T.relmap = relmap; T.ent_ptr = ent_ptr; T.ent_r = ent_r; T.ent_c = ent_c;
-  T.ent_a = ent_a; T.ent_b = ent_b; T.front_off = front_off; T.cb_off = cb_off; T.vec_off = vec_off;
-  T.piv_off = piv_off;
+  T.ent_a = ent_a; T.ent_b = ent_b; T.cb_off = cb_off;
   // workspaces
   const int64_t ent = std::max<int32_t>(P.max_level_width, 1);
   LargeWork& W = c->W;
   W.cap = static_cast<int32_t>(ent);
-  W.p21_off = p21_off;
   W.list = nullptr;
 #define AL(dst, count) do { st = dev_alloc(c, &dst, count); if (st != KEP_OK) { kep_destroy(c); return st; } } while (0)
-  AL(W.k, ent); AL(W.w, ent); AL(W.q, ent); AL(W.fails, ent); AL(W.done, ent);
+  AL(W.k, ent); AL(W.w, ent); AL(W.q, ent); AL(W.fails, ent); AL(W.swap, ent); AL(W.done, ent);
   AL(W.L11, ent * kPanel * kPanel); AL(W.Dblk, ent * 2 * kPanel); AL(W.pi, ent * kPanel);
   AL(W.pt, ent * kPanel); AL(W.colmax, ent * kPanel);
-  AL(W.P21, std::max<int64_t>(P.max_large_rows, 1) * kPanel);
   AL(c->d_cbpool, P.cb_total);
   AL(c->d_red, 8);
-  AL(c->d_vasm, P.vec_total); AL(c->d_vfac, P.vec_total);
   AL(c->d_bnew, P.n); AL(c->d_xnew, P.n);
   AL(c->d_io0, P.n); AL(c->d_io1, P.n); AL(c->d_io2, P.n);
 #undef AL
+  st = setup_memory(c);
+  if (st != KEP_OK) { kep_destroy(c); return st; }
   if (cudaMallocHost(reinterpret_cast<void**>(&c->h_done), sizeof(int32_t) * ent) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(long long) * 8) != cudaSuccess) {
     kep_destroy(c);
@@ -307,6 +366,7 @@ kep_status kep_solve(kep_ctx* c, const double* rhs, double* x, int64_t nrhs, int
     if (st != KEP_OK) return st;
   }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  c->timer.collect();
   return KEP_OK;
 }
 
@@ -328,6 +388,30 @@ kep_status kep_spmv(kep_ctx* c, const double* x, double* ax, double* bx, int ptr
   }
   if (st != KEP_OK) return st;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  c->timer.collect();
+  return KEP_OK;
+}
+
+kep_status kep_set_timing(kep_ctx* c, int enable) {
+  if (!c) return KEP_ERR_INVALID;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  c->timer.collect();
+  c->timer.enabled = enable != 0;
+  return KEP_OK;
+}
+
+kep_status kep_get_timing(kep_ctx* c, kep_timing* out, int reset) {
+  if (!c || !out) return KEP_ERR_INVALID;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  c->timer.collect();
+  int64_t total = 0;
+  for (int k = 0; k < KEP_NKCLASS; ++k) {
+    out->launches[k] = c->timer.launches[k];
+    out->ms[k] = c->timer.ms[k];
+    total += c->timer.launches[k];
+  }
+  out->total_launches = total;
+  if (reset) c->timer.reset();
   return KEP_OK;
 }
 
@@ -335,9 +419,11 @@ void kep_destroy(kep_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->mem_allocs) cudaFree(p);
   if (c->h_done) cudaFreeHost(c->h_done);
   if (c->h_red) cudaFreeHost(c->h_red);
   c->driver_release();
+  c->timer.release();
   delete c;
 }
 

@@ -57,7 +57,7 @@ __global__ void lf_init_kernel(FrontTables T, FactorSlot S, double* cbpool, Larg
     S.nelim[t] = 0;
     S.d_out[t] = 0;
     S.cnt[3 * t] = S.cnt[3 * t + 1] = S.cnt[3 * t + 2] = 0;
-    W.k[b] = 0; W.q[b] = 0; W.w[b] = 0; W.fails[b] = 0; W.done[b] = bad ? 1 : 0;
+    W.k[b] = 0; W.q[b] = 0; W.w[b] = 0; W.fails[b] = 0; W.swap[b] = 0; W.done[b] = bad ? 1 : 0;
     if (bad) {
       atomicOr(&S.status[0], ST_POOL);
       atomicCAS(&S.status[1], -1, t);
@@ -382,12 +382,21 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&S.status[0], ST_ROOT_FORCED);
   }
   if (q == 0) {
-    // no pivot of this block passes the threshold: the remaining fully-summed columns go to
-    // the parent (delayed pivots)
+    // the block's first pivot fails the threshold: move that pivot's column(s) to the end of the
+    // fully-summed range and retry with the others; once every remaining column has failed in
+    // turn without progress, the remaining columns go to the parent (delayed pivots)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      W.done[b] = 1;
-      S.nelim[t] = k;
-      S.d_out[t] = p - k;
+      const int32_t nf = W.pt[b * kPanel] == 2 ? 2 : 1;
+      const int32_t f = W.fails[b] + 1;
+      W.fails[b] = f;
+      if (f > p - k || p - k <= nf) {
+        W.done[b] = 1;
+        S.nelim[t] = k;
+        S.d_out[t] = p - k;
+        W.swap[b] = 0;
+      } else {
+        W.swap[b] = nf;
+      }
     }
     return;
   }
@@ -455,6 +464,7 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
         S.cnt[3 * t] += neg; S.cnt[3 * t + 1] += zero; S.cnt[3 * t + 2] += pos;
         if (!finite) { atomicOr(&S.status[0], ST_NONFINITE); atomicCAS(&S.status[1], -1, t); }
         W.q[b] = q;
+        W.fails[b] = 0;
       }
       __syncthreads();
     } else if (item <= nA) {
@@ -483,6 +493,60 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
       __syncthreads();
     }
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// move a failed pivot to the end: symmetric interchange of fully-summed positions a < z of the
+// front (both < p, so every touched entry lives in the L storage), with its row bookkeeping
+// ------------------------------------------------------------------------------------------
+KEP_D void sym_swap_front(double* L, int64_t ld, int32_t m, int32_t a, int32_t z, int32_t* rv, int32_t* ap) {
+  if (a == z) return;
+  if (a > z) { int32_t tmp = a; a = z; z = tmp; }
+  for (int32_t c = threadIdx.x; c < a; c += blockDim.x) {        // rows a and z of earlier columns
+    double* col = L + static_cast<int64_t>(c) * ld;
+    double x = col[a]; col[a] = col[z]; col[z] = x;
+  }
+  for (int32_t c = a + 1 + threadIdx.x; c < z; c += blockDim.x) { // (c, a) <-> (z, c)
+    double* pa = L + static_cast<int64_t>(a) * ld + c;
+    double* pz = L + static_cast<int64_t>(c) * ld + z;
+    double x = *pa; *pa = *pz; *pz = x;
+  }
+  for (int32_t r = z + 1 + threadIdx.x; r < m; r += blockDim.x) { // (r, a) <-> (r, z)
+    double* pa = L + static_cast<int64_t>(a) * ld + r;
+    double* pz = L + static_cast<int64_t>(z) * ld + r;
+    double x = *pa; *pa = *pz; *pz = x;
+  }
+  if (threadIdx.x == 0) {
+    double* da = L + static_cast<int64_t>(a) * ld + a;
+    double* dz = L + static_cast<int64_t>(z) * ld + z;
+    double x = *da; *da = *dz; *dz = x;
+    int32_t v = rv[a]; rv[a] = rv[z]; rv[z] = v;
+    v = ap[a]; ap[a] = ap[z]; ap[z] = v;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) lf_swap_kernel(FrontTables T, FactorSlot S, LargeWork W, Batch B) {
+  const int32_t b = B.e0 + blockIdx.x;
+  if (W.done[b]) return;
+  const int32_t nf = W.swap[b];
+  if (nf == 0) return;
+  const int32_t t = B.lf[b];
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in, p = T.p_sym[t] + d_in;
+  const int32_t k = W.k[b];
+  double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  int32_t* rv = S.rowvar + T.vec_off[t];
+  int32_t* ap = S.apos + T.vec_off[t];
+  const int32_t a0 = k + W.pi[b * kPanel];
+  int32_t a1 = nf == 2 ? k + W.pi[b * kPanel + 1] : -1;
+  sym_swap_front(L, ld, m, a0, p - 1, rv, ap);
+  if (nf == 2) {
+    if (a1 == p - 1) a1 = a0;              // the first interchange moved it
+    sym_swap_front(L, ld, m, a1, p - 2, rv, ap);
+  }
+  if (threadIdx.x == 0) W.swap[b] = 0;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -647,17 +711,19 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
         max_ent = std::max<int64_t>(max_ent, P.ent_ptr[t + 1] - P.ent_ptr[t]);
       }
       const int gx_cols = grid_cap(std::max(max_p, max_c), std::max<int64_t>(1, (target + nb - 1) / nb));
-      lf_init_kernel<<<dim3(gx_cols, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B);
-      lf_scatter_kernel<<<dim3(grid_cap((max_ent + 255) / 256, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 256, 0, st>>>(
-          F.T, F.S, F.cbpool, B, ca, cb);
+      KEP_LAUNCH(F.timer, KC_ASSEMBLE, st, lf_init_kernel<<<dim3(gx_cols, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
+      KEP_LAUNCH(F.timer, KC_ASSEMBLE, st,
+                 lf_scatter_kernel<<<dim3(grid_cap((max_ent + 255) / 256, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 256, 0, st>>>(
+                     F.T, F.S, F.cbpool, B, ca, cb));
       int32_t maxch = 0;
       for (int32_t i = e; i < e1; ++i) {
         int32_t t = P.level_fronts[lb + i];
         maxch = std::max(maxch, P.child_ptr[t + 1] - P.child_ptr[t]);
       }
       for (int32_t s = 0; s < maxch; ++s)
-        lf_extend_kernel<<<dim3(grid_cap(max_m, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 128, 0, st>>>(
-            F.T, F.S, F.cbpool, B, s);
+        KEP_LAUNCH(F.timer, KC_ASSEMBLE, st,
+                   lf_extend_kernel<<<dim3(grid_cap(max_m, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 128, 0, st>>>(
+                       F.T, F.S, F.cbpool, B, s));
       const int64_t rowtiles = (max_m + kRowTile - 1) / kRowTile;
       const int gx_rows = grid_cap(rowtiles, std::max<int64_t>(1, (target + nb - 1) / nb));
       const int gx_apply = grid_cap(rowtiles + max_p / 32 + 2, std::max<int64_t>(1, (target + nb - 1) / nb));
@@ -666,16 +732,19 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       int64_t steps = (max_p + kPanel - 1) / kPanel + 1;
       while (true) {
         for (int64_t it = 0; it < steps; ++it) {
-          lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B);
-          lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B);
-          lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B);
-          lf_update_kernel<<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B);
+          KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B));
+          KEP_LAUNCH(F.timer, KC_L21, st, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B));
+          KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
+          KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
+          KEP_LAUNCH(F.timer, KC_UPDATE, st,
+                     lf_update_kernel<<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
         }
         // one more panel call finalises fronts whose last block was accepted
-        lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B);
+        KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B));
         if (cudaMemcpyAsync(F.h_done, F.W.done + e, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
           return KEP_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;
+        F.timer->collect();
         bool all = true;
         for (int32_t i = 0; i < nb; ++i) all = all && F.h_done[i];
         if (all) break;
@@ -684,10 +753,11 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       e = e1;
     }
   }
-  reduce_inertia_kernel<<<1, 1024, 0, st>>>(F.S, P.nfronts, F.d_red);
+  KEP_LAUNCH(F.timer, KC_REDUCE, st, reduce_inertia_kernel<<<1, 1024, 0, st>>>(F.S, P.nfronts, F.d_red));
   if (cudaMemcpyAsync(F.h_red, F.d_red, 6 * sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return KEP_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;
+  F.timer->collect();
   if (cudaGetLastError() != cudaSuccess) return KEP_ERR_CUDA;
   out->neg = F.h_red[0];
   out->zero = F.h_red[1];

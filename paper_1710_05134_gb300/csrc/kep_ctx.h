@@ -11,7 +11,9 @@ struct kep_ctx {
   int num_sms = 1;
   cudaStream_t stream = nullptr;
   kep::Plan plan;
-  std::vector<void*> allocs;        // every cudaMalloc of this context
+  std::vector<void*> allocs;        // cudaMallocs that live as long as the context
+  std::vector<void*> mem_allocs;    // cudaMallocs that depend on the slack plan (redone on re-plan)
+  int replans = 0;
   kep::FrontTables T{};
   int32_t* d_level_fronts = nullptr;
   int32_t* d_perm = nullptr;
@@ -40,6 +42,7 @@ struct kep_ctx {
   double* d_io0 = nullptr;
   double* d_io1 = nullptr;
   double* d_io2 = nullptr;
+  kep::Timer timer;
   // eigenpair driver state (owned by driver.cu)
   void* driver = nullptr;
   void driver_release();

@@ -20,6 +20,66 @@ constexpr double kBKAlpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
 constexpr double kThresholdU = 0.01;               // threshold pivoting parameter u
 
 // ---------------------------------------------------------------------------------------------
+// Kernel launch accounting: every launch is counted per class; when enabled, each launch is
+// bracketed by CUDA events on its stream and the elapsed times are summed at the next sync.
+// ---------------------------------------------------------------------------------------------
+enum KClass : int {
+  KC_ASSEMBLE = 0, KC_PANEL, KC_L21, KC_APPLY, KC_UPDATE, KC_REDUCE,
+  KC_SOLVE_FWD, KC_SOLVE_BWD, KC_PERM, KC_SPMV, KC_VEC, KC_COUNT
+};
+
+struct Timer {
+  bool enabled = false;
+  int64_t launches[KC_COUNT] = {};
+  double ms[KC_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> pending_cls;       // class of each recorded pair (events 2i, 2i+1)
+  cudaEvent_t next_event() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  // record the start event of a launch of class cls (returns false when disabled)
+  bool begin(int cls, cudaStream_t s) {
+    ++launches[cls];
+    if (!enabled) return false;
+    cudaEventRecord(next_event(), s);
+    pending_cls.push_back(cls);
+    return true;
+  }
+  void end(bool started, cudaStream_t s) {
+    if (started) cudaEventRecord(next_event(), s);
+  }
+  // after the stream has synchronised: add up the recorded pairs and recycle the events
+  void collect() {
+    for (size_t i = 0; i < pending_cls.size(); ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[pending_cls[i]] += t;
+    }
+    pending_cls.clear();
+    used = 0;
+  }
+  void reset() {
+    for (int c = 0; c < KC_COUNT; ++c) { launches[c] = 0; ms[c] = 0.0; }
+  }
+  void release() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear(); used = 0; pending_cls.clear();
+  }
+};
+
+#define KEP_LAUNCH(timer, cls, stream, ...)                  \
+  do {                                                        \
+    bool _kep_started = (timer)->begin((cls), (stream));      \
+    __VA_ARGS__;                                              \
+    (timer)->end(_kep_started, (stream));                     \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
 // Host-side symbolic plan (built once by kep_analyze, Section 3.3)
 // ---------------------------------------------------------------------------------------------
 struct Plan {
@@ -58,6 +118,7 @@ struct Plan {
   int32_t max_level_width = 0;
   std::vector<int64_t> p21_off;     // per front: offset of its L21 panel in the level workspace
   int32_t max_children = 0;
+  int32_t slack_base = 0;
   // statistics
   int64_t max_front = 0, nnz_factor = 0;
   double flops = 0;
@@ -70,6 +131,9 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
                       const std::vector<double>& av, const std::vector<double>& bv,
                       const double* coords, bool graph_order, int32_t slack_base, Plan& plan,
                       std::string& err);
+
+// (Re)compute the slack-dependent memory plan.
+void plan_memory(Plan& plan, int32_t slack_base);
 
 // ---------------------------------------------------------------------------------------------
 // Device layout
@@ -132,6 +196,7 @@ struct LargeWork {
   int32_t* w;           // current block width
   int32_t* q;           // accepted in current block
   int32_t* fails;       // consecutive failed blocks
+  int32_t* swap;        // pending move of a failed pivot (1 or 2 columns) to the end
   int32_t* done;        // 1 when the front has finished
   double* L11;          // per batch entry: kPanel*kPanel
   double* Dblk;         // per batch entry: 2*kPanel (diag, offdiag)
@@ -155,6 +220,7 @@ struct FactorLaunch {
   long long* h_red;         // pinned
   cudaStream_t stream;
   int num_sms;
+  Timer* timer;
 };
 
 struct SolveLaunch {
@@ -169,11 +235,13 @@ struct SolveLaunch {
   double* xnew;
   cudaStream_t stream;
   int num_sms;
+  Timer* timer;
 };
 
 kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, int* status_bits);
 kep_status run_solve(SolveLaunch& L, const double* b, double* x);
 kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
-                    const double* x, double* ya, double* yb, cudaStream_t st, int num_sms);
+                    const double* x, double* ya, double* yb, cudaStream_t st, int num_sms,
+                    Timer* timer);
 
 }  // namespace kep

@@ -193,18 +193,20 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   const Plan& P = *L.plan;
   cudaStream_t st = L.stream;
   const int g = L.num_sms * 4;
-  gather_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, b, L.bnew);
+  KEP_LAUNCH(L.timer, KC_PERM, st, gather_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, b, L.bnew));
   for (int32_t l = 0; l < P.nlevels; ++l) {
     const int32_t w = P.level_ptr[l + 1] - P.level_ptr[l];
-    sv_fwd_kernel<<<w, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + P.level_ptr[l], L.bnew,
-                                               L.vasm, L.vfac);
+    KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st,
+               sv_fwd_kernel<<<w, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + P.level_ptr[l], L.bnew,
+                                                          L.vasm, L.vfac));
   }
   for (int32_t l = P.nlevels - 1; l >= 0; --l) {
     const int32_t w = P.level_ptr[l + 1] - P.level_ptr[l];
-    sv_bwd_kernel<<<w, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + P.level_ptr[l], L.xnew,
-                                               L.vfac);
+    KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
+               sv_bwd_kernel<<<w, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + P.level_ptr[l], L.xnew,
+                                                          L.vfac));
   }
-  scatter_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, L.xnew, x);
+  KEP_LAUNCH(L.timer, KC_PERM, st, scatter_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, L.xnew, x));
   return cudaGetLastError() == cudaSuccess ? KEP_OK : KEP_ERR_CUDA;
 }
 

@@ -43,12 +43,16 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_ab_kernel(int64_t n, const 
 }  // namespace
 
 kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
-                    const double* x, double* ya, double* yb, cudaStream_t st, int num_sms) {
+                    const double* x, double* ya, double* yb, cudaStream_t st, int num_sms,
+                    Timer* timer) {
   const int64_t want = (n * 8 + kSpmvThreads - 1) / kSpmvThreads;
   const int grid = static_cast<int>(want < num_sms * 16 ? want : num_sms * 16);
-  if (ya && yb) spmv_ab_kernel<true, true><<<grid, kSpmvThreads, 0, st>>>(n, rp, ci, a, b, x, ya, yb);
-  else if (ya) spmv_ab_kernel<true, false><<<grid, kSpmvThreads, 0, st>>>(n, rp, ci, a, b, x, ya, yb);
-  else if (yb) spmv_ab_kernel<false, true><<<grid, kSpmvThreads, 0, st>>>(n, rp, ci, a, b, x, ya, yb);
+  if (ya && yb)
+    KEP_LAUNCH(timer, KC_SPMV, st, spmv_ab_kernel<true, true><<<grid, kSpmvThreads, 0, st>>>(n, rp, ci, a, b, x, ya, yb));
+  else if (ya)
+    KEP_LAUNCH(timer, KC_SPMV, st, spmv_ab_kernel<true, false><<<grid, kSpmvThreads, 0, st>>>(n, rp, ci, a, b, x, ya, yb));
+  else if (yb)
+    KEP_LAUNCH(timer, KC_SPMV, st, spmv_ab_kernel<false, true><<<grid, kSpmvThreads, 0, st>>>(n, rp, ci, a, b, x, ya, yb));
   return cudaGetLastError() == cudaSuccess ? KEP_OK : KEP_ERR_CUDA;
 }
 

@@ -22,8 +22,10 @@ KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 
 # symbols declared in include/kep.h
 EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
-            "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_destroy",
-            "kep_status_str"]
+            "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
+            "kep_get_timing", "kep_destroy", "kep_status_str"]
+KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
+                  "perm", "spmv", "vec"]
 
 
 class KepError(RuntimeError):
@@ -51,6 +53,11 @@ class Params(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int64), ("tau_res", ctypes.c_double), ("tau_diff", ctypes.c_double),
                 ("max_lanczos", ctypes.c_int64), ("max_si", ctypes.c_int64),
                 ("start_vectors", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 11), ("ms", ctypes.c_double * 11),
+                ("total_launches", ctypes.c_int64)]
 
 
 class Report(ctypes.Structure):
@@ -91,12 +98,14 @@ def lib() -> ctypes.CDLL:
         L.kep_spmv.argtypes = [P, P, P, P, I]
         L.kep_kth_eigenpair.argtypes = [P, I64, ctypes.POINTER(Params), ctypes.POINTER(D), P,
                                         ctypes.POINTER(Report)]
+        L.kep_set_timing.argtypes = [P, I]
+        L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
         L.kep_destroy.argtypes = [P]
         L.kep_destroy.restype = None
         L.kep_status_str.argtypes = [I]
         L.kep_status_str.restype = ctypes.c_char_p
         for name in ["kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
-                     "kep_solve", "kep_spmv", "kep_kth_eigenpair"]:
+                     "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing", "kep_get_timing"]:
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -192,6 +201,18 @@ class Problem:
         handle = getattr(stream, "cuda_stream", stream)
         self._stream = stream
         _check(lib().kep_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)), "kep_set_stream")
+
+    def set_timing(self, enable: bool):
+        """Per-launch CUDA-event timing of this context's kernels (launch counts are always kept)."""
+        _check(lib().kep_set_timing(self._h, 1 if enable else 0), "kep_set_timing")
+
+    def timing(self, reset: bool = False) -> dict:
+        """{class: (launches, milliseconds)} since the last reset, plus 'total_launches'."""
+        t = Timing()
+        _check(lib().kep_get_timing(self._h, ctypes.byref(t), 1 if reset else 0), "kep_get_timing")
+        d = {name: (int(t.launches[i]), float(t.ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
+        d["total_launches"] = int(t.total_launches)
+        return d
 
     def factor(self, sigma: float, *, allow_singular: bool = True) -> FactorResult:
         """LDL^T of A - sigma*B; .nu is the number of eigenvalues below sigma."""
