@@ -1,10 +1,505 @@
-// Three-stage k-th eigenpair driver (Algorithm 4).
+// Three-stage k-th eigenpair driver (Algorithm 4, Section 3.4) on the GPU path.
+//
+//  Stage 1 (Algorithm 2): factor B (task (ii) of Section 4.3), run the generalized Lanczos process
+//    A V_j = B V_j T_j + B v_{j+1} beta_j e_j^T (Eq. 2.2, V_j B-orthonormal, w = B^{-1} A v_j), take
+//    sigma^(j) = theta_1^(j) if k <= nu^(j-1) else theta_j^(j) and factor A - sigma^(j) B, until nu
+//    brackets k at j != 1.
+//  Stage 2 (Algorithm 1'): bisect [sigma_l, sigma_u) until nu_u - nu_l <= m_max.
+//  Stage 3 (Algorithm 3): factor A - sigma B at the midpoint and run the shift-and-invert Lanczos
+//    process of Eq. 2.5.  It is carried out for V = B^{-1} V~ (so V is B-orthonormal and only
+//    (A - sigma B)^{-1} and products with B are needed): (A - sigma B)^{-1} B V_j = V_j T~_j +
+//    v_{j+1} beta~_j e_j^T, the same T~_j.  Ritz values lambda_i = sigma + 1/theta~_i (Eq. 2.7); the
+//    modified Ritz vectors x_{i,2} = (A - sigma B)^{-1} V~_j y~_i (Eq. 2.9) follow without a solve from
+//    the decomposition: x_{i,2} = theta~_i V_j y~_i + v_{j+1} beta~_j (e_j^T y~_i) (proof of
+//    Proposition 1).  Bounds eta_i (Proposition 3, Eq. 3.1), inclusion (3.3), disjointness (3.4),
+//    residual and relative difference (3.5) decide convergence; the residual uses the identity
+//    r_{i,2} = -B v_{j+1} (beta~_j e_j^T y~_i / theta~_i) (Eq. 2.12) while iterating and is recomputed
+//    explicitly with the sparse products before the result is accepted.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
 #include "kep_ctx.h"
+#include "kep_vec.h"
 
-void kep_ctx::driver_release() {}
+namespace kep {
 
-extern "C" kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, double* lambda,
-                                        double* x, kep_report* report) {
-  (void)ctx; (void)k; (void)params; (void)lambda; (void)x; (void)report;
-  return KEP_ERR_INVALID;
+// ----------------------------------------------------------------------------------------------
+// symmetric tridiagonal eigenproblem: implicit QR steps with Wilkinson shifts, applied as Givens
+// rotations to a dense copy (m is at most a few hundred here), rotations accumulated into z
+// ----------------------------------------------------------------------------------------------
+bool tridiag_eigen(int m, const double* d, const double* e, double* w, double* z) {
+  std::vector<double> T(static_cast<size_t>(m) * m, 0.0);
+  auto t = [&](int i, int j) -> double& { return T[static_cast<size_t>(j) * m + i]; };
+  for (int i = 0; i < m; ++i) {
+    t(i, i) = d[i];
+    if (i + 1 < m) { t(i + 1, i) = e[i]; t(i, i + 1) = e[i]; }
+  }
+  for (int i = 0; i < m * m; ++i) z[i] = 0.0;
+  for (int i = 0; i < m; ++i) z[static_cast<size_t>(i) * m + i] = 1.0;
+  const double eps = 2.220446049250313e-16;
+  auto small = [&](int q) {   // is the sub-diagonal entry (q, q-1) negligible?
+    double s = std::fabs(t(q, q)) + std::fabs(t(q - 1, q - 1));
+    return std::fabs(t(q, q - 1)) <= eps * s || std::fabs(t(q, q - 1)) < 1e-300;
+  };
+  int q = m - 1;
+  int iter = 0;
+  const int max_iter = 60 * std::max(m, 1);
+  while (q > 0) {
+    if (small(q)) { t(q, q - 1) = t(q - 1, q) = 0.0; --q; continue; }
+    if (++iter > max_iter) return false;
+    int p = q - 1;
+    while (p > 0 && !small(p)) --p;
+    if (p > 0) { t(p, p - 1) = t(p - 1, p) = 0.0; }
+    // Wilkinson shift: eigenvalue of the trailing 2x2 block closer to t(q, q)
+    const double a = t(q - 1, q - 1), b = t(q, q - 1), c = t(q, q);
+    const double delta = 0.5 * (a - c);
+    const double sg = delta >= 0 ? 1.0 : -1.0;
+    const double mu = c - b * b / (delta + sg * std::sqrt(delta * delta + b * b));
+    double x = t(p, p) - mu, y = t(p + 1, p);
+    for (int k = p; k < q; ++k) {
+      const double r = std::hypot(x, y);
+      const double cs = r == 0.0 ? 1.0 : x / r, sn = r == 0.0 ? 0.0 : y / r;
+      const int lo = std::max(p, k - 1), hi = std::min(q, k + 2);
+      for (int col = lo; col <= hi; ++col) {      // rows k, k+1
+        const double u = t(k, col), v = t(k + 1, col);
+        t(k, col) = cs * u + sn * v;
+        t(k + 1, col) = -sn * u + cs * v;
+      }
+      for (int row = lo; row <= hi; ++row) {      // columns k, k+1
+        const double u = t(row, k), v = t(row, k + 1);
+        t(row, k) = cs * u + sn * v;
+        t(row, k + 1) = -sn * u + cs * v;
+      }
+      for (int row = 0; row < m; ++row) {         // accumulate Z <- Z G^T
+        double* zk = z + static_cast<size_t>(k) * m;
+        double* zk1 = z + static_cast<size_t>(k + 1) * m;
+        const double u = zk[row], v = zk1[row];
+        zk[row] = cs * u + sn * v;
+        zk1[row] = -sn * u + cs * v;
+      }
+      if (k + 1 < q) { x = t(k + 1, k); y = t(k + 2, k); }
+    }
+  }
+  // sort ascending
+  std::vector<int> idx(m);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int i, int j) { return t(i, i) < t(j, j); });
+  std::vector<double> zc(z, z + static_cast<size_t>(m) * m);
+  for (int i = 0; i < m; ++i) {
+    w[i] = t(idx[i], idx[i]);
+    std::memcpy(z + static_cast<size_t>(i) * m, zc.data() + static_cast<size_t>(idx[i]) * m, sizeof(double) * m);
+  }
+  return true;
+}
+
+namespace {
+
+struct Driver {
+  int64_t cap_cols = 0;
+  double* V = nullptr;      // n x cap_cols, B-orthonormal basis
+  double* BV = nullptr;     // B * V
+  double* w = nullptr;      // work vectors
+  double* u = nullptr;
+  double* u2 = nullptr;
+  double* coef = nullptr;   // device coefficients (cap_cols)
+  double* partial = nullptr;
+  int nblocks = 0;
+};
+
+// splitmix64 (Steele, Lea, Flood 2014) as a counter-based generator; Box-Muller for N(0, 1).
+uint64_t splitmix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+void gaussian_vector(uint64_t seed, int64_t n, double* out) {
+  const double two_pi = 6.283185307179586;
+  for (int64_t i = 0; i < n; i += 2) {
+    const uint64_t r1 = splitmix64(seed * 0x100000001b3ull + 2 * static_cast<uint64_t>(i));
+    const uint64_t r2 = splitmix64(seed * 0x100000001b3ull + 2 * static_cast<uint64_t>(i) + 1);
+    const double u1 = (static_cast<double>(r1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    const double u2 = static_cast<double>(r2 >> 11) * (1.0 / 9007199254740992.0);
+    const double rad = std::sqrt(-2.0 * std::log(u1));
+    out[i] = rad * std::cos(two_pi * u2);
+    if (i + 1 < n) out[i + 1] = rad * std::sin(two_pi * u2);
+  }
+}
+
+using clock_ = std::chrono::steady_clock;
+double seconds_since(clock_::time_point t0) {
+  return std::chrono::duration<double>(clock_::now() - t0).count();
+}
+
+}  // namespace
+}  // namespace kep
+
+using namespace kep;
+
+void kep_ctx::driver_release() {
+  Driver* d = static_cast<Driver*>(driver);
+  if (!d) return;
+  cudaFree(d->V); cudaFree(d->BV); cudaFree(d->w); cudaFree(d->u); cudaFree(d->u2);
+  cudaFree(d->coef); cudaFree(d->partial);
+  delete d;
+  driver = nullptr;
+}
+
+namespace {
+
+#define DTRY(x) do { kep_status _s = (x); if (_s != KEP_OK) return _s; } while (0)
+#define CTRY(x) do { if ((x) != cudaSuccess) return KEP_ERR_CUDA; } while (0)
+
+struct Run {
+  kep_ctx* c;
+  Driver* d;
+  VecOps ops;
+  int64_t n;
+  double norm_a;
+  kep_report rep{};
+
+  double* col(double* base, int64_t j) { return base + j * n; }
+
+  kep_status sync() { return cudaStreamSynchronize(c->stream) == cudaSuccess ? KEP_OK : KEP_ERR_CUDA; }
+
+  kep_status to_host(double* h, const double* dptr, int64_t cnt) {
+    CTRY(cudaMemcpyAsync(h, dptr, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+    return sync();
+  }
+
+  // out = V(:, 0:ncol)^T w on the host
+  kep_status dots(const double* Vb, int32_t ncol, const double* wv, double* out) {
+    ops.dots(Vb, n, ncol, wv, d->coef);
+    return to_host(out, d->coef, ncol);
+  }
+
+  // w -= Vb(:, 0:ncol) coef (coef from the host)
+  kep_status sub_combine(const double* Vb, int32_t ncol, const double* coef_h, double* wv) {
+    CTRY(cudaMemcpyAsync(d->coef, coef_h, sizeof(double) * ncol, cudaMemcpyHostToDevice, c->stream));
+    ops.combine(Vb, n, ncol, d->coef, -1.0, 1.0, wv);
+    return KEP_OK;
+  }
+
+  // nu(sigma) with slot 0 (a shift exactly at an eigenvalue is nudged upward)
+  kep_status nu_at(double& sigma, int64_t& nu) {
+    for (int attempt = 0; attempt < 8; ++attempt) {
+      kep_inertia in{};
+      kep_status st = ctx_factor(c, 0, 1.0, -sigma, &in);
+      rep.n_factor++;
+      if (st == KEP_OK) { nu = in.neg; return KEP_OK; }
+      if (st != KEP_ERR_SINGULAR) return st;
+      sigma += 8.0 * 2.220446049250313e-16 * std::max(1.0, norm_a) * std::max(1.0, std::fabs(sigma)) * (attempt + 1);
+    }
+    return KEP_ERR_SINGULAR;
+  }
+
+  kep_status factor_B() {
+    kep_inertia in{};
+    kep_status st = ctx_factor(c, 1, 0.0, 1.0, &in);
+    rep.n_factor++;
+    if (st == KEP_ERR_SINGULAR) return KEP_ERR_NOT_SPD;
+    if (st != KEP_OK) return st;
+    if (in.neg != 0 || in.zero != 0) return KEP_ERR_NOT_SPD;
+    return KEP_OK;
+  }
+
+  kep_status solve_B(const double* b, double* x) {
+    if (!c->slot[1].valid) DTRY(factor_B());   // a re-plan of the storage drops both factors
+    return ctx_solve_dev(c, 1, b, x);
+  }
+
+  // B-normalize column j of V (given in V(:, j)), fill BV(:, j); returns the B-norm
+  kep_status b_normalize(int64_t j, double& nrm) {
+    DTRY(ctx_spmv_dev(c, col(d->V, j), nullptr, col(d->BV, j)));
+    double s = 0;
+    DTRY(dots(col(d->V, j), 1, col(d->BV, j), &s));
+    if (!(s > 0)) return KEP_ERR_NOT_SPD;
+    nrm = std::sqrt(s);
+    ops.axpby(0.0, col(d->V, j), 1.0 / nrm, col(d->V, j));
+    ops.axpby(0.0, col(d->BV, j), 1.0 / nrm, col(d->BV, j));
+    return KEP_OK;
+  }
+
+  // full reorthogonalization of w against V(:, 0:ncol) in the B inner product, twice
+  kep_status reorth(int32_t ncol, double* wv, std::vector<double>& tmp) {
+    tmp.resize(ncol);
+    for (int pass = 0; pass < 2; ++pass) {
+      DTRY(dots(d->BV, ncol, wv, tmp.data()));
+      DTRY(sub_combine(d->V, ncol, tmp.data(), wv));
+    }
+    return KEP_OK;
+  }
+};
+
+}  // namespace
+
+extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params* params, double* lambda,
+                                        double* x_out, kep_report* report) {
+  if (!c || !lambda) return KEP_ERR_INVALID;
+  const int64_t n = c->plan.n;
+  if (k < 1 || k > n) return KEP_ERR_INVALID;
+  kep_params prm;
+  if (params) prm = *params; else kep_default_params(&prm);
+  if (prm.m_max < 1 || prm.max_lanczos < 2 || prm.max_si < 1) return KEP_ERR_INVALID;
+  const int64_t cap = std::min<int64_t>(n + 1, std::max(prm.max_lanczos, prm.max_si) + 2);
+  Driver* d = static_cast<Driver*>(c->driver);
+  if (!d || d->cap_cols < cap) {
+    c->driver_release();
+    d = new Driver();
+    c->driver = d;
+    d->cap_cols = cap;
+    d->nblocks = std::max(1, std::min<int>(c->num_sms * 4, static_cast<int>((n + 255) / 256)));
+    if (cudaMalloc(&d->V, sizeof(double) * n * cap) != cudaSuccess ||
+        cudaMalloc(&d->BV, sizeof(double) * n * cap) != cudaSuccess ||
+        cudaMalloc(&d->w, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&d->u, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&d->u2, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&d->coef, sizeof(double) * cap) != cudaSuccess ||
+        cudaMalloc(&d->partial, sizeof(double) * std::max<int64_t>(2, cap) * d->nblocks) != cudaSuccess) {
+      c->driver_release();
+      return KEP_ERR_NOMEM;
+    }
+  }
+  Run R;
+  R.c = c; R.d = d; R.n = n; R.norm_a = c->plan.norm_a_inf;
+  R.ops.n = n; R.ops.num_blocks = d->nblocks; R.ops.partial = d->partial; R.ops.stream = c->stream;
+  R.ops.timer = &c->timer;
+  kep_report& rep = R.rep;
+  std::vector<double> h_start(2 * n), tmp;
+  if (prm.start_vectors) std::memcpy(h_start.data(), prm.start_vectors, sizeof(double) * 2 * n);
+  else { gaussian_vector(prm.seed, n, h_start.data()); gaussian_vector(prm.seed + 1, n, h_start.data() + n); }
+
+  // ---------------- stage 1: Algorithm 2 ----------------
+  auto t0 = clock_::now();
+  DTRY(R.factor_B());
+  CTRY(cudaMemcpyAsync(d->V, h_start.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  double nrm = 0;
+  DTRY(R.b_normalize(0, nrm));                        // v_1 := v_1 / ||v_1||_B
+  std::vector<double> alpha, beta;
+  int64_t nu_prev = 0, nu_cur = 0;                    // nu^(0) := 0
+  double sig_prev = 0, sig_cur = 0;
+  bool bracketed = false;
+  for (int64_t j = 1; j <= prm.max_lanczos && j < cap; ++j) {
+    double* vj = R.col(d->V, j - 1);
+    DTRY(ctx_spmv_dev(c, vj, d->u, nullptr));         // u = A v_j
+    double a = 0;
+    DTRY(R.dots(vj, 1, d->u, &a));                    // alpha_j = v_j^T A v_j
+    DTRY(R.solve_B(d->u, d->w));                      // w = B^{-1} A v_j
+    R.ops.axpby(-a, vj, 1.0, d->w);
+    if (j > 1) R.ops.axpby(-beta.back(), R.col(d->V, j - 2), 1.0, d->w);
+    DTRY(R.reorth(static_cast<int32_t>(j), d->w, tmp));
+    CTRY(cudaMemcpyAsync(R.col(d->V, j), d->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    double b = 0;
+    DTRY(R.b_normalize(j, b));                        // beta_j = ||w||_B, v_{j+1} = w / beta_j
+    alpha.push_back(a);
+    beta.push_back(b);
+    // Ritz values of T_j (Eq. 2.3): the extreme ones are needed
+    const int m = static_cast<int>(j);
+    std::vector<double> wv(m), Z(static_cast<size_t>(m) * m);
+    if (!tridiag_eigen(m, alpha.data(), beta.data(), wv.data(), Z.data())) return KEP_ERR_NOT_CONVERGED;
+    sig_cur = (k <= nu_prev) ? wv[0] : wv[m - 1];
+    DTRY(R.nu_at(sig_cur, nu_cur));
+    rep.n_lanczos = j;
+    if (j != 1 && ((nu_cur < k && k <= nu_prev) || (nu_prev < k && k <= nu_cur))) { bracketed = true; break; }
+    nu_prev = nu_cur;
+    sig_prev = sig_cur;
+  }
+  if (!bracketed) return KEP_ERR_NOT_CONVERGED;
+  double lo = std::min(sig_prev, sig_cur), hi = std::max(sig_prev, sig_cur);
+  int64_t nl = std::min(nu_prev, nu_cur), nh = std::max(nu_prev, nu_cur);
+  rep.init_lo = lo; rep.init_hi = hi; rep.init_nu_lo = nl; rep.init_nu_hi = nh;
+  rep.t_stage[0] = seconds_since(t0);
+
+  // ---------------- stage 2: Algorithm 1' ----------------
+  t0 = clock_::now();
+  while (nh - nl > prm.m_max) {
+    double s = 0.5 * (lo + hi);
+    int64_t nu = 0;
+    DTRY(R.nu_at(s, nu));
+    rep.n_bisect++;
+    if (k <= nu) { hi = s; nh = nu; } else { lo = s; nl = nu; }
+    if (rep.n_bisect > 200) return KEP_ERR_CLUSTER;    // a multiple eigenvalue can stall the count
+  }
+  rep.sigma_lo = lo; rep.sigma_hi = hi; rep.nu_lo = nl; rep.nu_hi = nh;
+  rep.t_stage[1] = seconds_since(t0);
+
+  // ---------------- stage 3: Algorithm 3 ----------------
+  t0 = clock_::now();
+  const int64_t l = k - nl, mm = nh - nl;
+  double sigma = 0.5 * (lo + hi);
+  {
+    int64_t nu_mid = 0;
+    DTRY(R.nu_at(sigma, nu_mid));                     // factor of A - sigma B kept in slot 0
+  }
+  // v_1 = B^{-1} v~_1, so that ||v_1||_B = ||v~_1||_{B^{-1}}
+  CTRY(cudaMemcpyAsync(d->u, h_start.data() + n, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  DTRY(R.solve_B(d->u, d->V));
+  DTRY(R.b_normalize(0, nrm));
+  alpha.clear(); beta.clear();
+  std::vector<double> G;                              // 2-norm Gram matrix of [v_1 .. v_{j+1}]
+  int64_t gcap = cap;
+  G.assign(static_cast<size_t>(gcap) * gcap, 0.0);
+  {
+    double g = 0;
+    DTRY(R.dots(d->V, 1, d->V, &g));
+    G[0] = g;
+  }
+  std::vector<double> prev_c;                         // coefficients of x^{(j-1)}_i, i <= m, in V
+  int64_t prev_j = -1;
+  bool converged = false;
+  std::vector<double> res_lam, res_eta, best_coef;
+  int64_t best_j = 0;
+  for (int64_t j = 1; j <= prm.max_si && j + 1 < cap; ++j) {
+    double* vj = R.col(d->V, j - 1);
+    double* bvj = R.col(d->BV, j - 1);
+    DTRY(ctx_solve_dev(c, 0, bvj, d->w));             // w = (A - sigma B)^{-1} B v_j
+    double a = 0;
+    DTRY(R.dots(bvj, 1, d->w, &a));                   // alpha~_j = (B v_j)^T w
+    R.ops.axpby(-a, vj, 1.0, d->w);
+    if (j > 1) R.ops.axpby(-beta.back(), R.col(d->V, j - 2), 1.0, d->w);
+    DTRY(R.reorth(static_cast<int32_t>(j), d->w, tmp));
+    CTRY(cudaMemcpyAsync(R.col(d->V, j), d->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    double b = 0;
+    DTRY(R.b_normalize(j, b));
+    alpha.push_back(a);
+    beta.push_back(b);
+    {   // new column of the Gram matrix
+      std::vector<double> gc(j + 1);
+      DTRY(R.dots(d->V, static_cast<int32_t>(j + 1), R.col(d->V, j), gc.data()));
+      for (int64_t i = 0; i <= j; ++i) { G[i * gcap + j] = gc[i]; G[j * gcap + i] = gc[i]; }
+    }
+    rep.n_si_iter = j;
+    if (j < mm) continue;
+    const int m = static_cast<int>(j);
+    std::vector<double> th(m), Y(static_cast<size_t>(m) * m);
+    if (!tridiag_eigen(m, alpha.data(), beta.data(), th.data(), Y.data())) return KEP_ERR_NOT_CONVERGED;
+    // order by |theta~| descending (Eq. 3.2)
+    std::vector<int> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int p1, int p2) { return std::fabs(th[p1]) > std::fabs(th[p2]); });
+    const double bj = b;
+    double bnext_2norm = std::sqrt(std::max(0.0, G[j * gcap + j]));   // ||v_{j+1}||_2
+    // ||B v_{j+1}||_2 for the residual identity
+    double bvn = 0;
+    DTRY(R.dots(R.col(d->BV, j), 1, R.col(d->BV, j), &bvn));
+    bvn = std::sqrt(bvn);
+    (void)bnext_2norm;
+    std::vector<double> lam_i(mm), eta_i(mm), rest(mm), coef(static_cast<size_t>(mm) * (j + 1));
+    for (int64_t ii = 0; ii < mm; ++ii) {
+      const int p = ord[ii];
+      const double t = th[p];
+      const double* y = Y.data() + static_cast<size_t>(p) * m;
+      lam_i[ii] = sigma + 1.0 / t;                       // Eq. 2.7
+      const double rho = std::fabs(bj * y[m - 1] / t);
+      eta_i[ii] = (1.0 / std::fabs(t)) * rho / std::sqrt(1.0 + rho * rho);   // Eq. 3.1
+      double* cc = coef.data() + ii * (j + 1);
+      for (int q2 = 0; q2 < m; ++q2) cc[q2] = t * y[q2];   // x_{i,2} = theta V y + v_{j+1} beta (e_j^T y)
+      cc[m] = bj * y[m - 1];
+      double xn2 = 0;                                  // ||x||_2^2 = c^T G c
+      for (int64_t r1 = 0; r1 <= j; ++r1) {
+        double s = 0;
+        for (int64_t r2 = 0; r2 <= j; ++r2) s += G[r1 * gcap + r2] * cc[r2];
+        xn2 += cc[r1] * s;
+      }
+      rest[ii] = bvn * std::fabs(bj * y[m - 1] / t) / std::sqrt(std::max(xn2, 1e-300));   // Eq. 2.12
+    }
+    // inclusion (3.3) and disjointness (3.4)
+    bool ok = true;
+    for (int64_t ii = 0; ii < mm; ++ii)
+      if (!(lam_i[ii] - eta_i[ii] >= lo && lam_i[ii] + eta_i[ii] < hi)) ok = false;
+    std::vector<int> s_ord(mm);
+    std::iota(s_ord.begin(), s_ord.end(), 0);
+    std::sort(s_ord.begin(), s_ord.end(), [&](int p1, int p2) { return lam_i[p1] < lam_i[p2]; });
+    for (int64_t ii = 0; ii + 1 < mm; ++ii)
+      if (!(lam_i[s_ord[ii]] + eta_i[s_ord[ii]] < lam_i[s_ord[ii + 1]] - eta_i[s_ord[ii + 1]])) ok = false;
+    if (ok && rep.si_iter_bound == 0) rep.si_iter_bound = j;
+    for (int64_t ii = 0; ii < mm; ++ii) if (!(rest[ii] < prm.tau_res)) ok = false;
+    // relative difference (Eq. 3.5) between iterations j-1 and j, through the Gram matrix
+    bool diff_ok = prev_j == j - 1;
+    if (diff_ok) {
+      for (int64_t ii = 0; ii < mm && diff_ok; ++ii) {
+        const double* cn = coef.data() + ii * (j + 1);
+        const double* co = prev_c.data() + ii * j;    // length j (basis v_1..v_j)
+        std::vector<double> cpad(j + 1, 0.0), dv(j + 1);
+        for (int64_t r = 0; r < j; ++r) cpad[r] = co[r];
+        auto gram = [&](const double* u1, const double* u2) {
+          double acc = 0;
+          for (int64_t r1 = 0; r1 <= j; ++r1) {
+            double s2 = 0;
+            for (int64_t r2 = 0; r2 <= j; ++r2) s2 += G[r1 * gcap + r2] * u2[r2];
+            acc += u1[r1] * s2;
+          }
+          return acc;
+        };
+        const double nn = gram(cn, cn), no = gram(cpad.data(), cpad.data()), dot = gram(cn, cpad.data());
+        // scale x^{(j)} to the 2-norm of x^{(j-1)} with the sign that aligns them, then subtract
+        // in coefficient space (no cancellation between large norms)
+        const double s = (dot >= 0 ? 1.0 : -1.0) * std::sqrt(no / std::max(nn, 1e-300));
+        for (int64_t r = 0; r <= j; ++r) dv[r] = s * cn[r] - cpad[r];
+        const double dn2 = gram(dv.data(), dv.data());
+        if (!(std::sqrt(std::max(dn2, 0.0)) / std::sqrt(std::max(no, 1e-300)) < prm.tau_diff)) diff_ok = false;
+      }
+    }
+    prev_c.assign(static_cast<size_t>(mm) * (j + 1), 0.0);
+    for (int64_t ii = 0; ii < mm; ++ii)
+      for (int64_t r = 0; r <= j; ++r) prev_c[ii * (j + 1) + r] = coef[ii * (j + 1) + r];
+    // prev_c is read next iteration with stride j+1 == (next j)
+    prev_j = j;
+    if (!(ok && diff_ok)) continue;
+    // confirm the residuals explicitly: ||(A - lambda B) x||_2 / ||x||_2 < tau_res for i <= m
+    bool explicit_ok = true;
+    for (int64_t ii = 0; ii < mm && explicit_ok; ++ii) {
+      CTRY(cudaMemcpyAsync(d->coef, coef.data() + ii * (j + 1), sizeof(double) * (j + 1), cudaMemcpyHostToDevice,
+                           c->stream));
+      R.ops.combine(d->V, n, static_cast<int32_t>(j + 1), d->coef, 1.0, 0.0, d->w);
+      DTRY(ctx_spmv_dev(c, d->w, d->u, d->u2));
+      R.ops.resid_partials(d->u, d->u2, lam_i[ii], d->w);
+      std::vector<double> part(2 * d->nblocks);
+      DTRY(R.to_host(part.data(), d->partial, 2 * d->nblocks));
+      double rr = 0, xx = 0;
+      for (int bb = 0; bb < d->nblocks; ++bb) { rr += part[2 * bb]; xx += part[2 * bb + 1]; }
+      const double rel = std::sqrt(rr) / std::sqrt(std::max(xx, 1e-300));
+      if (!(rel < prm.tau_res)) explicit_ok = false;
+    }
+    if (!explicit_ok) continue;
+    converged = true;
+    // sort the interval's pairs increasingly and take the l-th (Algorithm 3, last two lines)
+    const int64_t pick = s_ord[l - 1];
+    best_coef.assign(coef.begin() + pick * (j + 1), coef.begin() + (pick + 1) * (j + 1));
+    best_j = j;
+    res_lam = lam_i; res_eta = eta_i;
+    rep.lambda = lam_i[pick];
+    rep.eta = eta_i[pick];
+    break;
+  }
+  if (!converged) return KEP_ERR_CLUSTER;
+  // x_k = V c, B-normalized; explicit residuals for the report
+  CTRY(cudaMemcpyAsync(d->coef, best_coef.data(), sizeof(double) * (best_j + 1), cudaMemcpyHostToDevice, c->stream));
+  R.ops.combine(d->V, n, static_cast<int32_t>(best_j + 1), d->coef, 1.0, 0.0, d->w);
+  DTRY(ctx_spmv_dev(c, d->w, d->u, d->u2));
+  double xbx = 0;
+  DTRY(R.dots(d->w, 1, d->u2, &xbx));
+  const double xs = 1.0 / std::sqrt(xbx);
+  R.ops.axpby(0.0, d->w, xs, d->w);
+  R.ops.axpby(0.0, d->u, xs, d->u);
+  R.ops.axpby(0.0, d->u2, xs, d->u2);
+  R.ops.resid_partials(d->u, d->u2, rep.lambda, d->w);
+  {
+    std::vector<double> part(2 * d->nblocks);
+    DTRY(R.to_host(part.data(), d->partial, 2 * d->nblocks));
+    double rr = 0, xx = 0;
+    for (int bb = 0; bb < d->nblocks; ++bb) { rr += part[2 * bb]; xx += part[2 * bb + 1]; }
+    rep.rel_res = std::sqrt(rr) / std::sqrt(xx);
+    rep.rel_res_normwise = rep.rel_res / std::max(R.norm_a, 1e-300);
+  }
+  if (x_out) DTRY(R.to_host(x_out, d->w, n));
+  rep.t_stage[2] = seconds_since(t0);
+  *lambda = rep.lambda;
+  if (report) *report = rep;
+  return KEP_OK;
 }

@@ -1,0 +1,90 @@
+"""GPU parity of Algorithm 4 (kep_kth_eigenpair) against the oracle.
+
+The random start vectors of Algorithms 2 and 3 are inputs: both sides get the same ones.
+lambda_k must agree with the oracle's dense generalized eigensolver within 1e-10 * ||A||_inf
+(the tolerance the method's validation targets), the eigenvector within 1e-8 after B-normalization
+and sign alignment, the relative residual must be below tau_res, and the intervals of Algorithms 2
+and 1' must carry the same exact inertia counts as the oracle's run."""
+import numpy as np
+import pytest
+
+from gen import make_pair, workload
+from oracle import core, three_stage as ts
+from tests.gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kep():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def small():
+    p = workload("small")
+    A, B = p.A().toarray(), p.B().toarray()
+    lam, X = core.gen_eig(A, B)
+    return p, A, B, lam, X
+
+
+def _check_pair(p, A, B, lam, X, k, lam_gpu, x_gpu, rep):
+    nrm = np.abs(A).sum(1).max()
+    assert abs(lam_gpu - lam[k - 1]) <= 1e-10 * nrm
+    assert abs(x_gpu @ B @ x_gpu - 1.0) < 1e-10
+    xd = X[:, k - 1]
+    x = x_gpu * np.sign(x_gpu @ B @ xd)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
+    r = np.linalg.norm(A @ x_gpu - lam_gpu * (B @ x_gpu)) / np.linalg.norm(x_gpu)
+    assert r < 1e-10 and rep["rel_res"] < 1e-10
+    assert rep["nu_lo"] < k <= rep["nu_hi"] and rep["nu_hi"] - rep["nu_lo"] <= 20
+    assert rep["init_nu_lo"] < k <= rep["init_nu_hi"]
+    assert rep["nu_lo"] == core.count_below(lam, rep["sigma_lo"])
+    assert rep["nu_hi"] == core.count_below(lam, rep["sigma_hi"])
+
+
+def test_kth_eigenpair_matches_oracle(kep, small):
+    p, A, B, lam, X = small
+    k = p.k
+    rng = np.random.default_rng(5)
+    v1, vt1 = rng.normal(size=p.n), rng.normal(size=p.n)
+    P = kep.Problem.from_pencil(p)
+    lam_g, x_g, rep = P.kth_eigenpair(k, start_vectors=np.concatenate([v1, vt1]))
+    _check_pair(p, A, B, lam, X, k, lam_g, x_g, rep)
+    # the oracle's Algorithm 4 from the same start vectors: same intervals and counts
+    r = ts.three_stage(ts.DenseOps(A, B), k, v1, vt1)
+    assert (rep["init_nu_lo"], rep["init_nu_hi"]) == (r.initial.nu_lower, r.initial.nu_upper)
+    assert abs(rep["init_lo"] - r.initial.lower) <= 1e-9 * abs(r.initial.lower)
+    assert abs(rep["init_hi"] - r.initial.upper) <= 1e-9 * abs(r.initial.upper)
+    assert (rep["nu_lo"], rep["nu_hi"]) == (r.narrowed.nu_lower, r.narrowed.nu_upper)
+    assert rep["n_lanczos"] == len(r.initial.history)
+    assert rep["n_bisect"] == len(r.narrowed.history)
+    nrm = np.abs(A).sum(1).max()
+    assert abs(lam_g - r.lam) <= 1e-10 * nrm
+    assert abs(rep["n_si_iter"] - r.kth.iterations) <= 3
+
+
+@pytest.mark.parametrize("frac", [0.05, 0.3, 0.8])
+def test_kth_eigenpair_other_indices(kep, small, frac):
+    p, A, B, lam, X = small
+    k = max(2, int(frac * p.n))
+    P = kep.Problem.from_pencil(p)
+    lam_g, x_g, rep = P.kth_eigenpair(k, seed=k)
+    _check_pair(p, A, B, lam, X, k, lam_g, x_g, rep)
+
+
+def test_kth_eigenpair_vacancy_pencil(kep):
+    p = make_pair(3, 3, 3, seed=2, vacancies=20)      # irregular spectrum
+    A, B = p.A().toarray(), p.B().toarray()
+    lam, X = core.gen_eig(A, B)
+    P = kep.Problem.from_pencil(p)
+    lam_g, x_g, rep = P.kth_eigenpair(p.k)
+    _check_pair(p, A, B, lam, X, p.k, lam_g, x_g, rep)
+
+
+def test_not_spd_B_rejected(kep):
+    p = make_pair(2, 2, 2, seed=1)
+    P = kep.Problem(p.n, p.rowptr, p.colind, p.a, p.a, p.coords)   # "B" = A is indefinite
+    with pytest.raises(kep.KepError) as e:
+        P.kth_eigenpair(p.k)
+    assert e.value.code == kep.KEP_ERR_NOT_SPD
