@@ -201,6 +201,29 @@ kep_status kep_set_timing(kep_ctx* ctx, int enable);
 /* Copy the counters into *out; reset (1) zeroes them afterwards.  Synchronises ctx's stream. */
 kep_status kep_get_timing(kep_ctx* ctx, kep_timing* out, int reset);
 
+/*
+ * kep_dense_inertia_noalloc - inertia (neg, zero, pos) of the dense symmetric matrix a - sigma*b,
+ * for callers that must not allocate device memory at the point of the call (a framework that
+ * owns all device memory through its own pool, a real-time loop that cannot afford cudaMalloc's
+ * synchronisation or failure).  The paper has no counterpart: it is a convenience form of the
+ * front elimination (Bunch-Kaufman, alpha = (1+sqrt 17)/8) for one small dense pencil, outside the
+ * sparse path.
+ *
+ * n        order, 1 <= n <= 512 (larger n returns KEP_ERR_INVALID).
+ * a, b     device pointers, column-major n x n with leading dimension lda >= n; only the lower
+ *          triangles are read; caller-owned, not modified.
+ * sigma    the shift.
+ * stream   cudaStream_t to run on (NULL: legacy default stream); the call synchronises it.
+ * out      host array of 3 int64: neg, zero, pos.
+ * The working copy lives in a fixed 2 MiB device array reserved by the library on every GPU that
+ * loads it, for the life of the process; no allocator is called.  The first call on each device
+ * looks up that array's device address, so make the first call on a device before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race and must be serialised
+ * by the caller.  Errors: KEP_ERR_INVALID (bad argument or n > 512), KEP_ERR_CUDA.
+ */
+kep_status kep_dense_inertia_noalloc(int64_t n, const double* a, const double* b, int64_t lda,
+                                     double sigma, void* stream, int64_t* out);
+
 /* Release every resource of ctx (NULL is accepted). */
 void kep_destroy(kep_ctx* ctx);
 

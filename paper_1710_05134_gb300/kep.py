@@ -23,7 +23,7 @@ KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 # symbols declared in include/kep.h
 EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
-            "kep_get_timing", "kep_destroy", "kep_status_str"]
+            "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc"]
 KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
                   "perm", "spmv", "vec"]
 
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(Report)]
         L.kep_set_timing.argtypes = [P, I]
         L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
+        L.kep_dense_inertia_noalloc.argtypes = [I64, P, P, I64, D, P, P]
+        L.kep_dense_inertia_noalloc.restype = I
         L.kep_destroy.argtypes = [P]
         L.kep_destroy.restype = None
         L.kep_status_str.argtypes = [I]
