@@ -451,20 +451,23 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
   for (int32_t l = 0; l < P.nlevels; ++l) P.level_ptr[l + 1] += P.level_ptr[l];
   P.level_fronts.resize(nt);
   P.level_nsmall.assign(P.nlevels, 0);
+  P.level_nbig_solve.assign(P.nlevels, 0);
   {
-    std::vector<std::vector<int32_t>> small(P.nlevels), large(P.nlevels);
-    for (int32_t t = 0; t < nt; ++t)
-      (P.m_alloc[t] <= kSmallMax ? small : large)[P.height[t]].push_back(t);
+    // every level's fronts in decreasing order: the largest ones (factored alone, solved by the
+    // multi-block path) lead, the rest form one batch
+    std::vector<std::vector<int32_t>> lv(P.nlevels);
+    for (int32_t t = 0; t < nt; ++t) lv[P.height[t]].push_back(t);
     for (int32_t l = 0; l < P.nlevels; ++l) {
-      // small fronts in decreasing size (larger shared-memory blocks launch first)
-      std::stable_sort(small[l].begin(), small[l].end(),
-                       [&](int32_t a, int32_t b) { return P.m_alloc[a] > P.m_alloc[b]; });
-      std::stable_sort(large[l].begin(), large[l].end(),
-                       [&](int32_t a, int32_t b) { return P.m_alloc[a] > P.m_alloc[b]; });
+      std::stable_sort(lv[l].begin(), lv[l].end(),
+                       [&](int32_t a, int32_t b) { return P.m_sym[a] > P.m_sym[b]; });
       int64_t o = P.level_ptr[l];
-      for (int32_t t : small[l]) P.level_fronts[o++] = t;
-      for (int32_t t : large[l]) P.level_fronts[o++] = t;
-      P.level_nsmall[l] = static_cast<int32_t>(small[l].size());
+      for (int32_t t : lv[l]) {
+        P.level_fronts[o++] = t;
+        if (P.m_sym[t] <= kSmallMax) P.level_nsmall[l]++;
+        if (P.m_sym[t] >= kSolveBigM && P.p_sym[t] >= kSolveBigP &&
+            P.level_nbig_solve[l] == static_cast<int32_t>(o - 1 - P.level_ptr[l]))
+          P.level_nbig_solve[l]++;
+      }
       P.max_level_width = std::max<int32_t>(P.max_level_width, P.level_ptr[l + 1] - P.level_ptr[l]);
     }
   }

@@ -139,6 +139,10 @@ kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inert
   if (st != KEP_OK) return st;
   S.ca = ca; S.cb = cb;
   c->slot_status[slot] = bits;
+  c->slot_nelim[slot].resize(c->plan.nfronts);
+  if (cudaMemcpy(c->slot_nelim[slot].data(), S.nelim, sizeof(int32_t) * c->plan.nfronts,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return KEP_ERR_CUDA;
   if (out) *out = in;
   if (bits & ST_POOL) return KEP_ERR_POOL;
   if (bits & ST_NONFINITE) return KEP_ERR_NONFINITE;
@@ -163,6 +167,8 @@ kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x) {
   L.vfac = c->d_vfac;
   L.bnew = c->d_bnew;
   L.xnew = c->d_xnew;
+  L.partial = c->d_solve_partial;
+  L.h_nelim = c->slot_nelim[slot].data();
   L.stream = c->stream;
   L.num_sms = c->num_sms;
   L.timer = &c->timer;
@@ -302,6 +308,7 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   AL(c->d_cbpool, P.cb_total);
   AL(c->d_red, 8);
   AL(c->d_bnew, P.n); AL(c->d_xnew, P.n);
+  AL(c->d_solve_partial, static_cast<size_t>(c->num_sms) * 4 * (kSolveBlk + 1));
   AL(c->d_io0, P.n); AL(c->d_io1, P.n); AL(c->d_io2, P.n);
 #undef AL
   st = setup_memory(c);

@@ -42,6 +42,8 @@ struct kep_ctx {
   double* d_io0 = nullptr;
   double* d_io1 = nullptr;
   double* d_io2 = nullptr;
+  double* d_solve_partial = nullptr;
+  std::vector<int32_t> slot_nelim[2];   // pivots eliminated per front, per slot (host copy)
   kep::Timer timer;
   // eigenpair driver state (owned by driver.cu)
   void* driver = nullptr;

@@ -16,6 +16,9 @@ namespace kep {
 // ---------------------------------------------------------------------------------------------
 constexpr int kSmallMax = 128;      // fronts with m_alloc <= this are factored in shared memory
 constexpr int kPanel = 32;          // block width of the large-front pivoting panel
+constexpr int kSolveBigM = 2048;    // fronts at least this large (and with kSolveBigP pivots) are
+constexpr int kSolveBigP = 128;     //   solved by the multi-block path
+constexpr int kSolveBlk = 64;       // pivot block of the multi-block solve
 constexpr double kBKAlpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
 constexpr double kThresholdU = 0.01;               // threshold pivoting parameter u
 
@@ -104,6 +107,7 @@ struct Plan {
   int32_t nlevels = 0;
   std::vector<int32_t> level_ptr, level_fronts;   // fronts of each level, small ones first
   std::vector<int32_t> level_nsmall;              // count of small fronts per level
+  std::vector<int32_t> level_nbig_solve;          // leading fronts of each level solved per block
   // memory plan.  Each front has persistent L storage (m_alloc x p_alloc, column-major,
   // ld = m_alloc: the fully-summed columns, later L and D) and a transient contribution block
   // (c x c, c = m_sym - p_sym, column-major) in a pool that lives from the front's factorization
@@ -233,6 +237,8 @@ struct SolveLaunch {
   double* vfac;
   double* bnew;
   double* xnew;
+  double* partial;            // num_sms * 4 * (kSolveBlk + 1) doubles
+  const int32_t* h_nelim;     // pivots eliminated per front (host copy of the factor's counts)
   cudaStream_t stream;
   int num_sms;
   Timer* timer;

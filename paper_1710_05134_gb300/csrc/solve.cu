@@ -8,6 +8,8 @@
 // its contribution rows is passed to the parent.  Backward pass, root to leaves: each front
 // reads the solution on its contribution rows (written by its ancestors), applies D^{-1} and
 // L^{-T}, and writes its own variables.  No atomics: the result does not depend on scheduling.
+#include <algorithm>
+
 #include "kep_device.cuh"
 
 namespace kep {
@@ -172,6 +174,200 @@ __global__ void __launch_bounds__(kSolveThreads) sv_bwd_kernel(FrontTables T, Fa
   for (int32_t c = threadIdx.x; c < nel; c += blockDim.x) xnew[rv[c]] = vf[c];
 }
 
+// ------------------------------------------------------------------------------------------
+// multi-block path for the largest fronts: the pivot range is cut into blocks of kSolveBlk
+// (boundaries moved by one where they would split a 2x2 pair); every block is one launch whose
+// CTAs all reproduce the small diagonal-block solve and then update their own rows.
+// ------------------------------------------------------------------------------------------
+KEP_D int32_t blk_start(const int8_t* piv, int32_t b, int32_t nel) {
+  if (b <= 0) return 0;
+  int32_t s = b * kSolveBlk;
+  if (s >= nel) return nel;
+  return piv[s] == 0 ? s + 1 : s;
+}
+
+// assembly of the front's right-hand side (children in order) and the pivot permutation
+__global__ void __launch_bounds__(1024) sv_big_prep_kernel(FrontTables T, FactorSlot S, int32_t t,
+                                                           const double* bnew, double* vasm, double* vfac) {
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in;
+  const int32_t psym = T.p_sym[t];
+  double* va = vasm + T.vec_off[t];
+  double* vf = vfac + T.vec_off[t];
+  const int32_t* ap = S.apos + T.vec_off[t];
+  const int32_t first = T.first[t];
+  for (int32_t i = threadIdx.x; i < m; i += blockDim.x)
+    va[i] = (i >= d_in && i < d_in + psym) ? bnew[first + i - d_in] : 0.0;
+  __syncthreads();
+  int32_t off = 0;
+  for (int32_t c = T.child_ptr[t]; c < T.child_ptr[t + 1]; ++c) {
+    const int32_t ch = T.child_idx[c];
+    const int32_t dout = S.d_out[ch], nelc = S.nelim[ch];
+    const int32_t nc = dout + (T.m_sym[ch] - T.p_sym[ch]);
+    const double* vc = vfac + T.vec_off[ch] + nelc;
+    for (int32_t q = threadIdx.x; q < nc; q += blockDim.x)
+      va[parent_pos(T, ch, q, dout, off, d_in)] += vc[q];
+    off += dout;
+    __syncthreads();
+  }
+  for (int32_t i = threadIdx.x; i < m; i += blockDim.x) vf[i] = va[ap[i]];
+}
+
+// forward block b: y(block) = L11^{-1} f(block) (every CTA), CTA 0 stores it in ysol; rows below
+// the block: f(a) -= L(a, block) y(block)
+__global__ void __launch_bounds__(256) sv_big_fwd_kernel(FrontTables T, FactorSlot S, int32_t t, int32_t b,
+                                                         double* vfac, double* ysol) {
+  __shared__ double y[kSolveBlk + 1];
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in;
+  const int32_t nel = S.nelim[t];
+  const int8_t* piv = S.piv + T.piv_off[t];
+  const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
+  if (k0 >= k1) return;
+  const double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  double* vf = vfac + T.vec_off[t];
+  double* ys = ysol + T.vec_off[t];
+  const int32_t kb = k1 - k0;
+  if (threadIdx.x < kb) y[threadIdx.x] = vf[k0 + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int32_t c = 0; c < kb;) {
+      if (piv[k0 + c] == 2) {
+        const double y0 = y[c], y1 = y[c + 1];
+        for (int32_t a = c + 2 + lane; a < kb; a += 32)
+          y[a] -= L[static_cast<int64_t>(k0 + c) * ld + k0 + a] * y0 + L[static_cast<int64_t>(k0 + c + 1) * ld + k0 + a] * y1;
+        c += 2;
+      } else {
+        const double y0 = y[c];
+        for (int32_t a = c + 1 + lane; a < kb; a += 32) y[a] -= L[static_cast<int64_t>(k0 + c) * ld + k0 + a] * y0;
+        c += 1;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x < kb) ys[k0 + threadIdx.x] = y[threadIdx.x];
+  for (int32_t a = k1 + blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int32_t c = 0; c < kb; ++c) s = fma(L[static_cast<int64_t>(k0 + c) * ld + a], y[c], s);
+    vf[a] -= s;
+  }
+}
+
+// backward preparation: solution on the contribution rows, z = D^{-1} y on the pivots
+__global__ void sv_big_bwd_prep_kernel(FrontTables T, FactorSlot S, int32_t t, const double* xnew,
+                                       const double* ysol, double* vfac) {
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in;
+  const int32_t nel = S.nelim[t];
+  double* vf = vfac + T.vec_off[t];
+  const double* ys = ysol + T.vec_off[t];
+  const int32_t* rv = S.rowvar + T.vec_off[t];
+  const int8_t* piv = S.piv + T.piv_off[t];
+  const double* Dd = S.Dd + T.piv_off[t];
+  const double* De = S.De + T.piv_off[t];
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    if (i >= nel) { vf[i] = xnew[rv[i]]; continue; }
+    if (piv[i] == 1) {
+      vf[i] = ys[i] / Dd[i];
+    } else if (piv[i] == 2) {
+      const double a = Dd[i], cc = Dd[i + 1], bb = De[i];
+      const double det = a * cc - bb * bb;
+      vf[i] = (cc * ys[i] - bb * ys[i + 1]) / det;
+    } else {
+      const double a = Dd[i - 1], cc = Dd[i], bb = De[i - 1];
+      const double det = a * cc - bb * bb;
+      vf[i] = (a * ys[i] - bb * ys[i - 1]) / det;
+    }
+  }
+}
+
+// backward block b, part 1: per-CTA partial sums s_c = sum_{a >= k1} L(a, k0 + c) x(a); warp w owns
+// columns w, w + 8, ..., its lanes stride the CTA's rows
+__global__ void __launch_bounds__(256) sv_big_bwd_partial_kernel(FrontTables T, FactorSlot S, int32_t t,
+                                                                 int32_t b, const double* vfac, double* partial) {
+  constexpr int kCols = (kSolveBlk + 1 + 7) / 8;
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in;
+  const int32_t nel = S.nelim[t];
+  const int8_t* piv = S.piv + T.piv_off[t];
+  const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
+  const int32_t kb = k1 - k0;
+  const double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  const double* vf = vfac + T.vec_off[t];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  double acc[kCols];
+#pragma unroll
+  for (int j = 0; j < kCols; ++j) acc[j] = 0.0;
+  for (int32_t a = k1 + blockIdx.x * 32 + lane; a < m; a += gridDim.x * 32) {
+    const double xa = vf[a];
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) {
+      const int32_t c = warp + 8 * j;
+      if (c < kb) acc[j] = fma(L[static_cast<int64_t>(k0 + c) * ld + a], xa, acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kCols; ++j) {
+    const int32_t c = warp + 8 * j;
+    const double v = warp_sum(acc[j]);
+    if (lane == 0 && c < kb) partial[static_cast<int64_t>(blockIdx.x) * (kSolveBlk + 1) + c] = v;
+  }
+}
+
+// backward block b, part 2 (one CTA): add the partials, solve the block's unit upper triangle
+__global__ void __launch_bounds__(128) sv_big_bwd_block_kernel(FrontTables T, FactorSlot S, int32_t t, int32_t b,
+                                                               int32_t nparts, const double* partial, double* vfac) {
+  __shared__ double part[kSolveBlk + 1];
+  const int32_t d_in = S.d_in[t];
+  (void)d_in;
+  const int32_t nel = S.nelim[t];
+  const int8_t* piv = S.piv + T.piv_off[t];
+  const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
+  const int32_t kb = k1 - k0;
+  const double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  double* vf = vfac + T.vec_off[t];
+  if (threadIdx.x < kb) {
+    double s = 0.0;
+    for (int32_t q = 0; q < nparts; ++q) s += partial[static_cast<int64_t>(q) * (kSolveBlk + 1) + threadIdx.x];
+    part[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int32_t c = k1 - 1; c >= k0;) {
+      if (piv[c] == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int32_t a = c + 1 + lane; a < k1; a += 32) {
+          s0 += L[static_cast<int64_t>(c - 1) * ld + a] * vf[a];
+          s1 += L[static_cast<int64_t>(c) * ld + a] * vf[a];
+        }
+        s0 = warp_sum(s0); s1 = warp_sum(s1);
+        if (lane == 0) { vf[c] -= part[c - k0] + s1; vf[c - 1] -= part[c - 1 - k0] + s0; }
+        c -= 2;
+      } else {
+        double s0 = 0.0;
+        for (int32_t a = c + 1 + lane; a < k1; a += 32) s0 += L[static_cast<int64_t>(c) * ld + a] * vf[a];
+        s0 = warp_sum(s0);
+        if (lane == 0) vf[c] -= part[c - k0] + s0;
+        c -= 1;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void sv_big_scatter_kernel(FrontTables T, FactorSlot S, int32_t t, const double* vfac, double* xnew) {
+  const int32_t nel = S.nelim[t];
+  const double* vf = vfac + T.vec_off[t];
+  const int32_t* rv = S.rowvar + T.vec_off[t];
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nel; c += gridDim.x * blockDim.x) xnew[rv[c]] = vf[c];
+}
+
 __global__ void gather_perm_kernel(int64_t n, const int32_t* perm, const double* src, double* dst) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -195,16 +391,42 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   const int g = L.num_sms * 4;
   KEP_LAUNCH(L.timer, KC_PERM, st, gather_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, b, L.bnew));
   for (int32_t l = 0; l < P.nlevels; ++l) {
-    const int32_t w = P.level_ptr[l + 1] - P.level_ptr[l];
-    KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st,
-               sv_fwd_kernel<<<w, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + P.level_ptr[l], L.bnew,
-                                                          L.vasm, L.vfac));
+    const int32_t lb = P.level_ptr[l], w = P.level_ptr[l + 1] - lb, nbig = P.level_nbig_solve[l];
+    for (int32_t i = 0; i < nbig; ++i) {
+      const int32_t t = P.level_fronts[lb + i];
+      const int32_t nel = L.h_nelim[t];
+      KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st, sv_big_prep_kernel<<<1, 1024, 0, st>>>(L.T, L.S, t, L.bnew, L.vasm, L.vfac));
+      const int32_t rows = P.m_alloc[t];
+      const int grid = static_cast<int>(std::min<int64_t>(g, (rows + 255) / 256 + 1));
+      for (int32_t bb = 0; bb * kSolveBlk < nel; ++bb)
+        KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st, sv_big_fwd_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, bb, L.vfac, L.vasm));
+    }
+    if (w > nbig)
+      KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st,
+                 sv_fwd_kernel<<<w - nbig, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + lb + nbig, L.bnew,
+                                                                   L.vasm, L.vfac));
   }
   for (int32_t l = P.nlevels - 1; l >= 0; --l) {
-    const int32_t w = P.level_ptr[l + 1] - P.level_ptr[l];
-    KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
-               sv_bwd_kernel<<<w, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + P.level_ptr[l], L.xnew,
-                                                          L.vfac));
+    const int32_t lb = P.level_ptr[l], w = P.level_ptr[l + 1] - lb, nbig = P.level_nbig_solve[l];
+    for (int32_t i = 0; i < nbig; ++i) {
+      const int32_t t = P.level_fronts[lb + i];
+      const int32_t nel = L.h_nelim[t];
+      const int32_t rows = P.m_alloc[t];
+      const int grid = static_cast<int>(std::min<int64_t>(g, (rows + 255) / 256 + 1));
+      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st, sv_big_bwd_prep_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, L.xnew, L.vasm, L.vfac));
+      const int32_t nblk = (nel + kSolveBlk - 1) / kSolveBlk;
+      for (int32_t bb = nblk - 1; bb >= 0; --bb) {
+        KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
+                   sv_big_bwd_partial_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, bb, L.vfac, L.partial));
+        KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
+                   sv_big_bwd_block_kernel<<<1, 128, 0, st>>>(L.T, L.S, t, bb, grid, L.partial, L.vfac));
+      }
+      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st, sv_big_scatter_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, L.vfac, L.xnew));
+    }
+    if (w > nbig)
+      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
+                 sv_bwd_kernel<<<w - nbig, kSolveThreads, 0, st>>>(L.T, L.S, L.d_level_fronts + lb + nbig, L.xnew,
+                                                                   L.vfac));
   }
   KEP_LAUNCH(L.timer, KC_PERM, st, scatter_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, L.xnew, x));
   return cudaGetLastError() == cudaSuccess ? KEP_OK : KEP_ERR_CUDA;

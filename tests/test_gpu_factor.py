@@ -200,3 +200,21 @@ def test_timing_counters(kep, small):
     t = P.timing(reset=True)
     assert t["update"][0] > 0 and t["update"][1] > 0
     assert t["total_launches"] == sum(v[0] for k, v in t.items() if k != "total_launches")
+
+
+def test_solve_multiblock_fronts_vs_sparse_lu(kep):
+    """Fronts of order >= 2048 take the multi-block solve; compare with the oracle's sparse LU."""
+    p = make_pair(8, 8, 8, seed=3)            # n = 16384, largest front > 2048
+    P = kep.Problem.from_pencil(p)
+    assert P.info.max_front >= 2048
+    s = 0.37
+    r = P.factor(s)
+    assert r.status == 0
+    ops = ts.SparseOps(p)
+    rng = np.random.default_rng(4)
+    b = rng.normal(size=p.n)
+    x = P.solve(b)
+    xr = ops.shifted_solver(s)(b)
+    assert np.abs(x - xr).max() <= 1e-9 * np.abs(xr).max()
+    M = (p.A() - s * p.B()).tocsr()
+    assert np.linalg.norm(M @ x - b) <= 1e-13 * abs(M).sum(1).max() * np.linalg.norm(x)
