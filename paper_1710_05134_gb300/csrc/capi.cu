@@ -303,6 +303,7 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   W.list = nullptr;
 #define AL(dst, count) do { st = dev_alloc(c, &dst, count); if (st != KEP_OK) { kep_destroy(c); return st; } } while (0)
   AL(W.k, ent); AL(W.w, ent); AL(W.q, ent); AL(W.fails, ent); AL(W.swap, ent); AL(W.done, ent);
+  AL(W.ws, ent); AL(W.we, ent); AL(W.kend, ent); AL(W.flush, ent); AL(W.reset, ent); AL(W.finish, ent);
   AL(W.L11, ent * kPanel * kPanel); AL(W.Dblk, ent * 2 * kPanel); AL(W.pi, ent * kPanel);
   AL(W.pt, ent * kPanel); AL(W.colmax, ent * kPanel);
   AL(c->d_cbpool, P.cb_total);

@@ -58,6 +58,7 @@ __global__ void lf_init_kernel(FrontTables T, FactorSlot S, double* cbpool, Larg
     S.d_out[t] = 0;
     S.cnt[3 * t] = S.cnt[3 * t + 1] = S.cnt[3 * t + 2] = 0;
     W.k[b] = 0; W.q[b] = 0; W.w[b] = 0; W.fails[b] = 0; W.swap[b] = 0; W.done[b] = bad ? 1 : 0;
+    W.ws[b] = 0; W.we[b] = 0; W.kend[b] = 0; W.flush[b] = 0; W.reset[b] = 1; W.finish[b] = 0;
     if (bad) {
       atomicOr(&S.status[0], ST_POOL);
       atomicCAS(&S.status[1], -1, t);
@@ -145,13 +146,18 @@ __global__ void __launch_bounds__(32) lf_panel_kernel(FrontTables T, FactorSlot 
   const int32_t d_in = S.d_in[t];
   const int32_t p = T.p_sym[t] + d_in;
   const int32_t k = W.k[b] + W.q[b];
+  int32_t we = W.we[b];
+  if (k < p && (k >= we || W.reset[b])) we = min(k + kWindow, p);   // open a new pivot window
   __syncwarp();
-  if (lane == 0) { W.k[b] = k; W.q[b] = 0; }
+  if (lane == 0) {
+    W.k[b] = k; W.q[b] = 0; W.flush[b] = 0;
+    if (k < p && (k >= W.we[b] || W.reset[b])) { W.ws[b] = k; W.we[b] = we; W.reset[b] = 0; }
+  }
   if (k >= p) {
     if (lane == 0) { W.done[b] = 1; S.nelim[t] = k; S.d_out[t] = p - k; W.w[b] = 0; }
     return;
   }
-  const int32_t w = min(kPanel, p - k);
+  const int32_t w = min(kPanel, we - k);
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
   for (int32_t c = 0; c < w; ++c) {
@@ -385,12 +391,17 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
     // the block's first pivot fails the threshold: move that pivot's column(s) to the end of the
     // fully-summed range and retry with the others; once every remaining column has failed in
     // turn without progress, the remaining columns go to the parent (delayed pivots)
+    // (the window's accepted pivots are first applied to everything right of the window, so the
+    // column swapped in from the end of the range is up to date)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       const int32_t nf = W.pt[b * kPanel] == 2 ? 2 : 1;
       const int32_t f = W.fails[b] + 1;
       W.fails[b] = f;
+      W.kend[b] = k;
+      W.flush[b] = k > W.ws[b] ? 1 : 0;
+      W.reset[b] = 1;
       if (f > p - k || p - k <= nf) {
-        W.done[b] = 1;
+        W.finish[b] = 1;
         S.nelim[t] = k;
         S.d_out[t] = p - k;
         W.swap[b] = 0;
@@ -465,6 +476,7 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
         if (!finite) { atomicOr(&S.status[0], ST_NONFINITE); atomicCAS(&S.status[1], -1, t); }
         W.q[b] = q;
         W.fails[b] = 0;
+        if (k + q >= W.we[b]) { W.kend[b] = k + q; W.flush[b] = 1; }   // window complete
       }
       __syncthreads();
     } else if (item <= nA) {
@@ -528,7 +540,12 @@ KEP_D void sym_swap_front(double* L, int64_t ld, int32_t m, int32_t a, int32_t z
 
 __global__ void __launch_bounds__(256) lf_swap_kernel(FrontTables T, FactorSlot S, LargeWork W, Batch B) {
   const int32_t b = B.e0 + blockIdx.x;
+  if (threadIdx.x == 0) W.flush[b] = 0;    // this step's flush (if any) has run
   if (W.done[b]) return;
+  if (W.finish[b]) {                       // the window flush of a front that delays the rest ran
+    if (threadIdx.x == 0) { W.done[b] = 1; W.finish[b] = 0; }
+    return;
+  }
   const int32_t nf = W.swap[b];
   if (nf == 0) return;
   const int32_t t = B.lf[b];
@@ -553,88 +570,120 @@ __global__ void __launch_bounds__(256) lf_swap_kernel(FrontTables T, FactorSlot 
 // Schur update of the trailing matrix: C(i, j) -= sum_c L(i, c) (L D)(j, c) over the q accepted
 // pivots, for s = k + q <= j <= i < m.  64 x 64 tiles, 256 threads with 4 x 4 register tiles.
 // ------------------------------------------------------------------------------------------
-KEP_D void tile_bounds(int32_t bidx, int32_t nL, int32_t s, int32_t p, int32_t m, int32_t& lo,
-                       int32_t& hi) {
-  if (bidx < nL) { lo = s + bidx * kTile; hi = min(lo + kTile, p); }
-  else { lo = p + (bidx - nL) * kTile; hi = min(lo + kTile, m); }
-}
+// Block partition of a trailing region that starts at s: blocks of kTile rows/columns, split at p
+// (the boundary between L storage and the contribution block), up to m.
+struct Part {
+  int32_t s, p, m, nL, base2, nR;
+  KEP_D void init(int32_t s_, int32_t p_, int32_t m_) {
+    s = s_; p = p_; m = m_;
+    nL = s < p ? (p - s + kTile - 1) / kTile : 0;
+    base2 = s > p ? s : p;
+    nR = nL + (m > base2 ? (m - base2 + kTile - 1) / kTile : 0);
+  }
+  KEP_D int32_t lo(int32_t b) const { return b < nL ? s + b * kTile : base2 + (b - nL) * kTile; }
+  KEP_D int32_t hi(int32_t b) const {
+    return b < nL ? min(s + (b + 1) * kTile, p) : min(base2 + (b - nL + 1) * kTile, m);
+  }
+};
 
-__global__ void __launch_bounds__(256) lf_update_kernel(FrontTables T, FactorSlot S, double* cbpool,
-                                                        LargeWork W, Batch B) {
+// Schur update C(i, j) -= sum_{c in [c0, c1)} L(i, c) (L D)(j, c) for s <= j < ce, j <= i < m.
+//  WINDOW = true : the rank-q update of the current pivot window's own columns (c0 = k,
+//                  c1 = k + q, s = k + q, ce = window end);
+//  WINDOW = false: the deferred update of everything right of the window with all pivots the
+//                  window accepted (c0 = window start, c1 = its last accepted pivot + 1,
+//                  s = ce' = window end, ce = m), issued once per window ("flush").
+// 64 x 64 tiles, 256 threads with 4 x 4 FP64 register tiles, the pivot range in chunks of 32.
+template <bool WINDOW>
+__global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot S, double* cbpool,
+                                                       LargeWork W, Batch B) {
   __shared__ double Ai[kPanel][kTile + 1];
   __shared__ double Wj[kPanel][kTile + 1];
-  __shared__ double dd[kPanel], de[kPanel];
-  __shared__ int8_t pt[kPanel];
   const int32_t b = B.e0 + blockIdx.y;
-  if (W.done[b]) return;
-  const int32_t q = W.q[b];
-  if (q == 0) return;
+  int32_t c0, c1, s, ce;
+  if (WINDOW) {
+    if (W.done[b]) return;
+    const int32_t q = W.q[b];
+    if (q == 0) return;
+    c0 = W.k[b]; c1 = c0 + q; s = c1; ce = W.we[b];
+  } else {
+    if (W.done[b] || !W.flush[b]) return;
+    c0 = W.ws[b]; c1 = W.kend[b]; s = W.we[b];
+  }
   const int32_t t = B.lf[b];
   const int32_t d_in = S.d_in[t];
   const FrontView v = front_view(T, S, cbpool, t, d_in);
-  const int32_t k = W.k[b];
-  const int32_t s = k + q;
-  const int32_t nL = v.p > s ? (v.p - s + kTile - 1) / kTile : 0;
-  const int32_t nC = (v.c + kTile - 1) / kTile;
-  const int32_t nb = nL + nC;
-  const int32_t ntiles = nb * (nb + 1) / 2;
+  if (!WINDOW) ce = v.m;
+  if (c1 <= c0 || s >= ce) return;
+  Part P;
+  P.init(s, v.p, v.m);
+  int32_t nJ = 0;
+  while (nJ < P.nR && P.lo(nJ) < ce) ++nJ;
+  // tiles (bi, bj), bj < nJ, bi >= bj; tiles of column block bj start at bj*nR - bj*(bj-1)/2
+  const int64_t ntiles = static_cast<int64_t>(nJ) * P.nR - static_cast<int64_t>(nJ) * (nJ - 1) / 2;
   if (blockIdx.x >= ntiles) return;
   const int64_t po = T.piv_off[t];
-  if (threadIdx.x < q) {
-    dd[threadIdx.x] = S.Dd[po + k + threadIdx.x];
-    de[threadIdx.x] = S.De[po + k + threadIdx.x];
-    pt[threadIdx.x] = S.piv[po + k + threadIdx.x];
-  }
-  const double* Lk = v.L + static_cast<int64_t>(k) * v.ldL;   // column k of L
+  const double* Dd = S.Dd + po;
+  const double* De = S.De + po;
+  const int8_t* pv = S.piv + po;
+  const double* Lb = v.L;
+  const int64_t ld = v.ldL;
   const int32_t tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int32_t bi = static_cast<int32_t>((sqrt(8.0 * tile + 1.0) - 1.0) * 0.5);
-    while (bi * (bi + 1) / 2 > tile) --bi;
-    while ((bi + 1) * (bi + 2) / 2 <= tile) ++bi;
-    const int32_t bj = tile - bi * (bi + 1) / 2;
-    int32_t I0, I1, J0, J1;
-    tile_bounds(bi, nL, s, v.p, v.m, I0, I1);
-    tile_bounds(bj, nL, s, v.p, v.m, J0, J1);
-    __syncthreads();
-    // A_I = L(I, k..k+q) and W_J = L(J, k..k+q) D (a 2x2 block mixes its two columns)
-    for (int32_t e = threadIdx.x; e < kPanel * kTile; e += blockDim.x) {
-      const int32_t r = e % kTile, c = e / kTile;
-      double ai = 0.0, wj = 0.0;
-      if (c < q) {
-        if (I0 + r < I1) ai = Lk[static_cast<int64_t>(c) * v.ldL + I0 + r];
-        if (J0 + r < J1) {
-          const double x = Lk[static_cast<int64_t>(c) * v.ldL + J0 + r];
-          const int8_t ptc = pt[c];
-          if (ptc == 1) {
-            wj = x * dd[c];
-          } else if (ptc == 2) {
-            const double y = Lk[static_cast<int64_t>(c + 1) * v.ldL + J0 + r];
-            wj = x * dd[c] + y * de[c];
-          } else {
-            const double y = Lk[static_cast<int64_t>(c - 1) * v.ldL + J0 + r];
-            wj = y * de[c - 1] + x * dd[c];
-          }
-        }
-      }
-      Ai[c][r] = ai;
-      Wj[c][r] = wj;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int32_t lo = 0, hi = nJ - 1;            // largest bj with start(bj) <= tile
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) / 2;
+      const int64_t st = static_cast<int64_t>(mid) * P.nR - static_cast<int64_t>(mid) * (mid - 1) / 2;
+      if (st <= tile) lo = mid; else hi = mid - 1;
     }
-    __syncthreads();
+    const int32_t bj = lo;
+    const int64_t stj = static_cast<int64_t>(bj) * P.nR - static_cast<int64_t>(bj) * (bj - 1) / 2;
+    const int32_t bi = bj + static_cast<int32_t>(tile - stj);
+    const int32_t I0 = P.lo(bi), I1 = P.hi(bi);
+    const int32_t J0 = P.lo(bj), J1 = min(P.hi(bj), ce);
     double acc[4][4];
 #pragma unroll
     for (int32_t x = 0; x < 4; ++x)
 #pragma unroll
       for (int32_t y = 0; y < 4; ++y) acc[x][y] = 0.0;
-    for (int32_t c = 0; c < q; ++c) {
-      double a[4], wv[4];
+    for (int32_t k0 = c0; k0 < c1; k0 += kPanel) {
+      const int32_t kn = min(kPanel, c1 - k0);
+      __syncthreads();
+      // A_I = L(I, chunk) and W_J = L(J, chunk) D (a 2x2 block mixes its two columns)
+      for (int32_t e = threadIdx.x; e < kPanel * kTile; e += blockDim.x) {
+        const int32_t r = e % kTile, cc = e / kTile;
+        double ai = 0.0, wj = 0.0;
+        if (cc < kn) {
+          const int32_t c = k0 + cc;
+          if (I0 + r < I1) ai = Lb[static_cast<int64_t>(c) * ld + I0 + r];
+          if (J0 + r < J1) {
+            const double x = Lb[static_cast<int64_t>(c) * ld + J0 + r];
+            const int8_t ptc = pv[c];
+            if (ptc == 1) {
+              wj = x * Dd[c];
+            } else if (ptc == 2) {
+              const double y = Lb[static_cast<int64_t>(c + 1) * ld + J0 + r];
+              wj = x * Dd[c] + y * De[c];
+            } else {
+              const double y = Lb[static_cast<int64_t>(c - 1) * ld + J0 + r];
+              wj = y * De[c - 1] + x * Dd[c];
+            }
+          }
+        }
+        Ai[cc][r] = ai;
+        Wj[cc][r] = wj;
+      }
+      __syncthreads();
+      for (int32_t cc = 0; cc < kn; ++cc) {
+        double a[4], wv[4];
 #pragma unroll
-      for (int32_t x = 0; x < 4; ++x) a[x] = Ai[c][ty + 16 * x];
+        for (int32_t x = 0; x < 4; ++x) a[x] = Ai[cc][ty + 16 * x];
 #pragma unroll
-      for (int32_t y = 0; y < 4; ++y) wv[y] = Wj[c][tx + 16 * y];
+        for (int32_t y = 0; y < 4; ++y) wv[y] = Wj[cc][tx + 16 * y];
 #pragma unroll
-      for (int32_t x = 0; x < 4; ++x)
+        for (int32_t x = 0; x < 4; ++x)
 #pragma unroll
-        for (int32_t y = 0; y < 4; ++y) acc[x][y] = fma(a[x], wv[y], acc[x][y]);
+          for (int32_t y = 0; y < 4; ++y) acc[x][y] = fma(a[x], wv[y], acc[x][y]);
+      }
     }
 #pragma unroll
     for (int32_t y = 0; y < 4; ++y) {
@@ -729,15 +778,18 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       const int gx_apply = grid_cap(rowtiles + max_p / 32 + 2, std::max<int64_t>(1, (target + nb - 1) / nb));
       const int64_t tb = (max_m + kTile - 1) / kTile + 1;
       const int gx_upd = grid_cap(tb * (tb + 1) / 2, std::max<int64_t>(1, (F.num_sms * 4 + nb - 1) / nb));
+      const int gx_win = grid_cap(tb * (kWindow / kTile + 1), std::max<int64_t>(1, (F.num_sms * 4 + nb - 1) / nb));
       int64_t steps = (max_p + kPanel - 1) / kPanel + 1;
       while (true) {
         for (int64_t it = 0; it < steps; ++it) {
           KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_L21, st, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
-          KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                     lf_update_kernel<<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
+                     lf_schur_kernel<true><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
+          KEP_LAUNCH(F.timer, KC_UPDATE, st,
+                     lf_schur_kernel<false><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
+          KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
         }
         // one more panel call finalises fronts whose last block was accepted
         KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B));

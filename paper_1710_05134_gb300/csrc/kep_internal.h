@@ -16,6 +16,8 @@ namespace kep {
 // ---------------------------------------------------------------------------------------------
 constexpr int kSmallMax = 128;      // fronts with m_alloc <= this are factored in shared memory
 constexpr int kPanel = 32;          // block width of the large-front pivoting panel
+constexpr int kWindow = 256;        // pivot window: the trailing matrix right of it is updated once
+                                    //   per window with all of the window's pivots
 constexpr int kSolveBigM = 2048;    // fronts at least this large (and with kSolveBigP pivots) are
 constexpr int kSolveBigP = 128;     //   solved by the multi-block path
 constexpr int kSolveBlk = 64;       // pivot block of the multi-block solve
@@ -201,6 +203,12 @@ struct LargeWork {
   int32_t* q;           // accepted in current block
   int32_t* fails;       // consecutive failed blocks
   int32_t* swap;        // pending move of a failed pivot (1 or 2 columns) to the end
+  int32_t* ws;          // current pivot window [ws, we)
+  int32_t* we;
+  int32_t* kend;        // pivots [ws, kend) wait for the flush update
+  int32_t* flush;       // 1: the flush update of the window is due this step
+  int32_t* reset;       // 1: open a new window at the next pivot block
+  int32_t* finish;      // 1: the front delays its remaining columns after the flush
   int32_t* done;        // 1 when the front has finished
   double* L11;          // per batch entry: kPanel*kPanel
   double* Dblk;         // per batch entry: 2*kPanel (diag, offdiag)
