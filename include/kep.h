@@ -122,6 +122,19 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind,
                        const double* a_val, const double* b_val, int flags,
                        const double* coords, kep_ctx** out);
 
+/*
+ * Arithmetic of the deferred Schur update (the update of a front's trailing matrix with a window of
+ * up to 256 pivots, Algorithm 1' factorization step).
+ *   KEP_SCHUR_FP64      FP64 FMA tiles everywhere.
+ *   KEP_SCHUR_EMULATED  (default, min_front 4096) fronts of order >= min_front form the update from bf16 tensor-core
+ *                       products of an exact splitting of L and L*D into seven 8-bit pieces per
+ *                       entry (per-row power-of-two scales, exact FP32 level sums, exact int64
+ *                       combination): as accurate as an FP64 update, on the tensor pipe.
+ * Takes effect at the next factorization.  Errors: KEP_ERR_INVALID.
+ */
+enum { KEP_SCHUR_FP64 = 0, KEP_SCHUR_EMULATED = 1 };
+kep_status kep_set_schur_mode(kep_ctx* ctx, int mode, int64_t min_front);
+
 /* Fill *info with the symbolic facts of ctx. */
 kep_status kep_get_info(const kep_ctx* ctx, kep_info* info);
 

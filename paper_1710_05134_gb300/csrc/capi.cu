@@ -89,6 +89,8 @@ void release_memory(kep_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (void* p : c->mem_allocs) cudaFree(p);
   c->mem_allocs.clear();
+  c->emul_ws = nullptr;
+  c->emul_cap_rows = 0;
   for (int i = 0; i < 2; ++i) { c->slot_ready[i] = false; c->slot[i].valid = false; }
 }
 
@@ -132,6 +134,28 @@ kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inert
   F.stream = c->stream;
   F.num_sms = c->num_sms;
   F.timer = &c->timer;
+  F.emul_min = c->schur_mode == KEP_SCHUR_EMULATED ? c->emul_min_front : 0;
+  F.emul_ws = nullptr;
+  F.emul_cap_rows = 0;
+  if (F.emul_min > 0) {
+    int64_t cap = 0;
+    for (int32_t t = 0; t < c->plan.nfronts; ++t)
+      if (c->plan.m_alloc[t] >= F.emul_min) cap = std::max<int64_t>(cap, c->plan.m_alloc[t]);
+    if (cap > 0) {
+      if (c->emul_cap_rows < cap) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, emul_workspace_bytes(cap)) != cudaSuccess) return KEP_ERR_NOMEM;
+        if (cudaMemset(p, 0, emul_workspace_bytes(cap)) != cudaSuccess) return KEP_ERR_CUDA;
+        c->mem_allocs.push_back(p);
+        c->emul_ws = p;
+        c->emul_cap_rows = cap;
+      }
+      F.emul_ws = c->emul_ws;
+      F.emul_cap_rows = c->emul_cap_rows;
+    } else {
+      F.emul_min = 0;
+    }
+  }
   int bits = 0;
   kep_inertia in{0, 0, 0, 0};
   kep_status st = run_factor(F, ca, cb, &in, &bits);
@@ -341,6 +365,13 @@ kep_status kep_get_info(const kep_ctx* c, kep_info* info) {
 kep_status kep_set_stream(kep_ctx* c, void* stream) {
   if (!c) return KEP_ERR_INVALID;
   c->stream = static_cast<cudaStream_t>(stream);
+  return KEP_OK;
+}
+
+kep_status kep_set_schur_mode(kep_ctx* c, int mode, int64_t min_front) {
+  if (!c || (mode != KEP_SCHUR_FP64 && mode != KEP_SCHUR_EMULATED) || min_front < 1) return KEP_ERR_INVALID;
+  c->schur_mode = mode;
+  c->emul_min_front = min_front;
   return KEP_OK;
 }
 

@@ -747,8 +747,15 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
     while (e < width) {
       int32_t t0 = P.level_fronts[lb + e];
       int32_t e1;
-      if (P.m_alloc[t0] > 4096) e1 = e + 1;
-      else e1 = std::min<int32_t>(width, e + 65535);
+      const bool emul = F.emul_min > 0 && P.m_alloc[t0] >= F.emul_min;
+      if (P.m_alloc[t0] > 4096 || emul) {
+        e1 = e + 1;
+      } else {
+        e1 = e + 1;                  // the rest of the level (sorted by size), stopping at a front
+        while (e1 < width && e1 - e < 65535 &&   // that must go alone
+               !(F.emul_min > 0 && P.m_alloc[P.level_fronts[lb + e1]] >= F.emul_min))
+          ++e1;
+      }
       const int32_t nb = e1 - e;
       Batch B{F.d_level_fronts + lb, e};
       int64_t max_m = 0, max_p = 0, max_c = 0, max_ent = 0;
@@ -787,8 +794,12 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_UPDATE, st,
                      lf_schur_kernel<true><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
-          KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                     lf_schur_kernel<false><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
+          if (emul)
+            launch_emul_flush(F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
+                              F.num_sms, F.timer);
+          else
+            KEP_LAUNCH(F.timer, KC_UPDATE, st,
+                       lf_schur_kernel<false><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
         }
         // one more panel call finalises fronts whose last block was accepted

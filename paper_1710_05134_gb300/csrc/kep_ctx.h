@@ -45,6 +45,10 @@ struct kep_ctx {
   double* d_solve_partial = nullptr;
   std::vector<int32_t> slot_nelim[2];   // pivots eliminated per front, per slot (host copy)
   kep::Timer timer;
+  int schur_mode = KEP_SCHUR_EMULATED;
+  int64_t emul_min_front = 4096;
+  void* emul_ws = nullptr;          // tensor-core flush workspace (in mem_allocs)
+  int64_t emul_cap_rows = 0;
   // eigenpair driver state (owned by driver.cu)
   void* driver = nullptr;
   void driver_release();

@@ -23,7 +23,9 @@ KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 # symbols declared in include/kep.h
 EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
-            "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc"]
+            "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
+            "kep_set_schur_mode"]
+KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
 KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
                   "perm", "spmv", "vec"]
 
@@ -102,6 +104,8 @@ def lib() -> ctypes.CDLL:
         L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
         L.kep_dense_inertia_noalloc.argtypes = [I64, P, P, I64, D, P, P]
         L.kep_dense_inertia_noalloc.restype = I
+        L.kep_set_schur_mode.argtypes = [P, I, I64]
+        L.kep_set_schur_mode.restype = I
         L.kep_destroy.argtypes = [P]
         L.kep_destroy.restype = None
         L.kep_status_str.argtypes = [I]
@@ -203,6 +207,12 @@ class Problem:
         handle = getattr(stream, "cuda_stream", stream)
         self._stream = stream
         _check(lib().kep_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)), "kep_set_stream")
+
+    def set_schur_mode(self, emulated: bool, min_front: int = 4096):
+        """Deferred Schur updates of fronts of order >= min_front on the tensor cores (FP64-accurate
+        splitting) when emulated, else FP64 FMA everywhere."""
+        _check(lib().kep_set_schur_mode(self._h, KEP_SCHUR_EMULATED if emulated else KEP_SCHUR_FP64,
+                                        int(min_front)), "kep_set_schur_mode")
 
     def set_timing(self, enable: bool):
         """Per-launch CUDA-event timing of this context's kernels (launch counts are always kept)."""
