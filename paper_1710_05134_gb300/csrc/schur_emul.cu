@@ -5,18 +5,20 @@
 // products the tensor cores sum exactly (an error-free splitting in the manner of Ozaki et al.):
 //
 //  * column balancing: column c of L is scaled by 2^{-u_c} and column c of W by 2^{u_c} (u_c from
-//    the two columns' largest entries), which leaves every product unchanged and keeps the
+//    the two columns' largest exponents), which leaves every product unchanged and keeps the
 //    spread of D out of the rows;
-//  * every row is scaled by a power of two 2^e (max |x| < 2^e) and cut into kSlices integer
-//    pieces, x = 2^e sum_a s_a 2^{-8a}, |s_1| <= 256, |s_a| <= 128 (a > 1), each exact in bf16;
-//  * for each level g = a + b (g <= kSlices + 1) and each K chunk of 32, the tensor cores sum
-//    sum_{a+b=g} sum_c s_a(i, c) t_b(j, c) in FP32; every partial sum is an integer below 2^24
-//    (at most 2^16 + 6 * 2^14 per term, 32 terms), so these FP32 sums are exact;
+//  * every row is scaled by a power of two 2^e (|x| < 2^e for all its entries) and written in
+//    sign-magnitude base-256 digits, |x| 2^{8-e} = sum_a d_a 256^{1-a}, d_a in [0, 255], a = 1..8,
+//    cut from the double's significand with integer shifts (the dropped tail is below 2^-64 of
+//    the row's largest entry); each signed digit is exact in bf16;
+//  * for each level g = a + b (g <= 9) and each K chunk of 32, the tensor cores sum
+//    sum_{a+b=g} sum_c s_a(i, c) t_b(j, c) in FP32; every partial sum is an integer of magnitude
+//    at most 8 * 255^2 * 32 < 2^24, so these FP32 sums are exact;
 //  * the level sums are combined exactly in two int64 accumulators (levels 2..5 and 6..9) and
 //    C(i, j) -= 2^{e_i + f_j} (hi 2^-40 + lo 2^-72) in FP64 once per window.
 //
-// The only rounding is the dropped tail of the splitting (2^-64 of a balanced row's largest
-// entry) and the final FP64 conversion: as accurate as an FP64 rank-r update.
+// The only roundings are the one FP64 product L D, the dropped digit tail and the final FP64
+// conversion: as accurate as an FP64 rank-r update.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -35,11 +37,12 @@ constexpr int kEThreads = 128;                // 4 warps, 32 x 32 each
 constexpr size_t kEmulSmem = 2ull * kSlices * kETile * kEPitch * sizeof(__nv_bfloat16);
 
 struct EmulArgs {
-  __nv_bfloat16* Ls;   // [kSlices][rows][kWindow]
-  __nv_bfloat16* Ws;
-  int32_t* eL;         // [rows]
+  __nv_bfloat16* Ls;   // [kSlices][rows][kWindow] signed digits of the balanced, scaled L rows
+  __nv_bfloat16* Ws;   // same for W
+  double* Wv;          // [kWindow][rows] W = L D (column-major, like L)
+  int32_t* eL;         // [rows] row scale exponents
   int32_t* eW;
-  unsigned long long* cmax;   // [2][kWindow]: largest |L(., c)| and |W(., c)| (as double bits)
+  int32_t* cexp;       // [2][kWindow] largest biased exponent of |L(., c)| and |W(., c)|
   int64_t cap_rows;
 };
 
@@ -47,8 +50,8 @@ KEP_D double pow2(int e) {
   return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
 }
 
-KEP_D int exp_above(double m) {       // smallest e with m < 2^e (m > 0)
-  return ilogb(m) + 1;
+KEP_D int bexp(double x) {                    // biased exponent field (0 for zero / subnormal)
+  return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
 // W(i, c) = sum_c' L(i, c') D(c', c) for the window's pivot c (2x2 blocks mix two columns)
@@ -61,18 +64,33 @@ KEP_D double wval(const double* L, int64_t ld, int64_t i, int32_t c, const doubl
   return L[static_cast<int64_t>(c - 1) * ld + i] * De[c - 1] + x * Dd[c];
 }
 
-KEP_D void cut(double x, int e, __nv_bfloat16* out, int64_t stride) {
-  double r = ldexp(x, 8 - e);
-#pragma unroll
-  for (int a = 0; a < kSlices; ++a) {
-    const double v = rint(r);
-    out[a * stride] = __float2bfloat16_rn(static_cast<float>(v));
-    r = (r - v) * 256.0;
-  }
+KEP_D int balance_shift(const EmulArgs& E, int32_t c) {
+  const int ex = E.cexp[c], ey = E.cexp[kWindow + c];
+  if (ex == 0 || ey == 0) return 0;
+  const int d = ex - ey;
+  return d >= 0 ? d / 2 : -((-d + 1) / 2);     // floor(d / 2)
 }
 
-// Largest |L(i, c)| and |W(i, c)| over the rows i in [we, m), per window column c (one thread
-// per column, CTAs over row chunks).
+// 64-bit fixed point floor(|x| 2^{-u} 2^{8-e} 2^56) of a normal double x (0 for zero/subnormal)
+KEP_D unsigned long long fixed56(double x, int u, int e) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((bits >> 52) & 0x7ff);
+  if (E == 0) return 0ull;
+  const unsigned long long M = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = E - 1011 - u - e;             // value M 2^{E-1075} scaled by 2^{-u+8-e+56}
+  if (sh >= 0) return M << sh;                 // sh <= 11 because the scaled value is below 256
+  if (sh <= -64) return 0ull;
+  return M >> (-sh);
+}
+
+KEP_D __nv_bfloat16 digit_bf16(unsigned d, bool neg) {
+  const float f = __uint2float_rn(d);          // d <= 255: exact, low 16 bits of f are zero
+  const unsigned short h = static_cast<unsigned short>(__float_as_uint(f) >> 16) | (neg && d ? 0x8000 : 0);
+  return __ushort_as_bfloat16(h);
+}
+
+// Pass 1: W = L D for the window's columns over the rows [we, m), and per column the largest
+// exponents of |L| and |W| (CTAs over row chunks, one thread per column).
 __global__ void __launch_bounds__(256) lf_colmax_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
                                                         int32_t b, EmulArgs E) {
   if (W.done[b] || !W.flush[b]) return;
@@ -81,35 +99,47 @@ __global__ void __launch_bounds__(256) lf_colmax_kernel(FrontTables T, FactorSlo
   const int32_t m = T.m_sym[t] + d_in;
   const int32_t c0 = W.ws[b], c1 = W.kend[b], s = W.we[b];
   const int32_t r = c1 - c0;
-  if (r <= 0 || s >= m || static_cast<int32_t>(threadIdx.x) >= r) return;
+  if (r <= 0 || s >= m) return;
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
   const int64_t po = T.piv_off[t];
-  const int32_t c = c0 + threadIdx.x;
   const int64_t rows = m - s;
+  // threads over rows (coalesced), loop over the window's columns
   const int64_t chunk = (rows + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
-  double mx = 0.0, my = 0.0;
-  for (int64_t row = r0; row < r1; ++row) {
-    const int64_t i = s + row;
-    mx = fmax(mx, fabs(L[static_cast<int64_t>(c) * ld + i]));
-    my = fmax(my, fabs(wval(L, ld, i, c, S.Dd + po, S.De + po, S.piv + po)));
+  __shared__ int sx[kWindow], sy[kWindow];
+  for (int32_t c = threadIdx.x; c < kWindow; c += blockDim.x) { sx[c] = 0; sy[c] = 0; }
+  __syncthreads();
+  for (int32_t c = 0; c < r; ++c) {
+    int mx = 0, my = 0;
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+      const int64_t i = s + row;
+      const double x = L[static_cast<int64_t>(c0 + c) * ld + i];
+      const double y = wval(L, ld, i, c0 + c, S.Dd + po, S.De + po, S.piv + po);
+      E.Wv[static_cast<int64_t>(c) * E.cap_rows + row] = y;
+      mx = max(mx, bexp(x));
+      my = max(my, bexp(y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      my = max(my, __shfl_xor_sync(0xffffffffu, my, o));
+    }
+    if ((threadIdx.x & 31) == 0) { atomicMax(&sx[c], mx); atomicMax(&sy[c], my); }
   }
-  atomicMax(&E.cmax[threadIdx.x], static_cast<unsigned long long>(__double_as_longlong(mx)));
-  atomicMax(&E.cmax[kWindow + threadIdx.x], static_cast<unsigned long long>(__double_as_longlong(my)));
+  __syncthreads();
+  for (int32_t c = threadIdx.x; c < r; c += blockDim.x) {
+    atomicMax(&E.cexp[c], sx[c]);
+    atomicMax(&E.cexp[kWindow + c], sy[c]);
+  }
 }
 
-KEP_D int balance_shift(const EmulArgs& E, int32_t c) {
-  const double mx = __longlong_as_double(static_cast<long long>(E.cmax[c]));
-  const double my = __longlong_as_double(static_cast<long long>(E.cmax[kWindow + c]));
-  if (!(mx > 0.0) || !(my > 0.0)) return 0;
-  const int d = ilogb(mx) - ilogb(my);
-  return d >= 0 ? d / 2 : -((-d + 1) / 2);     // floor(d / 2)
-}
-
-// Slices of the balanced L(i, ws..kend) and W(i, ws..kend) for the rows i in [we, m).
-__global__ void __launch_bounds__(128) lf_slice_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
+// Pass 2: per row, the scale exponent of the balanced row, then the eight signed digits of every
+// entry, staged through shared memory so each (digit, row) segment is stored contiguously.
+constexpr int kSRows = 32;                     // rows per CTA
+__global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
                                                        int32_t b, EmulArgs E) {
+  __shared__ __nv_bfloat16 sd[2][kSlices][kSRows][kEK + 2];
+  __shared__ int se[2][kSRows];
   if (W.done[b] || !W.flush[b]) return;
   const int32_t t = lf[b];
   const int32_t d_in = S.d_in[t];
@@ -120,32 +150,64 @@ __global__ void __launch_bounds__(128) lf_slice_kernel(FrontTables T, FactorSlot
   const int32_t rc = (r + kEK - 1) / kEK * kEK;
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
-  const int64_t po = T.piv_off[t];
-  const double* Dd = S.Dd + po;
-  const double* De = S.De + po;
-  const int8_t* pv = S.piv + po;
-  const int64_t stride = E.cap_rows * kWindow;   // between slices
-  for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; row < m - s;
-       row += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = s + row;
-    double mx = 0.0, my = 0.0;
-    for (int32_t c = 0; c < r; ++c) {
-      const int u = balance_shift(E, c);
-      mx = fmax(mx, fabs(ldexp(L[static_cast<int64_t>(c0 + c) * ld + i], -u)));
-      my = fmax(my, fabs(ldexp(wval(L, ld, i, c0 + c, Dd, De, pv), u)));
-    }
-    const int el = mx > 0.0 ? exp_above(mx) : 0;
-    const int ew = my > 0.0 ? exp_above(my) : 0;
-    E.eL[row] = el;
-    E.eW[row] = ew;
-    __nv_bfloat16* ls = E.Ls + row * kWindow;
-    __nv_bfloat16* ws = E.Ws + row * kWindow;
-    for (int32_t c = 0; c < rc; ++c) {
-      const int u = c < r ? balance_shift(E, c) : 0;
-      const double x = c < r ? ldexp(L[static_cast<int64_t>(c0 + c) * ld + i], -u) : 0.0;
-      const double y = c < r ? ldexp(wval(L, ld, i, c0 + c, Dd, De, pv), u) : 0.0;
-      cut(x, el, ls + c, stride);
-      cut(y, ew, ws + c, stride);
+  const int64_t rows = m - s;
+  const int64_t stride = E.cap_rows * kWindow;   // between digits
+  const int lr = threadIdx.x % kSRows;           // row within the CTA's block (loads: coalesced)
+  const int lc = threadIdx.x / kSRows;           // 8 column lanes
+  for (int64_t rb = static_cast<int64_t>(blockIdx.x) * kSRows; rb < rows; rb += static_cast<int64_t>(gridDim.x) * kSRows) {
+    const int64_t row = rb + lr;
+    const bool ok = row < rows;
+    // row exponents of the balanced entries
+    int ex = 0, ey = 0;
+    if (ok)
+      for (int32_t c = lc; c < r; c += 256 / kSRows) {
+        const int u = balance_shift(E, c);
+        const int bx = bexp(L[static_cast<int64_t>(c0 + c) * ld + s + row]);
+        const int by = bexp(E.Wv[static_cast<int64_t>(c) * E.cap_rows + row]);
+        if (bx) ex = max(ex, bx - u);
+        if (by) ey = max(ey, by + u);
+      }
+    __syncthreads();
+    if (lc == 0) { se[0][lr] = 0; se[1][lr] = 0; }
+    __syncthreads();
+    atomicMax(&se[0][lr], ex);
+    atomicMax(&se[1][lr], ey);
+    __syncthreads();
+    const int el = se[0][lr] ? se[0][lr] - 1022 : 0;      // |x 2^-u| < 2^el for the whole row
+    const int ew = se[1][lr] ? se[1][lr] - 1022 : 0;
+    if (ok && lc == 0) { E.eL[row] = el; E.eW[row] = ew; }
+    for (int32_t kc = 0; kc < rc; kc += kEK) {
+      for (int32_t cc = lc; cc < kEK; cc += 256 / kSRows) {
+        const int32_t c = kc + cc;
+        double x = 0.0, y = 0.0;
+        int u = 0;
+        if (ok && c < r) {
+          u = balance_shift(E, c);
+          x = L[static_cast<int64_t>(c0 + c) * ld + s + row];
+          y = E.Wv[static_cast<int64_t>(c) * E.cap_rows + row];
+        }
+        const unsigned long long X = fixed56(x, u, el), Y = fixed56(y, -u, ew);
+        const bool nx = x < 0.0, ny = y < 0.0;
+#pragma unroll
+        for (int a = 0; a < kSlices; ++a) {
+          sd[0][a][lr][cc] = digit_bf16(static_cast<unsigned>((X >> (56 - 8 * a)) & 0xff), nx);
+          sd[1][a][lr][cc] = digit_bf16(static_cast<unsigned>((Y >> (56 - 8 * a)) & 0xff), ny);
+        }
+      }
+      __syncthreads();
+      // store: 2 operands x 8 digits x 32 rows x 32 columns, 4 bytes per thread-store
+      for (int32_t e = threadIdx.x; e < 2 * kSlices * kSRows * (kEK / 2); e += blockDim.x) {
+        const int32_t pair = e % (kEK / 2);
+        const int32_t rr = (e / (kEK / 2)) % kSRows;
+        const int32_t a = (e / (kEK / 2 * kSRows)) % kSlices;
+        const int32_t which = e / (kEK / 2 * kSRows * kSlices);
+        const int64_t grow = rb + rr;
+        if (grow >= rows) continue;
+        const __nv_bfloat162 v2 = __halves2bfloat162(sd[which][a][rr][2 * pair], sd[which][a][rr][2 * pair + 1]);
+        __nv_bfloat16* dst = (which == 0 ? E.Ls : E.Ws) + a * stride + grow * kWindow + kc + 2 * pair;
+        *reinterpret_cast<__nv_bfloat162*>(dst) = v2;
+      }
+      __syncthreads();
     }
   }
 }
@@ -159,8 +221,8 @@ __global__ void __launch_bounds__(kEThreads, 2) lf_flush_emul_kernel(FrontTables
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem_raw);
   __nv_bfloat16* Bs = As + kSlices * kETile * kEPitch;
   if (W.done[b] || !W.flush[b]) return;
-  if (blockIdx.x == 0)                        // column maxima are used up: clear for the next window
-    for (int32_t c = threadIdx.x; c < 2 * kWindow; c += blockDim.x) E.cmax[c] = 0ull;
+  if (blockIdx.x == 0)                        // column exponents are used up: clear for the next window
+    for (int32_t c = threadIdx.x; c < 2 * kWindow; c += blockDim.x) E.cexp[c] = 0;
   const int32_t t = lf[b];
   const int32_t d_in = S.d_in[t];
   const FrontView v = front_view(T, S, cbpool, t, d_in);
@@ -262,7 +324,7 @@ __global__ void __launch_bounds__(kEThreads, 2) lf_flush_emul_kernel(FrontTables
 #pragma unroll
             for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
-              for (int e = 0; e < 4; ++e) Vh[mi][ni][e] += static_cast<long long>(acc[mi][ni][e]) * mul;
+              for (int e = 0; e < 4; ++e) Vh[mi][ni][e] += static_cast<long long>(__float2int_rz(acc[mi][ni][e])) * mul;
         } else {
           const long long mul = 1ll << (8 * (kSlices + 1 - g));
 #pragma unroll
@@ -270,7 +332,7 @@ __global__ void __launch_bounds__(kEThreads, 2) lf_flush_emul_kernel(FrontTables
 #pragma unroll
             for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
-              for (int e = 0; e < 4; ++e) Vl[mi][ni][e] += static_cast<long long>(acc[mi][ni][e]) * mul;
+              for (int e = 0; e < 4; ++e) Vl[mi][ni][e] += static_cast<long long>(__float2int_rz(acc[mi][ni][e])) * mul;
         }
       }
     }
@@ -295,8 +357,8 @@ __global__ void __launch_bounds__(kEThreads, 2) lf_flush_emul_kernel(FrontTables
 }  // namespace
 
 size_t emul_workspace_bytes(int64_t cap_rows) {
-  return 2ull * kSlices * cap_rows * kWindow * sizeof(__nv_bfloat16) + 2ull * cap_rows * sizeof(int32_t) +
-         2ull * kWindow * sizeof(unsigned long long) + 256;
+  return 2ull * kSlices * cap_rows * kWindow * sizeof(__nv_bfloat16) + kWindow * cap_rows * sizeof(double) +
+         2ull * cap_rows * sizeof(int32_t) + 2ull * kWindow * sizeof(int32_t) + 512;
 }
 
 // Slice and flush for batch entry b (a front factored alone); both kernels return at once unless
@@ -313,13 +375,14 @@ void launch_emul_flush(const FrontTables& T, const FactorSlot& S, double* cbpool
   E.cap_rows = cap_rows;
   E.Ls = static_cast<__nv_bfloat16*>(ws);
   E.Ws = E.Ls + static_cast<int64_t>(kSlices) * cap_rows * kWindow;
-  E.eL = reinterpret_cast<int32_t*>(E.Ws + static_cast<int64_t>(kSlices) * cap_rows * kWindow);
+  E.Wv = reinterpret_cast<double*>(E.Ws + static_cast<int64_t>(kSlices) * cap_rows * kWindow);
+  E.eL = reinterpret_cast<int32_t*>(E.Wv + static_cast<int64_t>(kWindow) * cap_rows);
   E.eW = E.eL + cap_rows;
-  E.cmax = reinterpret_cast<unsigned long long*>(
-      (reinterpret_cast<uintptr_t>(E.eW + cap_rows) + 255) / 256 * 256);
-  const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + 127) / 128, num_sms * 8)));
-  KEP_LAUNCH(timer, KC_UPDATE, st, lf_colmax_kernel<<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
-  KEP_LAUNCH(timer, KC_UPDATE, st, lf_slice_kernel<<<gs, 128, 0, st>>>(T, S, W, lf, b, E));
+  E.cexp = E.eW + cap_rows;
+  const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + kSRows - 1) / kSRows, num_sms * 8)));
+  const int gc = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + 255) / 256, num_sms * 2)));
+  KEP_LAUNCH(timer, KC_UPDATE, st, lf_colmax_kernel<<<gc, 256, 0, st>>>(T, S, W, lf, b, E));
+  KEP_LAUNCH(timer, KC_UPDATE, st, lf_slice_kernel<<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
   KEP_LAUNCH(timer, KC_UPDATE, st,
              lf_flush_emul_kernel<<<num_sms * 2, kEThreads, kEmulSmem, st>>>(T, S, cbpool, W, lf, b, E));
 }
