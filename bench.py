@@ -101,6 +101,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _measured_peaks():
+    """bf16 peaks (FLOP/s) from MEASURED_PEAKS.json when present, else the fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16": (d["bf16_tflops"] * 1e12, "measured (MEASURED_PEAKS.json bf16_tflops, burst)"),
+                "bf16_sustained": (d["bf16_tflops_sustained"] * 1e12,
+                                   "measured (MEASURED_PEAKS.json bf16_tflops_sustained)")}
+    except (OSError, KeyError, ValueError):
+        return {"bf16": (1.9e15, "fallback 1.9 PFLOP/s bf16 burst"),
+                "bf16_sustained": (1.7e15, "fallback 1.7 PFLOP/s bf16 sustained")}
+
+
 def flops_of(p) -> float:
     """Symbolic factorization flops of the GPU plan for pencil p (host analysis only)."""
     import paper_1710_05134_gb300 as kep
@@ -165,6 +179,8 @@ def main():
     ap.add_argument("--workload", default="scale", choices=["scale", "mid", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kth", action="store_true",
+                    help="also run Algorithm 4 once (k = n/2) and report the time to lambda_k")
     ap.add_argument("--event-timing", type=int, default=1,
                     help="bracket every launch with CUDA events for the per-kernel roofline (1) or not (0)")
     args = ap.parse_args()
@@ -253,18 +269,33 @@ def main():
                "h2d_bytes_per_step": 2 * 8 * n,
                "d2h_bytes_per_step": 3 * 8 * n + 32}
 
-    # roofline of the dominant kernel: the FP64 Schur-update tiles
-    upd_launches, upd_ms = timing["update"]
-    roofline = None
-    if upd_ms > 0:
-        achieved = info.flops_factor * args.steps / (upd_ms / 1e3)
-        roofline = {"bound": "alu", "kernel": "lf_update_kernel (FP64 FMA Schur tiles)",
-                    "achieved": achieved / 1e12, "peak": FP64_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_DERIVED, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 entry in "
-                                   "MEASURED_PEAKS.json; DFMA probe measured 1.19 TF/s at ~2.0 GHz)",
-                    "launches": upd_launches, "kernel_ms": upd_ms,
-                    "share_of_step": upd_ms / ms if ms > 0 else None}
+    # roofline of the dominant kernel class (by event time in the timed region)
+    peaks = _measured_peaks()
+    classes = {k: v for k, v in timing.items() if k not in ("total_launches", "flops")}
+    dom = max(classes, key=lambda k: classes[k][1])
+    fl = timing["flops"]
+    roofline, rooflines = None, {}
+    if classes["update"][1] > 0 and fl["update"] > 0:
+        a = fl["update"] / (classes["update"][1] / 1e3)
+        rooflines["update"] = {"bound": "alu", "kernel": "lf_schur_kernel (FP64 FMA tiles)",
+                               "achieved": a / 1e12, "peak": FP64_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
+                               "frac": a / FP64_PEAK_DERIVED,
+                               "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                               "launches": classes["update"][0], "kernel_ms": classes["update"][1]}
+    if classes["flush_tc"][1] > 0 and fl["flush_tc"] > 0:
+        a = fl["flush_tc"] / (classes["flush_tc"][1] / 1e3)
+        pk, src = peaks["bf16_sustained"]
+        rooflines["flush_tc"] = {"bound": "tensor", "kernel": "lf_flush_emul_kernel (bf16 mma.sync, exact splitting)",
+                                 "achieved": a / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s", "frac": a / pk,
+                                 "peak_source": src, "launches": classes["flush_tc"][0],
+                                 "kernel_ms": classes["flush_tc"][1],
+                                 "fp64_equivalent_tflops": fl["flush_fp64_equivalent"] / (classes["flush_tc"][1] / 1e3) / 1e12}
+    roofline = rooflines.get(dom)
+    if roofline is not None:
+        roofline = dict(roofline)
+        roofline["traffic"] = None
+        roofline["share_of_step"] = roofline["kernel_ms"] / ms if ms > 0 else None
+        roofline["class"] = dom
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -276,6 +307,14 @@ def main():
                           f"{CPU_SAMPLE['nx']}x{CPU_SAMPLE['ny']}x{CPU_SAMPLE['nz']} cells (n={ps.n}): "
                           f"{min(times):.2f} s per factorization, scaled to n={n} by the GPU plan's flop "
                           f"ratio {ratio:.3e}")}
+
+    kth = None
+    if args.kth and rank == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lam, xk, rep = P.kth_eigenpair(p.k)
+        t_kth = time.perf_counter() - t0
+        kth = {"time_to_lambda_k_s": t_kth, "k": p.k, "lambda_k": lam, "report": rep}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -292,8 +331,13 @@ def main():
                            "event_timing": bool(args.event_timing),
                            "nu": nus[args.warmup:args.warmup + args.steps]},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": timing["total_launches"],
-                "roofline": roofline, "cpu_baseline": cpu,
-                "kernels_ms": {k: v[1] for k, v in timing.items() if k != "total_launches"}}
+                "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu,
+                "factorization_fp64_equivalent_tflops": info.flops_factor * args.steps / (
+                    sum(classes[c][1] for c in ("assemble", "panel", "l21", "apply", "update", "reduce", "slice",
+                                                 "flush_tc")) / 1e3) / 1e12 if args.event_timing else None,
+                "kernels_ms": {k: v[1] for k, v in classes.items()}}
+        if kth is not None:
+            line["time_to_lambda_k"] = kth
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -196,16 +196,21 @@ kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, 
 
 /*
  * Kernel accounting.  Classes (index into the arrays): 0 assembly (zero, scatter, extend-add),
- * 1 pivot panel, 2 L21 rows, 3 apply, 4 Schur update, 5 inertia reduction, 6 forward solve,
- * 7 backward solve, 8 permutation, 9 SpMV, 10 vector operations of the eigenpair driver.
+ * 1 pivot panel, 2 L21 rows, 3 apply, 4 FP64 Schur tiles, 5 inertia reduction, 6 forward solve,
+ * 7 backward solve, 8 permutation, 9 SpMV, 10 vector operations of the eigenpair driver,
+ * 11 splitting for the tensor-core Schur update, 12 tensor-core Schur update.
  * launches[] always counts every kernel launch of ctx since the last reset.  ms[] sums the
  * CUDA-event time of each launch (events recorded on ctx's stream around the launch) and is
- * filled only while timing is enabled.
+ * filled only while timing is enabled.  flops[] is the algorithmic work counted on the device:
+ * class 4 the FP64 multiply-adds x 2 of its updates, class 12 the bf16 tensor-core products x 2
+ * it issued; flush_fp64_equivalent_flops is the FP64 update work those products carried out.
  */
-#define KEP_NKCLASS 11
+#define KEP_NKCLASS 13
 typedef struct {
   int64_t launches[KEP_NKCLASS];
   double ms[KEP_NKCLASS];
+  double flops[KEP_NKCLASS];
+  double flush_fp64_equivalent_flops;
   int64_t total_launches;
 } kep_timing;
 

@@ -134,6 +134,7 @@ kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inert
   F.stream = c->stream;
   F.num_sms = c->num_sms;
   F.timer = &c->timer;
+  F.flops = c->d_flops;
   F.emul_min = c->schur_mode == KEP_SCHUR_EMULATED ? c->emul_min_front : 0;
   F.emul_ws = nullptr;
   F.emul_cap_rows = 0;
@@ -332,6 +333,8 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   AL(W.pt, ent * kPanel); AL(W.colmax, ent * kPanel);
   AL(c->d_cbpool, P.cb_total);
   AL(c->d_red, 8);
+  AL(c->d_flops, KC_COUNT + 1);
+  if (cudaMemset(c->d_flops, 0, sizeof(unsigned long long) * (KC_COUNT + 1)) != cudaSuccess) { kep_destroy(c); return KEP_ERR_CUDA; }
   AL(c->d_bnew, P.n); AL(c->d_xnew, P.n);
   AL(c->d_solve_partial, static_cast<size_t>(c->num_sms) * 4 * (kSolveBlk + 1));
   AL(c->d_io0, P.n); AL(c->d_io1, P.n); AL(c->d_io2, P.n);
@@ -444,13 +447,20 @@ kep_status kep_get_timing(kep_ctx* c, kep_timing* out, int reset) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
   c->timer.collect();
   int64_t total = 0;
+  unsigned long long fl[KC_COUNT + 1];
+  if (cudaMemcpy(fl, c->d_flops, sizeof(fl), cudaMemcpyDeviceToHost) != cudaSuccess) return KEP_ERR_CUDA;
   for (int k = 0; k < KEP_NKCLASS; ++k) {
     out->launches[k] = c->timer.launches[k];
     out->ms[k] = c->timer.ms[k];
+    out->flops[k] = static_cast<double>(fl[k]);
     total += c->timer.launches[k];
   }
+  out->flush_fp64_equivalent_flops = static_cast<double>(fl[KC_COUNT]);
   out->total_launches = total;
-  if (reset) c->timer.reset();
+  if (reset) {
+    c->timer.reset();
+    if (cudaMemset(c->d_flops, 0, sizeof(fl)) != cudaSuccess) return KEP_ERR_CUDA;
+  }
   return KEP_OK;
 }
 

@@ -595,7 +595,7 @@ struct Part {
 // 64 x 64 tiles, 256 threads with 4 x 4 FP64 register tiles, the pivot range in chunks of 32.
 template <bool WINDOW>
 __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot S, double* cbpool,
-                                                       LargeWork W, Batch B) {
+                                                       LargeWork W, Batch B, unsigned long long* flops) {
   __shared__ double Ai[kPanel][kTile + 1];
   __shared__ double Wj[kPanel][kTile + 1];
   const int32_t b = B.e0 + blockIdx.y;
@@ -621,6 +621,10 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot
   // tiles (bi, bj), bj < nJ, bi >= bj; tiles of column block bj start at bj*nR - bj*(bj-1)/2
   const int64_t ntiles = static_cast<int64_t>(nJ) * P.nR - static_cast<int64_t>(nJ) * (nJ - 1) / 2;
   if (blockIdx.x >= ntiles) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {   // algorithmic flops: 2 * rank per updated entry
+    const int64_t w = ce - s, h = v.m - s;
+    atomicAdd(flops, static_cast<unsigned long long>(2 * static_cast<int64_t>(c1 - c0) * (w * h - w * (w - 1) / 2)));
+  }
   const int64_t po = T.piv_off[t];
   const double* Dd = S.Dd + po;
   const double* De = S.De + po;
@@ -793,13 +797,15 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
           KEP_LAUNCH(F.timer, KC_L21, st, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                     lf_schur_kernel<true><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
+                     lf_schur_kernel<true><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
+                                                                            F.flops + KC_UPDATE));
           if (emul)
             launch_emul_flush(F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
-                              F.num_sms, F.timer);
+                              F.num_sms, F.timer, F.flops);
           else
             KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                       lf_schur_kernel<false><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
+                       lf_schur_kernel<false><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
+                                                                                F.flops + KC_UPDATE));
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
         }
         // one more panel call finalises fronts whose last block was accepted

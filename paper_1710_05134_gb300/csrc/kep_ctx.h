@@ -32,6 +32,7 @@ struct kep_ctx {
   double* d_cbpool = nullptr;
   kep::LargeWork W{};
   long long* d_red = nullptr;
+  unsigned long long* d_flops = nullptr;   // per kernel class (+1: FP64 work the tensor flush stands for)
   long long* h_red = nullptr;       // pinned
   int32_t* h_done = nullptr;        // pinned
   // solve workspaces

@@ -30,7 +30,7 @@ constexpr double kThresholdU = 0.01;               // threshold pivoting paramet
 // ---------------------------------------------------------------------------------------------
 enum KClass : int {
   KC_ASSEMBLE = 0, KC_PANEL, KC_L21, KC_APPLY, KC_UPDATE, KC_REDUCE,
-  KC_SOLVE_FWD, KC_SOLVE_BWD, KC_PERM, KC_SPMV, KC_VEC, KC_COUNT
+  KC_SOLVE_FWD, KC_SOLVE_BWD, KC_PERM, KC_SPMV, KC_VEC, KC_SLICE, KC_FLUSH_TC, KC_COUNT
 };
 
 struct Timer {
@@ -236,6 +236,7 @@ struct FactorLaunch {
   int64_t emul_min;         // fronts with m_alloc >= this use the tensor-core flush (0: never)
   void* emul_ws;            // its workspace
   int64_t emul_cap_rows;
+  unsigned long long* flops;   // per kernel class: algorithmic flops, counted on the device
 };
 
 struct SolveLaunch {
@@ -259,7 +260,7 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
 size_t emul_workspace_bytes(int64_t cap_rows);
 void launch_emul_flush(const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
                        const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
-                       cudaStream_t st, int num_sms, Timer* timer);
+                       cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops);
 kep_status run_solve(SolveLaunch& L, const double* b, double* x);
 kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
                     const double* x, double* ya, double* yb, cudaStream_t st, int num_sms,

@@ -216,7 +216,7 @@ KEP_D uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const ui
 
 __global__ void __launch_bounds__(kEThreads, 2) lf_flush_emul_kernel(FrontTables T, FactorSlot S, double* cbpool,
                                                                      LargeWork W, const int32_t* lf, int32_t b,
-                                                                     EmulArgs E) {
+                                                                     EmulArgs E, unsigned long long* flops) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem_raw);
   __nv_bfloat16* Bs = As + kSlices * kETile * kEPitch;
@@ -238,6 +238,14 @@ __global__ void __launch_bounds__(kEThreads, 2) lf_flush_emul_kernel(FrontTables
   auto blo = [&](int32_t q) { return q < nL ? s + q * kETile : base2 + (q - nL) * kETile; };
   auto bhi = [&](int32_t q) { return q < nL ? min(s + (q + 1) * kETile, v.p) : min(base2 + (q - nL + 1) * kETile, v.m); };
   const int64_t ntiles = static_cast<int64_t>(nR) * (nR + 1) / 2;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // tensor-core work issued: every tile, every K chunk, every (level, pair) product
+    constexpr int64_t kPairs = kSlices * (kSlices + 1) / 2;
+    atomicAdd(&flops[KC_FLUSH_TC], static_cast<unsigned long long>(2 * kPairs * rc * ntiles * kETile * kETile));
+    // the FP64 update it stands for
+    const int64_t h = v.m - s;
+    atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (h * (h + 1) / 2)));
+  }
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int wr = warp >> 1, wc = warp & 1;
   const int gq = lane >> 2, tq = lane & 3;
@@ -365,7 +373,7 @@ size_t emul_workspace_bytes(int64_t cap_rows) {
 // the front's window flush is due this step.
 void launch_emul_flush(const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
                        const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
-                       cudaStream_t st, int num_sms, Timer* timer) {
+                       cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lf_flush_emul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kEmulSmem));
@@ -381,10 +389,10 @@ void launch_emul_flush(const FrontTables& T, const FactorSlot& S, double* cbpool
   E.cexp = E.eW + cap_rows;
   const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + kSRows - 1) / kSRows, num_sms * 8)));
   const int gc = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + 255) / 256, num_sms * 2)));
-  KEP_LAUNCH(timer, KC_UPDATE, st, lf_colmax_kernel<<<gc, 256, 0, st>>>(T, S, W, lf, b, E));
-  KEP_LAUNCH(timer, KC_UPDATE, st, lf_slice_kernel<<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
-  KEP_LAUNCH(timer, KC_UPDATE, st,
-             lf_flush_emul_kernel<<<num_sms * 2, kEThreads, kEmulSmem, st>>>(T, S, cbpool, W, lf, b, E));
+  KEP_LAUNCH(timer, KC_SLICE, st, lf_colmax_kernel<<<gc, 256, 0, st>>>(T, S, W, lf, b, E));
+  KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
+  KEP_LAUNCH(timer, KC_FLUSH_TC, st,
+             lf_flush_emul_kernel<<<num_sms * 2, kEThreads, kEmulSmem, st>>>(T, S, cbpool, W, lf, b, E, flops));
 }
 
 }  // namespace kep

@@ -27,7 +27,7 @@ EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream
             "kep_set_schur_mode"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
 KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
-                  "perm", "spmv", "vec"]
+                  "perm", "spmv", "vec", "slice", "flush_tc"]
 
 
 class KepError(RuntimeError):
@@ -58,7 +58,8 @@ class Params(ctypes.Structure):
 
 
 class Timing(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 11), ("ms", ctypes.c_double * 11),
+    _fields_ = [("launches", ctypes.c_int64 * 13), ("ms", ctypes.c_double * 13),
+                ("flops", ctypes.c_double * 13), ("flush_fp64_equivalent_flops", ctypes.c_double),
                 ("total_launches", ctypes.c_int64)]
 
 
@@ -219,11 +220,14 @@ class Problem:
         _check(lib().kep_set_timing(self._h, 1 if enable else 0), "kep_set_timing")
 
     def timing(self, reset: bool = False) -> dict:
-        """{class: (launches, milliseconds)} since the last reset, plus 'total_launches'."""
+        """{class: (launches, milliseconds)} since the last reset, plus 'total_launches' and
+        'flops' ({class: device-counted algorithmic flops}, 'flush_fp64_equivalent')."""
         t = Timing()
         _check(lib().kep_get_timing(self._h, ctypes.byref(t), 1 if reset else 0), "kep_get_timing")
         d = {name: (int(t.launches[i]), float(t.ms[i])) for i, name in enumerate(KERNEL_CLASSES)}
         d["total_launches"] = int(t.total_launches)
+        d["flops"] = {name: float(t.flops[i]) for i, name in enumerate(KERNEL_CLASSES)}
+        d["flops"]["flush_fp64_equivalent"] = float(t.flush_fp64_equivalent_flops)
         return d
 
     def factor(self, sigma: float, *, allow_singular: bool = True) -> FactorResult:

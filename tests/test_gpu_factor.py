@@ -199,7 +199,8 @@ def test_timing_counters(kep, small):
     P.factor(0.3)
     t = P.timing(reset=True)
     assert t["update"][0] > 0 and t["update"][1] > 0
-    assert t["total_launches"] == sum(v[0] for k, v in t.items() if k != "total_launches")
+    assert t["total_launches"] == sum(v[0] for k, v in t.items() if k not in ("total_launches", "flops"))
+    assert t["flops"]["update"] > 0
 
 
 def test_solve_multiblock_fronts_vs_sparse_lu(kep):
