@@ -171,6 +171,7 @@ kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inert
   if (out) *out = in;
   if (bits & ST_POOL) return KEP_ERR_POOL;
   if (bits & ST_NONFINITE) return KEP_ERR_NONFINITE;
+  if (bits & ST_TIMEOUT) return KEP_ERR_TIMEOUT;
   if (in.neg + in.zero + in.pos != c->plan.n) return KEP_ERR_POOL;
   S.valid = true;
   c->slot_zero[slot] = in.zero;

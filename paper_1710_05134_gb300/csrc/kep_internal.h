@@ -193,6 +193,7 @@ enum : int32_t {
   ST_POOL = 1,          // delays exceeded a front's slack
   ST_NONFINITE = 2,     // NaN/Inf pivot
   ST_ROOT_FORCED = 4,   // a root block failed the threshold test and was accepted as is
+  ST_TIMEOUT = 8,       // a bounded wait inside a tensor-core kernel gave up
 };
 
 // Large-front step workspace (per level batch).
