@@ -14,10 +14,10 @@
 //    operations (the dropped tail is below 2^-63 of 2^e); each digit times the sign of x is exact
 //    in bf16 and every digit product is at most 2^14 in magnitude;
 //  * the tensor cores (tcgen05, accumulators in tensor memory) sum, for each level g = a + b
-//    (2 <= g <= 9), the products s_a(i, c) t_b(j, c) over the whole window in two FP32
-//    accumulators, one for a <= 4 and one for a >= 5.  Each holds at most 4 pairs x 256 columns x
-//    2^14 = 2^24 in magnitude, integers all along, so every FP32 sum is exact;
-//  * the twelve exact level sums of an entry are combined in integers and C(i, j) receives
+//    (2 <= g <= 9) and each half of the window (128 columns), the products s_a(i, c) t_b(j, c) in
+//    one FP32 accumulator.  It holds at most 8 pairs x 128 columns x 2^14 = 2^24 in magnitude,
+//    integers all along, so every FP32 sum is exact;
+//  * the exact level sums of an entry are combined in integers and C(i, j) receives
 //    -2^{e_i + f_j - 72} (V_hi 2^32 + V_lo), rounded once to FP64.
 //
 // The only roundings are the one FP64 product L D, the dropped digit tail and the final FP64
@@ -26,7 +26,9 @@
 // Tensor-core layout: a CTA owns a 128 x 32 tile of C (rows i, columns j).  Per 16-column step it
 // issues eight MMAs, slice a of the L rows (M = 128) against slices 1 .. 9-a of the W rows stacked
 // along N (N = 32 (9-a)), writing the accumulators of levels a+1 .. 9 side by side in tensor
-// memory; both operands are staged in shared memory by bulk copies in a five-step pipeline.
+// memory (8 levels x 32 columns per half window, two such buffers, so the MMAs of one half run
+// while the epilogue reads the other); both operands are staged in shared memory by bulk copies
+// in a five-step pipeline.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -46,21 +48,34 @@ constexpr uint32_t kStageA = 2 * kSlices * kTM * 16;   // [k-block 2][slice 8][r
 constexpr uint32_t kStageB = 2 * kSlices * kTN * 16;   // [k-block 2][slice 8][row 32][16 B]
 constexpr uint32_t kStageBytes = kStageA + kStageB;
 constexpr size_t kFlushSmem = static_cast<size_t>(kStages) * kStageBytes + 1024;
-constexpr int kFlushThreads = 192;            // warps 0-3 epilogue, 4 copies, 5 MMA issue
-constexpr uint32_t kTmemCols = 512;           // 8 + 4 level accumulators x 32 columns (384 used)
+constexpr int kEpiWarps = 8;                  // epilogue: warp w reads lanes 32 (w % 4), columns 16 (w / 4)
+constexpr int kFlushThreads = (kEpiWarps + 2) * 32;   // + one copy warp, one MMA-issue warp
+constexpr uint32_t kTmemCols = 512;           // 2 buffers x 8 level accumulators x 32 columns
+constexpr int kHalf = 8;                      // 16-column steps per accumulation (128 columns)
 constexpr uint64_t kWaitNs = 2000000000ull;   // bounded waits: 2 s
 constexpr int kNoExp = -(1 << 20);            // row maximum of an all-zero row
 
 struct EmulArgs {
-  __nv_bfloat16* Ls;   // digits of the balanced, scaled L rows: [slice][k-block][row (pitch R)][8]
-  __nv_bfloat16* Ws;   // same for W
+  __nv_bfloat16* Ls;   // digits of the balanced, scaled L rows, tile-contiguous (ldig_off)
+  __nv_bfloat16* Ws;   // digits of the W rows (wdig_off)
   double* Wv;          // [kWindow][cap_rows] W = L D (column-major, like L)
   int32_t* eL;         // [R] row scale exponents
   int32_t* eW;
   int32_t* cexp;       // [2][kWindow] largest biased exponent of |L(., c)| and |W(., c)|
   int64_t cap_rows;
-  int64_t R;           // row pitch of the digit arrays (>= rows + kTM)
+  int64_t R;           // rows of the digit arrays (a multiple of kTM, >= rows + kTM)
 };
+
+// Digit layouts: for the L rows, blocks of 128 rows, then 16-column steps, then the two 8-column
+// halves, then the slice, then [128 rows][8 columns]; for the W rows the same with blocks of 32.
+// One step of one tile is then a contiguous 32 KiB (L) and 8 KiB (W) run whose order is that of
+// the shared-memory operands.
+KEP_D int64_t ldig_off(int a, int32_t q, int64_t row) {      // q: 8-column block
+  return (((((row >> 7) * (kWindow / 16) + (q >> 1)) * 2 + (q & 1)) * kSlices + a) * kTM + (row & (kTM - 1))) * 8;
+}
+KEP_D int64_t wdig_off(int a, int32_t q, int64_t row) {
+  return (((((row >> 5) * (kWindow / 16) + (q >> 1)) * 2 + (q & 1)) * kSlices + a) * kTN + (row & (kTN - 1))) * 8;
+}
 
 KEP_HD int64_t digit_pitch(int64_t cap_rows) { return (cap_rows + kTM - 1) / kTM * kTM + kTM; }
 
@@ -219,26 +234,40 @@ __global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot
             else pk[a][e / 2] |= d[a] << 16;
           }
         }
-        __nv_bfloat16* base = which == 0 ? E.Ls : E.Ws;
 #pragma unroll
         for (int a = 0; a < kSlices; ++a)
-          *reinterpret_cast<uint4*>(base + ((static_cast<int64_t>(a) * kKB + q) * E.R + row) * 8) =
+          *reinterpret_cast<uint4*>(which == 0 ? E.Ls + ldig_off(a, q, row) : E.Ws + wdig_off(a, q, row)) =
               make_uint4(pk[a][0], pk[a][1], pk[a][2], pk[a][3]);
       }
     }
   }
 }
 
-// Tiles of the lower triangle of [s, m): i-blocks of 128 rows, j-blocks of 32; i-block I pairs
-// with j-blocks 0 .. 4I+3 (the last one with all j-blocks).
-KEP_D void tile_ij(int64_t t, int64_t nI, int64_t& I, int64_t& J) {
-  const int64_t full = 2 * (nI - 1) * nI;
-  if (t >= full) { I = nI - 1; J = t - full; return; }
-  int64_t i = static_cast<int64_t>((sqrt(1.0 + 2.0 * static_cast<double>(t)) - 1.0) * 0.5);
-  while (i > 0 && 2 * i * (i + 1) > t) --i;
-  while (2 * (i + 1) * (i + 2) <= t) ++i;
-  I = i;
-  J = t - 2 * i * (i + 1);
+// Tiles of the lower triangle of [s, m): i-blocks of 128 rows, j-blocks of 32.  Bands of kBand
+// i-blocks are taken in turn; inside a band the order is j-major, so the concurrently running
+// tiles share their j-blocks (the W digits are read from memory about once per band).  Slots of
+// a band's rectangle above the diagonal or past the last j-block are empty (false).
+constexpr int kBand = 8;
+KEP_D int64_t tile_slots(int64_t nI, int64_t nJ) {
+  int64_t n = 0;
+  for (int64_t I0 = 0; I0 < nI; I0 += kBand) {
+    const int64_t I1 = min(I0 + kBand, nI);
+    n += (I1 - I0) * min(4 * I1, nJ);
+  }
+  return n;
+}
+KEP_D bool tile_ij(int64_t t, int64_t nI, int64_t nJ, int64_t& I, int64_t& J) {
+  for (int64_t I0 = 0; I0 < nI; I0 += kBand) {
+    const int64_t I1 = min(I0 + kBand, nI);
+    const int64_t cnt = (I1 - I0) * min(4 * I1, nJ);
+    if (t < cnt) {
+      J = t / (I1 - I0);
+      I = I0 + t % (I1 - I0);
+      return J < 4 * (I + 1);
+    }
+    t -= cnt;
+  }
+  return false;
 }
 
 // (hi 2^32 + lo) 2^scale rounded to the nearest double (ties to even), integer operations only;
@@ -276,7 +305,34 @@ KEP_D double combine_to_double(long long hi, long long lo, int scale) {
 }
 
 // Exact integer from an FP32 level sum that holds an integer (|v| <= 2^24).
-KEP_D int level_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
+KEP_D int level_int(float v) { return __float2int_rn(v); }
+
+// The level sums of one entry over one half window (x[g]: level g+2, |x[g]| <= 2^24) added in
+// base 256 to levels 2..5 (vh) and 6..9 (vl).  Fast path: with every level sum at most 2^22 in
+// magnitude, v + 1.5 2^23 lands in [2^23, 2^24], where the float's bits minus those of 1.5 2^23
+// are the integer v; otherwise (rare) each sum is converted on its own.
+constexpr float kMagic = 12582912.0f;          // 1.5 2^23
+constexpr int kMagicBits = 0x4B400000;
+KEP_D void add_levels(const float (&x)[8], long long& vh, long long& vl) {
+  int l[8];
+  unsigned worst = 0;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    l[g] = __float_as_int(x[g] + kMagic) - kMagicBits;
+    worst = max(worst, static_cast<unsigned>(l[g] + (1 << 22)));   // in [0, 2^23] when exact
+  }
+  if (worst <= (1u << 23)) {
+    vh += static_cast<long long>(l[0] * 256 + l[1]) * 65536 + (l[2] * 256 + l[3]);
+    vl += static_cast<long long>(l[4] * 256 + l[5]) * 65536 + (l[6] * 256 + l[7]);
+  } else {
+#pragma unroll
+    for (int g = 0; g < 8; ++g) l[g] = level_int(x[g]);
+    vh += (static_cast<long long>(l[0]) << 24) + (static_cast<long long>(l[1]) << 16) +
+          (static_cast<long long>(l[2]) << 8) + l[3];
+    vl += (static_cast<long long>(l[4]) << 24) + (static_cast<long long>(l[5]) << 16) +
+          (static_cast<long long>(l[6]) << 8) + l[7];
+  }
+}
 
 __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTables T, FactorSlot S, double* cbpool,
                                                                        LargeWork W, const int32_t* lf, int32_t b,
@@ -284,7 +340,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
-  __shared__ __align__(8) uint64_t tfull_bar, tempty_bar, drain_bar;
+  __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   if (W.done[b] || !W.flush[b]) return;
@@ -297,23 +353,24 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   const int32_t r = c1 - c0;
   if (r <= 0 || s >= v.m) return;
   const int KS = (r + 15) / 16;               // 16-column steps
+  const int NH = (KS + kHalf - 1) / kHalf;    // accumulation halves
   const int64_t h = v.m - s;
   const int64_t nI = (h + kTM - 1) / kTM, nJ = (h + kTN - 1) / kTN;
-  const int64_t ntiles = 2 * nI * (nI - 1) + nJ;
+  const int64_t nslots = tile_slots(nI, nJ);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // tensor-core work issued, and the FP64 update it stands for
+    // tensor-core work issued (2 nI (nI - 1) + nJ tiles), and the FP64 update it stands for
+    const int64_t ntiles = 2 * nI * (nI - 1) + nJ;
     atomicAdd(&flops[KC_FLUSH_TC],
               static_cast<unsigned long long>(2ll * kTM * (kSlices * (kSlices + 1) / 2) * kTN * 16 * KS * ntiles));
     atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (h * (h + 1) / 2)));
   }
-  if (blockIdx.x >= ntiles) return;
+  if (blockIdx.x >= nslots) return;
   unsigned char* sbase =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) { tc::mbar_init(&full_bar[i], 1); tc::mbar_init(&empty_bar[i], 1); }
-    tc::mbar_init(&tfull_bar, 1);
-    tc::mbar_init(&tempty_bar, 4 * 32);
+    for (int i = 0; i < 2; ++i) { tc::mbar_init(&tfull_bar[i], 1); tc::mbar_init(&tempty_bar[i], kEpiWarps * 32); }
     tc::mbar_init(&drain_bar, 1);
     tc::fence_mbar_init();
     abort_flag = 0;
@@ -326,36 +383,26 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
-  const int64_t total = my_tiles * KS;
 
-  if (warp == 4) {
-    // ---- producer: bulk copies of one 16-column step of all digits of the tile's rows ----
+  if (warp == kEpiWarps) {
+    // ---- producer: one bulk copy per operand per 16-column step ----
     if (lane == 0) {
       int64_t f = 0;
       bool ok = true;
-      for (; f < total; ++f) {
-        const int st = static_cast<int>(f % kStages);
-        if (f >= kStages && !tc::mbar_wait(&empty_bar[st], static_cast<uint32_t>((f / kStages - 1) & 1), kWaitNs)) {
-          ok = false;
-          break;
-        }
+      for (int64_t slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
         int64_t I, J;
-        tile_ij(blockIdx.x + (f / KS) * gridDim.x, nI, I, J);
-        const int kk = static_cast<int>(f % KS);
-        unsigned char* sa = sbase + static_cast<size_t>(st) * kStageBytes;
-        unsigned char* sb = sa + kStageA;
-        tc::mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
-#pragma unroll 1
-        for (int kb = 0; kb < 2; ++kb)
-#pragma unroll 1
-          for (int a = 0; a < kSlices; ++a) {
-            const int64_t q = static_cast<int64_t>(a) * kKB + 2 * kk + kb;
-            tc::bulk_g2s(sa + kb * (kStageA / 2) + a * (kTM * 16), E.Ls + (q * E.R + I * kTM) * 8, kTM * 16,
-                         &full_bar[st]);
-            tc::bulk_g2s(sb + kb * (kStageB / 2) + a * (kTN * 16), E.Ws + (q * E.R + J * kTN) * 8, kTN * 16,
-                         &full_bar[st]);
+        if (!tile_ij(slot, nI, nJ, I, J)) continue;
+        for (int kk = 0; kk < KS; ++kk, ++f) {
+          const int st = static_cast<int>(f % kStages);
+          if (f >= kStages && !tc::mbar_wait(&empty_bar[st], static_cast<uint32_t>((f / kStages - 1) & 1), kWaitNs)) {
+            ok = false;
+            break;
           }
+          unsigned char* sa = sbase + static_cast<size_t>(st) * kStageBytes;
+          tc::mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
+          tc::bulk_g2s(sa, E.Ls + ldig_off(0, 2 * kk, I * kTM), kStageA, &full_bar[st]);
+          tc::bulk_g2s(sa + kStageA, E.Ws + wdig_off(0, 2 * kk, J * kTN), kStageB, &full_bar[st]);
+        }
       }
       if (!ok) {
         abort_flag = 1;
@@ -364,95 +411,112 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
           tc::mbar_wait(&full_bar[g % kStages], static_cast<uint32_t>((g / kStages) & 1), kWaitNs);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == kEpiWarps + 1) {
     // ---- MMA issue: per step, slice a of L against the stacked slices 1 .. 8-a of W ----
     if (lane == 0) {
       const uint32_t s0 = tc::smem_addr(sbase);
-      int64_t f = 0;
+      int64_t f = 0, u = 0;                     // steps, half-window accumulations issued
       bool ok = true;
-      for (int64_t n = 0; n < my_tiles && ok; ++n) {
-        if (n > 0 && !tc::mbar_wait(&tempty_bar, static_cast<uint32_t>((n - 1) & 1), kWaitNs)) {
-          ok = false;
-          break;
-        }
-        tc::fence_after_sync();
-        for (int kk = 0; kk < KS; ++kk, ++f) {
-          const int st = static_cast<int>(f % kStages);
-          if (!tc::mbar_wait(&full_bar[st], static_cast<uint32_t>((f / kStages) & 1), kWaitNs)) {
+      for (int64_t slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
+        int64_t I, J;
+        if (!tile_ij(slot, nI, nJ, I, J)) continue;
+        for (int hh = 0; hh < NH && ok; ++hh, ++u) {
+          const int buf = static_cast<int>(u & 1);
+          if (u >= 2 && !tc::mbar_wait(&tempty_bar[buf], static_cast<uint32_t>(((u >> 1) - 1) & 1), kWaitNs)) {
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t sa = s0 + st * kStageBytes, sb = sa + kStageA;
-          const uint64_t bdesc = tc::smem_desc(sb, kStageB / 2, 128);
+          const uint32_t dbase = tmem + static_cast<uint32_t>(buf * kSlices * kTN);
+          const int k1 = min(KS, (hh + 1) * kHalf);
+          for (int kk = hh * kHalf; kk < k1; ++kk, ++f) {
+            const int st = static_cast<int>(f % kStages);
+            if (!tc::mbar_wait(&full_bar[st], static_cast<uint32_t>((f / kStages) & 1), kWaitNs)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = s0 + st * kStageBytes, sb = sa + kStageA;
+            const uint64_t bdesc = tc::smem_desc(sb, kStageB / 2, 128);
 #pragma unroll
-          for (int a = 0; a < kSlices; ++a) {
-            // accumulator of level a+2 (a < 4: first set, columns 32 a; else second set)
-            const uint32_t d = tmem + static_cast<uint32_t>(a < 4 ? a * kTN : 8 * kTN + (a - 4) * kTN);
-            const uint32_t acc = (kk > 0 || (a != 0 && a != 4)) ? 1u : 0u;
-            tc::mma_bf16(d, tc::smem_desc(sa + a * (kTM * 16), kStageA / 2, 128), bdesc,
-                         tc::idesc_bf16(kTM, (kSlices - a) * kTN), acc);
+            for (int a = 0; a < kSlices; ++a)   // levels a+2 .. 9 at columns 32 a ..
+              tc::mma_bf16(dbase + static_cast<uint32_t>(a * kTN), tc::smem_desc(sa + a * (kTM * 16), kStageA / 2, 128),
+                           bdesc, tc::idesc_bf16(kTM, (kSlices - a) * kTN),
+                           (kk > hh * kHalf || a > 0) ? 1u : 0u);
+            tc::mma_commit(&empty_bar[st]);
           }
-          tc::mma_commit(&empty_bar[st]);
+          if (!ok) break;
+          tc::mma_commit(&tfull_bar[buf]);
         }
-        if (!ok) break;
-        tc::mma_commit(&tfull_bar);
       }
       if (!ok) abort_flag = 1;
       tc::mma_commit(&drain_bar);               // all MMAs of this CTA done before tensor memory goes
       tc::mbar_wait(&drain_bar, 0, kWaitNs);
     }
   } else {
-    // ---- epilogue: warp w reads lanes (rows) 32w .. 32w+31 ----
-    const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
-    for (int64_t n = 0; n < my_tiles; ++n) {
-      if (!tc::mbar_wait(&tfull_bar, static_cast<uint32_t>(n & 1), kWaitNs)) {
+    // ---- epilogue: warp w reads lanes (rows) 32 (w % 4) .. +31, columns 16 (w / 4) .. +15 ----
+    constexpr int kCols = kTN / 2;
+    const int quarter = warp & 3, c_lo = (warp >> 2) * kCols;
+    const uint32_t trow = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
+    int64_t u = 0;
+    bool ok = true;
+    for (int64_t slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
+      int64_t I, J;
+      if (!tile_ij(slot, nI, nJ, I, J)) continue;
+      long long vh[kCols], vl[kCols];
+#pragma unroll
+      for (int c = 0; c < kCols; ++c) { vh[c] = 0; vl[c] = 0; }
+      for (int hh = 0; hh < NH; ++hh, ++u) {
+        const int buf = static_cast<int>(u & 1);
+        if (!tc::mbar_wait(&tfull_bar[buf], static_cast<uint32_t>((u >> 1) & 1), kWaitNs)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t tb = trow + static_cast<uint32_t>(buf * kSlices * kTN);
+#pragma unroll
+        for (int cg = 0; cg < kCols / 8; ++cg) {
+          uint32_t x[8][8];
+#pragma unroll
+          for (int g = 0; g < 8; ++g) tc::tmem_ld8(tb + g * kTN + c_lo + cg * 8, x[g]);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int g = 0; g < 8; ++g) tc::tmem_keep(x[g]);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            float xs[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) xs[g] = __uint_as_float(x[g][e]);
+            add_levels(xs, vh[cg * 8 + e], vl[cg * 8 + e]);
+          }
+        }
+        // this buffer is free for the MMAs of a later half window
+        tc::fence_before_sync();
+        tc::mbar_arrive(&tempty_bar[buf]);
+      }
+      if (!ok) {
         abort_flag = 1;
         break;
       }
-      tc::fence_after_sync();
-      int64_t I, J;
-      tile_ij(blockIdx.x + n * gridDim.x, nI, I, J);
-      long long vh[kTN], vl[kTN];
-#pragma unroll
-      for (int cg = 0; cg < kTN / 8; ++cg) {
-        uint32_t x[8][8], y[4][8];
-#pragma unroll
-        for (int g = 0; g < 8; ++g) tc::tmem_ld8(trow + g * kTN + cg * 8, x[g]);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) tc::tmem_ld8(trow + 8 * kTN + g * kTN + cg * 8, y[g]);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int g = 0; g < 8; ++g) tc::tmem_keep(x[g]);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) tc::tmem_keep(y[g]);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          int lv[8];
-#pragma unroll
-          for (int g = 0; g < 8; ++g) lv[g] = level_int(x[g][e]);
-#pragma unroll
-          for (int g = 4; g < 8; ++g) lv[g] += level_int(y[g - 4][e]);
-          // levels 2..5 and 6..9 in base 256 (each level sum below 2^25 in magnitude)
-          vh[cg * 8 + e] = (static_cast<long long>(lv[0]) << 24) + (static_cast<long long>(lv[1]) << 16) +
-                           (static_cast<long long>(lv[2]) << 8) + lv[3];
-          vl[cg * 8 + e] = (static_cast<long long>(lv[4]) << 24) + (static_cast<long long>(lv[5]) << 16) +
-                           (static_cast<long long>(lv[6]) << 8) + lv[7];
-        }
-      }
-      // tensor memory is free for the next tile; the FP64 part overlaps its MMAs
-      tc::fence_before_sync();
-      tc::mbar_arrive(&tempty_bar);
-      const int64_t i = s + I * kTM + warp * 32 + lane;
+      const int64_t i = s + I * kTM + quarter * 32 + lane;
       if (i < v.m) {
         const int ei = E.eL[i - s];
+        double upd[kCols], cv[kCols];
 #pragma unroll
-        for (int c = 0; c < kTN; ++c) {
-          const int64_t j = s + J * kTN + c;
-          if (j <= i) {
-            const double upd = combine_to_double(vh[c], vl[c], ei + E.eW[j - s] - 72);
-            *v.at(static_cast<int32_t>(i), static_cast<int32_t>(j)) -= upd;
-          }
+        for (int c = 0; c < kCols; ++c) {
+          const int64_t j = s + J * kTN + c_lo + c;
+          upd[c] = j <= i ? combine_to_double(vh[c], vl[c], ei + E.eW[j - s] - 72) : 0.0;
+        }
+        // all loads first (the stores below could alias them as far as the compiler knows)
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+          const int64_t j = s + J * kTN + c_lo + c;
+          cv[c] = j <= i ? *v.at(static_cast<int32_t>(i), static_cast<int32_t>(j)) : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+          const int64_t j = s + J * kTN + c_lo + c;
+          if (j <= i) *v.at(static_cast<int32_t>(i), static_cast<int32_t>(j)) = cv[c] - upd[c];
         }
       }
     }
