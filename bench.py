@@ -285,7 +285,7 @@ def main():
     if classes["flush_tc"][1] > 0 and fl["flush_tc"] > 0:
         a = fl["flush_tc"] / (classes["flush_tc"][1] / 1e3)
         pk, src = peaks["bf16_sustained"]
-        rooflines["flush_tc"] = {"bound": "tensor", "kernel": "lf_flush_emul_kernel (bf16 mma.sync, exact splitting)",
+        rooflines["flush_tc"] = {"bound": "tensor", "kernel": "lf_flush_tc_kernel (tcgen05 bf16, exact splitting)",
                                  "achieved": a / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s", "frac": a / pk,
                                  "peak_source": src, "launches": classes["flush_tc"][0],
                                  "kernel_ms": classes["flush_tc"][1],

@@ -796,16 +796,20 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
           KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_L21, st, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
-          KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                     lf_schur_kernel<true><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
-                                                                            F.flops + KC_UPDATE));
-          if (emul)
-            launch_emul_flush(F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
-                              F.num_sms, F.timer, F.flops);
-          else
+          if (emul) {
+            // in-window and trailing updates on the tensor cores (FP64-accurate splitting)
+            launch_emul_update(true, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
+                               F.num_sms, F.timer, F.flops);
+            launch_emul_update(false, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
+                               F.num_sms, F.timer, F.flops);
+          } else {
+            KEP_LAUNCH(F.timer, KC_UPDATE, st,
+                       lf_schur_kernel<true><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
+                                                                              F.flops + KC_UPDATE));
             KEP_LAUNCH(F.timer, KC_UPDATE, st,
                        lf_schur_kernel<false><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
                                                                                 F.flops + KC_UPDATE));
+          }
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
         }
         // one more panel call finalises fronts whose last block was accepted

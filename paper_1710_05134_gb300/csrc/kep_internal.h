@@ -259,9 +259,9 @@ struct SolveLaunch {
 
 kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, int* status_bits);
 size_t emul_workspace_bytes(int64_t cap_rows);
-void launch_emul_flush(const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
-                       const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
-                       cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops);
+void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
+                        const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
+                        cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops);
 kep_status run_solve(SolveLaunch& L, const double* b, double* x);
 kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
                     const double* x, double* ya, double* yb, cudaStream_t st, int num_sms,

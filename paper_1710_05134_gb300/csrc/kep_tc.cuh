@@ -28,24 +28,31 @@ KEP_D void mbar_arrive(uint64_t* bar) {
 KEP_D void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-KEP_D bool mbar_test(uint64_t* bar, uint32_t parity) {
+// One try: returns true once the phase with the given parity has completed; otherwise the thread
+// may sleep up to about `hint_ns` (or until the phase completes) before the call returns false.
+KEP_D bool mbar_test(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 0) {
   uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
+  if (hint_ns)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
   return done != 0;
 }
-// Waits until the phase with the given parity has completed; gives up after `limit_ns` and
-// returns false.
+// Waits until the phase with the given parity has completed, sleeping between tries; gives up
+// after `limit_ns` and returns false.
 KEP_D bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
-#pragma unroll 1
-    for (int i = 0; i < 64; ++i)
-      if (mbar_test(bar, parity)) return true;
+    if (mbar_test(bar, parity, 20000u)) return true;
     if (global_ns() - t0 > limit_ns) return false;
   }
 }
@@ -107,6 +114,13 @@ KEP_D void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr)
                : "memory");
 }
+// 32 lanes x 4 consecutive 32-bit columns.
+KEP_D void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr)
+               : "memory");
+}
 // Completes the warp's outstanding tensor-memory loads.
 KEP_D void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 // Ties registers written by tmem_ld8 to a point after tmem_wait_ld, so that no use of them is
@@ -116,6 +130,9 @@ KEP_D void tmem_keep(uint32_t (&v)[8]) {
                : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
                :
                : "memory");
+}
+KEP_D void tmem_keep(uint32_t (&v)[4]) {
+  asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]) : : "memory");
 }
 
 }  // namespace tc

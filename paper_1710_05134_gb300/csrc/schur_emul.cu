@@ -5,9 +5,10 @@
 // whose products the tensor cores sum exactly (an error-free splitting in the manner of Ozaki et
 // al.):
 //
-//  * column balancing: column c of L is scaled by 2^{-u_c} and column c of W by 2^{u_c} (u_c from
-//    the two columns' largest exponents), which leaves every product unchanged and keeps the
-//    spread of D out of the rows;
+//  * column balancing: column c of L is scaled by 2^{-u_c} and column c of W by 2^{u_c}, u_c half
+//    the exponent of the pivot's magnitude with the sign reversed (max |W(., c)| is about
+//    |D_c| max |L(., c)|), which leaves every product unchanged and keeps the spread of D out of
+//    the rows;
 //  * every row is scaled by a power of two 2^e with |x| < 2^{e-1} for all its entries, and
 //    |x| 2^{8-e} (< 128) is written in balanced base-256 digits, sum_a d_a 256^{1-a}, a = 1..8,
 //    d_1 in [0, 128], d_a in [-128, 127] otherwise, cut from the double's significand with integer
@@ -48,7 +49,7 @@ constexpr uint32_t kStageA = 2 * kSlices * kTM * 16;   // [k-block 2][slice 8][r
 constexpr uint32_t kStageB = 2 * kSlices * kTN * 16;   // [k-block 2][slice 8][row 32][16 B]
 constexpr uint32_t kStageBytes = kStageA + kStageB;
 constexpr size_t kFlushSmem = static_cast<size_t>(kStages) * kStageBytes + 1024;
-constexpr int kEpiWarps = 8;                  // epilogue: warp w reads lanes 32 (w % 4), columns 16 (w / 4)
+constexpr int kEpiWarps = 16;                 // epilogue: warp w reads lanes 32 (w % 4), columns 8 (w / 4)
 constexpr int kFlushThreads = (kEpiWarps + 2) * 32;   // + one copy warp, one MMA-issue warp
 constexpr uint32_t kTmemCols = 512;           // 2 buffers x 8 level accumulators x 32 columns
 constexpr int kHalf = 8;                      // 16-column steps per accumulation (128 columns)
@@ -58,11 +59,8 @@ constexpr int kNoExp = -(1 << 20);            // row maximum of an all-zero row
 struct EmulArgs {
   __nv_bfloat16* Ls;   // digits of the balanced, scaled L rows, tile-contiguous (ldig_off)
   __nv_bfloat16* Ws;   // digits of the W rows (wdig_off)
-  double* Wv;          // [kWindow][cap_rows] W = L D (column-major, like L)
   int32_t* eL;         // [R] row scale exponents
   int32_t* eW;
-  int32_t* cexp;       // [2][kWindow] largest biased exponent of |L(., c)| and |W(., c)|
-  int64_t cap_rows;
   int64_t R;           // rows of the digit arrays (a multiple of kTM, >= rows + kTM)
 };
 
@@ -93,11 +91,17 @@ KEP_D double wval(const double* L, int64_t ld, int64_t i, int32_t c, const doubl
   return L[static_cast<int64_t>(c - 1) * ld + i] * De[c - 1] + x * Dd[c];
 }
 
-KEP_D int balance_shift(const EmulArgs& E, int32_t c) {
-  const int ex = E.cexp[c], ey = E.cexp[kWindow + c];
-  if (ex == 0 || ey == 0) return 0;
-  const int d = ex - ey;
-  return d >= 0 ? d / 2 : -((-d + 1) / 2);     // floor(d / 2)
+// Balancing shift of pivot column c: floor(-e/2) for the exponent e of its pivot's magnitude (the
+// larger entry of a 2x2 block), 0 for a zero pivot.
+KEP_D int balance_shift(const double* Dd, const double* De, const int8_t* pv, int32_t c) {
+  const int8_t pt = pv[c];
+  const double d = pt == 1 ? fabs(Dd[c])
+                 : pt == 2 ? fmax(fabs(Dd[c]), fabs(De[c]))
+                           : fmax(fabs(De[c - 1]), fabs(Dd[c]));
+  const int e = bexp(d);
+  if (e == 0) return 0;
+  const int n = 1023 - e;
+  return n >= 0 ? n / 2 : -((-n + 1) / 2);       // floor(n / 2)
 }
 
 // 64-bit fixed point floor(|x| 2^{-u} 2^{8-e} 2^56) of a normal double x (0 for zero/subnormal);
@@ -127,65 +131,51 @@ KEP_D void balanced_digits(double x, int u, int e, uint32_t (&d)[kSlices]) {
   }
 }
 
-// Pass 1: W = L D for the window's columns over the rows [we, m), and per column the largest
-// exponents of |L| and |W| (CTAs over row chunks, one thread per column).
-__global__ void __launch_bounds__(256) lf_colmax_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
-                                                        int32_t b, EmulArgs E) {
-  if (W.done[b] || !W.flush[b]) return;
-  const int32_t t = lf[b];
-  const int32_t d_in = S.d_in[t];
-  const int32_t m = T.m_sym[t] + d_in;
-  const int32_t c0 = W.ws[b], c1 = W.kend[b], s = W.we[b];
-  const int32_t r = c1 - c0;
-  if (r <= 0 || s >= m) return;
-  const double* L = S.F + T.front_off[t];
-  const int64_t ld = T.m_alloc[t];
-  const int64_t po = T.piv_off[t];
-  const int64_t rows = m - s;
-  // threads over rows (coalesced), loop over the window's columns
-  const int64_t chunk = (rows + gridDim.x - 1) / gridDim.x;
-  const int64_t r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
-  __shared__ int sx[kWindow], sy[kWindow];
-  for (int32_t c = threadIdx.x; c < kWindow; c += blockDim.x) { sx[c] = 0; sy[c] = 0; }
-  __syncthreads();
-  for (int32_t c = 0; c < r; ++c) {
-    int mx = 0, my = 0;
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-      const int64_t i = s + row;
-      const double x = L[static_cast<int64_t>(c0 + c) * ld + i];
-      const double y = wval(L, ld, i, c0 + c, S.Dd + po, S.De + po, S.piv + po);
-      E.Wv[static_cast<int64_t>(c) * E.cap_rows + row] = y;
-      mx = max(mx, bexp(x));
-      my = max(my, bexp(y));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      my = max(my, __shfl_xor_sync(0xffffffffu, my, o));
-    }
-    if ((threadIdx.x & 31) == 0) { atomicMax(&sx[c], mx); atomicMax(&sy[c], my); }
+// The update a launch performs for batch entry b this step, false when there is none.  Window
+// update (kWin): the pivots just accepted, columns [c0, c1) = [k, k + q), applied to the rest of
+// the pivot window, columns [c1, we).  Flush: the window's pivots [ws, kend) applied to the
+// trailing matrix, columns [we, m).  Rows [s, m) of L and rows [s, ce) of W take part, and C(i, j)
+// is updated for j in [s, ce), i in [j, m).
+template <bool kWin>
+KEP_D bool emul_range(const LargeWork& W, int32_t b, int32_t m, int32_t& c0, int32_t& c1, int32_t& s, int32_t& ce) {
+  if (W.done[b]) return false;
+  if (kWin) {
+    c0 = W.k[b];
+    c1 = c0 + W.q[b];
+    s = c1;
+    ce = min(W.we[b], m);
+  } else {
+    if (!W.flush[b]) return false;
+    c0 = W.ws[b];
+    c1 = W.kend[b];
+    s = W.we[b];
+    ce = m;
   }
-  __syncthreads();
-  for (int32_t c = threadIdx.x; c < r; c += blockDim.x) {
-    atomicMax(&E.cexp[c], sx[c]);
-    atomicMax(&E.cexp[kWindow + c], sy[c]);
-  }
+  return c1 > c0 && s < ce;
 }
 
-// Pass 2: per row, the scale exponents of the balanced L and W rows, then the digits of every
-// entry of the window (zero up to the next multiple of 16 columns).  Thread (row, half): the
-// half's 8-column blocks; each 16-byte store holds one row's 8 digits of one slice and block,
-// consecutive threads writing consecutive rows.
+// Digits: per row, the scale exponents of the balanced L and W rows (W = L D formed on the fly),
+// then the digits of every entry of the update's columns (zero up to the next multiple of 16
+// columns).  Thread (row, half): the half's 8-column blocks; each 16-byte store holds one row's 8
+// digits of one slice and block, consecutive threads writing consecutive rows.
 constexpr int kSRows = 128;
+template <bool kWin>
 __global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
                                                        int32_t b, EmulArgs E) {
   __shared__ int smx[2][2][kSRows];
-  if (W.done[b] || !W.flush[b]) return;
+  __shared__ int su[kWindow];
   const int32_t t = lf[b];
-  const int32_t d_in = S.d_in[t];
-  const int32_t m = T.m_sym[t] + d_in;
-  const int32_t c0 = W.ws[b], c1 = W.kend[b], s = W.we[b];
+  const int32_t m = T.m_sym[t] + S.d_in[t];
+  int32_t c0, c1, s, ce;
+  if (!emul_range<kWin>(W, b, m, c0, c1, s, ce)) return;
   const int32_t r = c1 - c0;
-  if (r <= 0 || s >= m) return;
+  const int64_t wrows = ce - s;
+  const int64_t po = T.piv_off[t];
+  const double* Dd = S.Dd + po;
+  const double* De = S.De + po;
+  const int8_t* pv = S.piv + po;
+  for (int32_t c = threadIdx.x; c < r; c += blockDim.x) su[c] = balance_shift(Dd, De, pv, c0 + c);
+  __syncthreads();
   const int32_t nq = (r + 15) / 16 * 2;          // 8-column blocks covering the padded window
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
@@ -197,9 +187,9 @@ __global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot
     int ex = kNoExp, ey = kNoExp;
     if (ok)
       for (int32_t c = half; c < r; c += 2) {
-        const int u = balance_shift(E, c);
+        const int u = su[c];
         const int bx = bexp(L[static_cast<int64_t>(c0 + c) * ld + s + row]);
-        const int by = bexp(E.Wv[static_cast<int64_t>(c) * E.cap_rows + row]);
+        const int by = row < wrows ? bexp(wval(L, ld, s + row, c0 + c, Dd, De, pv)) : 0;
         if (bx) ex = max(ex, bx - u);
         if (by) ey = max(ey, by + u);
       }
@@ -214,7 +204,7 @@ __global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot
     if (half == 0) { E.eL[row] = el; E.eW[row] = ew; }
     for (int32_t q = half; q < nq; q += 2) {
 #pragma unroll 1
-      for (int which = 0; which < 2; ++which) {
+      for (int which = 0; which < (row < wrows ? 2 : 1); ++which) {
         uint32_t pk[kSlices][4];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -222,9 +212,9 @@ __global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot
           double x = 0.0;
           int u = 0;
           if (c < r) {
-            u = balance_shift(E, c);
+            u = su[c];
             x = which == 0 ? L[static_cast<int64_t>(c0 + c) * ld + s + row]
-                           : E.Wv[static_cast<int64_t>(c) * E.cap_rows + row];
+                           : wval(L, ld, s + row, c0 + c, Dd, De, pv);
           }
           uint32_t d[kSlices];
           balanced_digits(x, which == 0 ? u : -u, which == 0 ? el : ew, d);
@@ -270,38 +260,31 @@ KEP_D bool tile_ij(int64_t t, int64_t nI, int64_t nJ, int64_t& I, int64_t& J) {
   return false;
 }
 
-// (hi 2^32 + lo) 2^scale rounded to the nearest double (ties to even), integer operations only;
-// |hi|, |lo| < 2^62.  Results below the normal range are flushed to zero.
-KEP_D double combine_to_double(long long hi, long long lo, int scale) {
-  unsigned long long L = (static_cast<unsigned long long>(hi) << 32) + static_cast<unsigned long long>(lo);
-  const unsigned long long carry = L < (static_cast<unsigned long long>(hi) << 32) ? 1ull : 0ull;
-  const long long H = (hi >> 32) + (lo >> 63) + static_cast<long long>(carry);
-  const bool neg = H < 0;
-  unsigned long long uh = static_cast<unsigned long long>(H);
-  if (neg) {
-    L = ~L + 1ull;
-    uh = ~uh + (L == 0ull ? 1ull : 0ull);
+// C - (hi 2^32 + lo) 2^scale for |hi|, |lo| < 2^52.  The integer V = hi 2^32 + lo is brought to
+// 64 bits as V = +-(T + f) 2^sh with an integer T < 2^56 and 0 <= f < 1; T and a sticky bit for
+// f != 0 then go through one correctly rounded int64 -> double conversion (2T + sticky has at
+// least 55 significant bits whenever f can be nonzero, so the sticky bit only breaks ties, which
+// rounds V to nearest), the power of two enters the exponent field, and one FP64 subtraction
+// follows.  Scaled values below 2^-1000 are treated as zero.
+KEP_D double sub_scaled(double C, long long hi, long long lo, int scale) {
+  const unsigned long long ah = static_cast<unsigned long long>(hi < 0 ? -hi : hi);
+  const int sh = max(0, 41 - __clzll(static_cast<long long>(ah)));   // bit length of |hi| minus 23
+  long long T2;                                  // 2T + sticky, with the sign of V
+  if (sh == 0) {                                 // |hi| < 2^23: V is exact in 64 bits, |V| < 2^56
+    T2 = (static_cast<long long>(static_cast<unsigned long long>(hi) << 32) + lo) * 2;
+  } else {                                       // V has the sign of hi
+    const long long h2 = hi < 0 ? -hi : hi, l2 = hi < 0 ? -lo : lo;
+    const long long T = (h2 << (32 - sh)) + (l2 >> sh);
+    const long long st = (static_cast<unsigned long long>(l2) & ((1ull << sh) - 1)) != 0ull ? 1 : 0;
+    T2 = hi < 0 ? -(2 * T + st) : 2 * T + st;
   }
-  int lz;
-  unsigned long long top, rest;
-  if (uh != 0ull) {
-    lz = __clzll(static_cast<long long>(uh));
-    top = lz ? (uh << lz) | (L >> (64 - lz)) : uh;
-    rest = L << lz;
-  } else {
-    if (L == 0ull) return 0.0;
-    lz = 64 + __clzll(static_cast<long long>(L));
-    top = L << (lz - 64);
-    rest = 0ull;
-  }
-  unsigned long long mant = top >> 11;          // 53 bits, leading one at bit 52
-  const unsigned long long rbit = (top >> 10) & 1ull;
-  const bool sticky = (top & 0x3ffull) != 0ull || rest != 0ull;
-  mant += rbit & ((sticky ? 1ull : 0ull) | (mant & 1ull));
-  const int E = 127 - lz + scale + 1023;        // biased exponent of the leading bit
-  if (E <= 0) return 0.0;
-  const unsigned long long bits = (static_cast<unsigned long long>(E - 1) << 52) + mant;
-  return __longlong_as_double(static_cast<long long>(bits | (neg ? (1ull << 63) : 0ull)));
+  const double d = __ll2double_rn(T2);           // V 2^{1-sh}, rounded once
+  const int e = sh - 1 + scale;                  // d 2^e = V 2^scale
+  const long long db = __double_as_longlong(d);
+  const int ed = static_cast<int>((db >> 52) & 0x7ff);
+  if (ed == 0 || ed + e < 24) return C;          // zero, or below 2^-1000
+  if (ed + e > 2046) return C - copysign(__longlong_as_double(0x7ff0000000000000ll), d);
+  return C - __longlong_as_double(db + (static_cast<long long>(e) << 52));
 }
 
 // Exact integer from an FP32 level sum that holds an integer (|v| <= 2^24).
@@ -310,21 +293,26 @@ KEP_D int level_int(float v) { return __float2int_rn(v); }
 // The level sums of one entry over one half window (x[g]: level g+2, |x[g]| <= 2^24) added in
 // base 256 to levels 2..5 (vh) and 6..9 (vl).  Fast path: with every level sum at most 2^22 in
 // magnitude, v + 1.5 2^23 lands in [2^23, 2^24], where the float's bits minus those of 1.5 2^23
-// are the integer v; otherwise (rare) each sum is converted on its own.
+// are the integer v (the constant offsets are taken out in one step); otherwise (rare) each sum
+// is converted on its own.
 constexpr float kMagic = 12582912.0f;          // 1.5 2^23
 constexpr int kMagicBits = 0x4B400000;
 KEP_D void add_levels(const float (&x)[8], long long& vh, long long& vl) {
-  int l[8];
-  unsigned worst = 0;
+  float big = 0.f;
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    l[g] = __float_as_int(x[g] + kMagic) - kMagicBits;
-    worst = max(worst, static_cast<unsigned>(l[g] + (1 << 22)));   // in [0, 2^23] when exact
-  }
-  if (worst <= (1u << 23)) {
-    vh += static_cast<long long>(l[0] * 256 + l[1]) * 65536 + (l[2] * 256 + l[3]);
-    vl += static_cast<long long>(l[4] * 256 + l[5]) * 65536 + (l[6] * 256 + l[7]);
+  for (int g = 0; g < 8; ++g) big = fmaxf(big, fabsf(x[g]));
+  if (big <= 4194304.0f) {
+    unsigned b[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) b[g] = __float_as_uint(x[g] + kMagic);
+    // (b0 - K) 256 + (b1 - K) = b0 256 + b1 - 257 K: exact modulo 2^32, and the result fits
+    constexpr unsigned kOff = 257u * static_cast<unsigned>(kMagicBits);
+    const int p0 = static_cast<int>(b[0] * 256u + b[1] - kOff), p1 = static_cast<int>(b[2] * 256u + b[3] - kOff);
+    const int p2 = static_cast<int>(b[4] * 256u + b[5] - kOff), p3 = static_cast<int>(b[6] * 256u + b[7] - kOff);
+    vh += static_cast<long long>(p0) * 65536 + p1;
+    vl += static_cast<long long>(p2) * 65536 + p3;
   } else {
+    int l[8];
 #pragma unroll
     for (int g = 0; g < 8; ++g) l[g] = level_int(x[g]);
     vh += (static_cast<long long>(l[0]) << 24) + (static_cast<long long>(l[1]) << 16) +
@@ -334,6 +322,7 @@ KEP_D void add_levels(const float (&x)[8], long long& vh, long long& vl) {
   }
 }
 
+template <bool kWin>
 __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTables T, FactorSlot S, double* cbpool,
                                                                        LargeWork W, const int32_t* lf, int32_t b,
                                                                        EmulArgs E, unsigned long long* flops) {
@@ -343,26 +332,24 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  if (W.done[b] || !W.flush[b]) return;
-  if (blockIdx.x == 0)                        // column exponents are used up: clear for the next window
-    for (int32_t c = threadIdx.x; c < 2 * kWindow; c += blockDim.x) E.cexp[c] = 0;
   const int32_t t = lf[b];
-  const int32_t d_in = S.d_in[t];
-  const FrontView v = front_view(T, S, cbpool, t, d_in);
-  const int32_t c0 = W.ws[b], c1 = W.kend[b], s = W.we[b];
+  const FrontView v = front_view(T, S, cbpool, t, S.d_in[t]);
+  int32_t c0, c1, s, ce;
+  if (!emul_range<kWin>(W, b, v.m, c0, c1, s, ce)) return;
   const int32_t r = c1 - c0;
-  if (r <= 0 || s >= v.m) return;
   const int KS = (r + 15) / 16;               // 16-column steps
   const int NH = (KS + kHalf - 1) / kHalf;    // accumulation halves
-  const int64_t h = v.m - s;
-  const int64_t nI = (h + kTM - 1) / kTM, nJ = (h + kTN - 1) / kTN;
+  const int64_t h = v.m - s, w = ce - s;
+  const int64_t nI = (h + kTM - 1) / kTM, nJ = (w + kTN - 1) / kTN;
   const int64_t nslots = tile_slots(nI, nJ);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // tensor-core work issued (2 nI (nI - 1) + nJ tiles), and the FP64 update it stands for
-    const int64_t ntiles = 2 * nI * (nI - 1) + nJ;
+    // tensor-core work issued (i-block I has min(4I + 4, nJ) tiles), and the FP64 update it
+    // stands for (2 r per updated entry)
+    const int64_t c = min(nI, nJ / 4);
+    const int64_t ntiles = 2 * c * (c + 1) + (nI - c) * nJ;
     atomicAdd(&flops[KC_FLUSH_TC],
               static_cast<unsigned long long>(2ll * kTM * (kSlices * (kSlices + 1) / 2) * kTN * 16 * KS * ntiles));
-    atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (h * (h + 1) / 2)));
+    atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (w * h - w * (w - 1) / 2)));
   }
   if (blockIdx.x >= nslots) return;
   unsigned char* sbase =
@@ -438,9 +425,10 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
             tc::fence_after_sync();
             const uint32_t sa = s0 + st * kStageBytes, sb = sa + kStageA;
             const uint64_t bdesc = tc::smem_desc(sb, kStageB / 2, 128);
+            const uint64_t adesc = tc::smem_desc(sa, kStageA / 2, 128);
 #pragma unroll
-            for (int a = 0; a < kSlices; ++a)   // levels a+2 .. 9 at columns 32 a ..
-              tc::mma_bf16(dbase + static_cast<uint32_t>(a * kTN), tc::smem_desc(sa + a * (kTM * 16), kStageA / 2, 128),
+            for (int a = 0; a < kSlices; ++a)   // levels a+2 .. 9 at columns 32 a ..; slice a of L
+              tc::mma_bf16(dbase + static_cast<uint32_t>(a * kTN), adesc + static_cast<uint64_t>(a * (kTM * 16 / 16)),
                            bdesc, tc::idesc_bf16(kTM, (kSlices - a) * kTN),
                            (kk > hh * kHalf || a > 0) ? 1u : 0u);
             tc::mma_commit(&empty_bar[st]);
@@ -454,8 +442,8 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
       tc::mbar_wait(&drain_bar, 0, kWaitNs);
     }
   } else {
-    // ---- epilogue: warp w reads lanes (rows) 32 (w % 4) .. +31, columns 16 (w / 4) .. +15 ----
-    constexpr int kCols = kTN / 2;
+    // ---- epilogue: warp w reads lanes (rows) 32 (w % 4) .. +31, columns 8 (w / 4) .. +7 ----
+    constexpr int kCols = kTN / (kEpiWarps / 4);
     const int quarter = warp & 3, c_lo = (warp >> 2) * kCols;
     const uint32_t trow = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     int64_t u = 0;
@@ -463,6 +451,22 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
     for (int64_t slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
       int64_t I, J;
       if (!tile_ij(slot, nI, nJ, I, J)) continue;
+      // this thread's row and its entries of C (column stride cs from the entry of column j0; the
+      // columns of a tile lie on one side of p except at one j-block of the front); they are
+      // brought into L2 while the MMAs run
+      const int64_t i = s + I * kTM + quarter * 32 + lane;
+      const int64_t j0 = s + J * kTN + c_lo;
+      const bool rowok = i < v.m && j0 <= i;
+      const bool split = j0 < v.p && j0 + kCols > v.p;
+      double* cp = rowok ? v.at(static_cast<int32_t>(i), static_cast<int32_t>(j0)) : nullptr;
+      const int64_t cs = j0 < v.p ? v.ldL : v.c;
+      auto centry = [&](int c) {
+        return split ? v.at(static_cast<int32_t>(i), static_cast<int32_t>(j0 + c)) : cp + c * cs;
+      };
+      if (rowok)
+#pragma unroll
+        for (int c = 0; c < kCols; ++c)
+          if (j0 + c <= i && j0 + c < ce) asm volatile("prefetch.global.L2 [%0];" ::"l"(centry(c)));
       long long vh[kCols], vl[kCols];
 #pragma unroll
       for (int c = 0; c < kCols; ++c) { vh[c] = 0; vl[c] = 0; }
@@ -475,19 +479,19 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
         tc::fence_after_sync();
         const uint32_t tb = trow + static_cast<uint32_t>(buf * kSlices * kTN);
 #pragma unroll
-        for (int cg = 0; cg < kCols / 8; ++cg) {
-          uint32_t x[8][8];
+        for (int cg = 0; cg < kCols / 4; ++cg) {
+          uint32_t x[8][4];
 #pragma unroll
-          for (int g = 0; g < 8; ++g) tc::tmem_ld8(tb + g * kTN + c_lo + cg * 8, x[g]);
+          for (int g = 0; g < 8; ++g) tc::tmem_ld4(tb + g * kTN + c_lo + cg * 4, x[g]);
           tc::tmem_wait_ld();
 #pragma unroll
           for (int g = 0; g < 8; ++g) tc::tmem_keep(x[g]);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
+          for (int e = 0; e < 4; ++e) {
             float xs[8];
 #pragma unroll
             for (int g = 0; g < 8; ++g) xs[g] = __uint_as_float(x[g][e]);
-            add_levels(xs, vh[cg * 8 + e], vl[cg * 8 + e]);
+            add_levels(xs, vh[cg * 4 + e], vl[cg * 4 + e]);
           }
         }
         // this buffer is free for the MMAs of a later half window
@@ -498,26 +502,15 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
         abort_flag = 1;
         break;
       }
-      const int64_t i = s + I * kTM + quarter * 32 + lane;
-      if (i < v.m) {
-        const int ei = E.eL[i - s];
-        double upd[kCols], cv[kCols];
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-          const int64_t j = s + J * kTN + c_lo + c;
-          upd[c] = j <= i ? combine_to_double(vh[c], vl[c], ei + E.eW[j - s] - 72) : 0.0;
-        }
+      if (rowok) {
+        const int ei = E.eL[i - s] - 72;
         // all loads first (the stores below could alias them as far as the compiler knows)
+        double cv[kCols];
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-          const int64_t j = s + J * kTN + c_lo + c;
-          cv[c] = j <= i ? *v.at(static_cast<int32_t>(i), static_cast<int32_t>(j)) : 0.0;
-        }
+        for (int c = 0; c < kCols; ++c) cv[c] = (j0 + c <= i && j0 + c < ce) ? *centry(c) : 0.0;
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-          const int64_t j = s + J * kTN + c_lo + c;
-          if (j <= i) *v.at(static_cast<int32_t>(i), static_cast<int32_t>(j)) = cv[c] - upd[c];
-        }
+        for (int c = 0; c < kCols; ++c)
+          if (j0 + c <= i && j0 + c < ce) *centry(c) = sub_scaled(cv[c], vh[c], vl[c], ei + E.eW[j0 + c - s]);
       }
     }
   }
@@ -532,15 +525,12 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
 
 EmulArgs emul_args(void* ws, int64_t cap_rows) {
   EmulArgs E;
-  E.cap_rows = cap_rows;
   E.R = digit_pitch(cap_rows);
   const int64_t plane = static_cast<int64_t>(kSlices) * kKB * E.R * 8;
   E.Ls = static_cast<__nv_bfloat16*>(ws);
   E.Ws = E.Ls + plane;
-  E.Wv = reinterpret_cast<double*>(E.Ws + plane);
-  E.eL = reinterpret_cast<int32_t*>(E.Wv + static_cast<int64_t>(kWindow) * cap_rows);
+  E.eL = reinterpret_cast<int32_t*>(E.Ws + plane);
   E.eW = E.eL + E.R;
-  E.cexp = E.eW + E.R;
   return E;
 }
 
@@ -548,27 +538,31 @@ EmulArgs emul_args(void* ws, int64_t cap_rows) {
 
 size_t emul_workspace_bytes(int64_t cap_rows) {
   const int64_t R = digit_pitch(cap_rows);
-  return 2ull * kSlices * kKB * R * 8 * sizeof(__nv_bfloat16) + kWindow * cap_rows * sizeof(double) +
-         2ull * R * sizeof(int32_t) + 2ull * kWindow * sizeof(int32_t) + 512;
+  return 2ull * kSlices * kKB * R * 8 * sizeof(__nv_bfloat16) + 2ull * R * sizeof(int32_t) + 512;
 }
 
-// Slice and flush for batch entry b (a front factored alone); the kernels return at once unless
-// the front's window flush is due this step.
-void launch_emul_flush(const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
-                       const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
-                       cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops) {
+// Window update (window = true) or flush for batch entry b (a front factored alone); the kernels
+// return at once unless the front has that update due this step.
+void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
+                        const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
+                        cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lf_flush_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
+    cudaFuncSetAttribute(lf_flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
+    cudaFuncSetAttribute(lf_flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
     attr_set = true;
   }
   const EmulArgs E = emul_args(ws, cap_rows);
   const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + kSRows - 1) / kSRows, num_sms * 4)));
-  const int gc = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + 255) / 256, num_sms * 2)));
-  KEP_LAUNCH(timer, KC_SLICE, st, lf_colmax_kernel<<<gc, 256, 0, st>>>(T, S, W, lf, b, E));
-  KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
-  KEP_LAUNCH(timer, KC_FLUSH_TC, st,
-             lf_flush_tc_kernel<<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, b, E, flops));
+  if (window) {
+    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<true><<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
+    KEP_LAUNCH(timer, KC_FLUSH_TC, st,
+               lf_flush_tc_kernel<true><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, b, E, flops));
+  } else {
+    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<false><<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
+    KEP_LAUNCH(timer, KC_FLUSH_TC, st,
+               lf_flush_tc_kernel<false><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, b, E, flops));
+  }
 }
 
 }  // namespace kep
