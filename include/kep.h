@@ -217,6 +217,10 @@ typedef struct {
 /* Enable (1) or disable (0) per-launch event timing; synchronises ctx's stream. */
 kep_status kep_set_timing(kep_ctx* ctx, int enable);
 
+/* Restrict event timing to the classes whose bit is set in mask (bit c: class c; all bits set by
+ * default); launch counts and flops are kept for every class.  Synchronises ctx's stream. */
+kep_status kep_set_timing_classes(kep_ctx* ctx, unsigned int mask);
+
 /* Copy the counters into *out; reset (1) zeroes them afterwards.  Synchronises ctx's stream. */
 kep_status kep_get_timing(kep_ctx* ctx, kep_timing* out, int reset);
 

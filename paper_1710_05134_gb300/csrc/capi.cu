@@ -443,6 +443,14 @@ kep_status kep_set_timing(kep_ctx* c, int enable) {
   return KEP_OK;
 }
 
+kep_status kep_set_timing_classes(kep_ctx* c, unsigned int mask) {
+  if (!c) return KEP_ERR_INVALID;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  c->timer.collect();
+  c->timer.mask = mask;
+  return KEP_OK;
+}
+
 kep_status kep_get_timing(kep_ctx* c, kep_timing* out, int reset) {
   if (!c || !out) return KEP_ERR_INVALID;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;

@@ -35,6 +35,7 @@ enum KClass : int {
 
 struct Timer {
   bool enabled = false;
+  uint32_t mask = 0xffffffffu;        // classes timed while enabled
   int64_t launches[KC_COUNT] = {};
   double ms[KC_COUNT] = {};
   std::vector<cudaEvent_t> pool;
@@ -51,7 +52,7 @@ struct Timer {
   // record the start event of a launch of class cls (returns false when disabled)
   bool begin(int cls, cudaStream_t s) {
     ++launches[cls];
-    if (!enabled) return false;
+    if (!enabled || !((mask >> cls) & 1u)) return false;
     cudaEventRecord(next_event(), s);
     pending_cls.push_back(cls);
     return true;

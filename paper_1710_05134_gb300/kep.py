@@ -23,6 +23,7 @@ KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 # symbols declared in include/kep.h
 EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
+            "kep_set_timing_classes",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
             "kep_set_schur_mode"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
@@ -102,6 +103,7 @@ def lib() -> ctypes.CDLL:
         L.kep_kth_eigenpair.argtypes = [P, I64, ctypes.POINTER(Params), ctypes.POINTER(D), P,
                                         ctypes.POINTER(Report)]
         L.kep_set_timing.argtypes = [P, I]
+        L.kep_set_timing_classes.argtypes = [P, ctypes.c_uint]
         L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
         L.kep_dense_inertia_noalloc.argtypes = [I64, P, P, I64, D, P, P]
         L.kep_dense_inertia_noalloc.restype = I
@@ -112,7 +114,8 @@ def lib() -> ctypes.CDLL:
         L.kep_status_str.argtypes = [I]
         L.kep_status_str.restype = ctypes.c_char_p
         for name in ["kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
-                     "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing", "kep_get_timing"]:
+                     "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing", "kep_get_timing",
+                     "kep_set_timing_classes"]:
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -215,8 +218,11 @@ class Problem:
         _check(lib().kep_set_schur_mode(self._h, KEP_SCHUR_EMULATED if emulated else KEP_SCHUR_FP64,
                                         int(min_front)), "kep_set_schur_mode")
 
-    def set_timing(self, enable: bool):
-        """Per-launch CUDA-event timing of this context's kernels (launch counts are always kept)."""
+    def set_timing(self, enable: bool, classes=None):
+        """Per-launch CUDA-event timing of this context's kernels (launch counts are always kept);
+        classes: names from KERNEL_CLASSES to time (default: all)."""
+        mask = 0xFFFFFFFF if classes is None else sum(1 << KERNEL_CLASSES.index(c) for c in classes)
+        _check(lib().kep_set_timing_classes(self._h, mask), "kep_set_timing_classes")
         _check(lib().kep_set_timing(self._h, 1 if enable else 0), "kep_set_timing")
 
     def timing(self, reset: bool = False) -> dict:
