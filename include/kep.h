@@ -146,8 +146,8 @@ kep_status kep_get_info(const kep_ctx* ctx, kep_info* info);
 kep_status kep_set_stream(kep_ctx* ctx, void* stream);
 
 /*
- * kep_factor - numeric LDL^T of A - sigma*B (Algorithm 1', lines "LDL^H <- PQ(A - sigma B)Q^T P^T"
- * and "nu := nu_0(D, I)"), and its inertia.
+ * kep_factor - numeric LDL^T of the permuted A - sigma*B and the inertia count read off D, the
+ * factorization step of Algorithm 1' (Section 2.1: Sylvester's law of inertia).
  *
  * The factor stays in ctx for kep_solve until the next kep_factor.  out->neg is nu_sigma(A, B),
  * the number of eigenvalues below sigma.  Returns KEP_ERR_SINGULAR (with *out filled) when an
