@@ -785,11 +785,15 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
                    lf_extend_kernel<<<dim3(grid_cap(max_m, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 128, 0, st>>>(
                        F.T, F.S, F.cbpool, B, s));
       const int64_t rowtiles = (max_m + kRowTile - 1) / kRowTile;
-      const int gx_rows = grid_cap(rowtiles, std::max<int64_t>(1, (target + nb - 1) / nb));
-      const int gx_apply = grid_cap(rowtiles + max_p / 32 + 2, std::max<int64_t>(1, (target + nb - 1) / nb));
+      // CTAs per front: enough for the largest front of the batch (fronts of one level differ in
+      // size by up to ~10x; CTAs beyond a front's own work return at once)
+      const int64_t per_front = std::max<int64_t>((target + nb - 1) / nb, F.num_sms);
+      const int gx_rows = grid_cap(rowtiles, per_front);
+      const int gx_apply = grid_cap(rowtiles + max_p / 32 + 2, per_front);
       const int64_t tb = (max_m + kTile - 1) / kTile + 1;
-      const int gx_upd = grid_cap(tb * (tb + 1) / 2, std::max<int64_t>(1, (F.num_sms * 4 + nb - 1) / nb));
-      const int gx_win = grid_cap(tb * (kWindow / kTile + 1), std::max<int64_t>(1, (F.num_sms * 4 + nb - 1) / nb));
+      const int64_t per_front_upd = std::max<int64_t>((F.num_sms * 4 + nb - 1) / nb, 2 * F.num_sms);
+      const int gx_upd = grid_cap(tb * (tb + 1) / 2, per_front_upd);
+      const int gx_win = grid_cap(tb * (kWindow / kTile + 1), per_front_upd);
       int64_t steps = (max_p + kPanel - 1) / kPanel + 1;
       while (true) {
         for (int64_t it = 0; it < steps; ++it) {
