@@ -133,14 +133,17 @@ __global__ void lf_extend_kernel(FrontTables T, FactorSlot S, double* cbpool, Ba
 // ------------------------------------------------------------------------------------------
 // pivoting panel: Bunch-Kaufman on the w x w diagonal block (one warp)
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) lf_panel_kernel(FrontTables T, FactorSlot S, LargeWork W,
-                                                      Batch B) {
+constexpr int kPanelThreads = 128;   // the pivot search runs in warp 0, the block updates in all four
+
+__global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, FactorSlot S, LargeWork W,
+                                                                 Batch B) {
   __shared__ double Bk[kPanel][kPanel + 1];
   __shared__ int32_t perm[kPanel];
-  __shared__ double dd[kPanel], de[kPanel];
+  __shared__ double dd[kPanel], de[kPanel], lv0[kPanel], lv1[kPanel];
   __shared__ int8_t pt[kPanel];
+  __shared__ int32_t s_kind, s_piv;
   const int32_t b = B.e0 + blockIdx.x;
-  const int32_t lane = threadIdx.x;
+  const int32_t tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
   if (W.done[b]) return;
   const int32_t t = B.lf[b];
   const int32_t d_in = S.d_in[t];
@@ -148,105 +151,119 @@ __global__ void __launch_bounds__(32) lf_panel_kernel(FrontTables T, FactorSlot 
   const int32_t k = W.k[b] + W.q[b];
   int32_t we = W.we[b];
   if (k < p && (k >= we || W.reset[b])) we = min(k + kWindow, p);   // open a new pivot window
-  __syncwarp();
-  if (lane == 0) {
+  __syncthreads();
+  if (tid == 0) {
     W.k[b] = k; W.q[b] = 0; W.flush[b] = 0;
     if (k < p && (k >= W.we[b] || W.reset[b])) { W.ws[b] = k; W.we[b] = we; W.reset[b] = 0; }
   }
   if (k >= p) {
-    if (lane == 0) { W.done[b] = 1; S.nelim[t] = k; S.d_out[t] = p - k; W.w[b] = 0; }
+    if (tid == 0) { W.done[b] = 1; S.nelim[t] = k; S.d_out[t] = p - k; W.w[b] = 0; }
     return;
   }
   const int32_t w = min(kPanel, we - k);
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
-  for (int32_t c = 0; c < w; ++c) {
-    double val = 0.0;
-    if (lane >= c && lane < w) val = L[static_cast<int64_t>(k + c) * ld + k + lane];
-    if (lane < w && lane >= c) { Bk[lane][c] = val; Bk[c][lane] = val; }
+  // the block's lower triangle, mirrored into a full symmetric copy
+  for (int32_t e = tid; e < kPanel * kPanel; e += kPanelThreads) {
+    const int32_t c = e / kPanel, r = e % kPanel;
+    if (r >= c && r < w && c < w) {
+      const double val = L[static_cast<int64_t>(k + c) * ld + k + r];
+      Bk[r][c] = val;
+      Bk[c][r] = val;
+    }
   }
-  perm[lane] = lane;
-  __syncwarp();
+  if (tid < kPanel) perm[tid] = tid;
+  __syncthreads();
   int32_t kk = 0;
   while (kk < w) {
-    // column kk below the diagonal: largest magnitude and its row
-    double v = (lane > kk && lane < w) ? fabs(Bk[lane][kk]) : -1.0;
-    double lam = warp_max(v);
-    unsigned ball = __ballot_sync(0xffffffffu, v == lam && lane > kk && lane < w);
-    int32_t r = ball ? __ffs(ball) - 1 : -1;
-    if (lam < 0) lam = 0.0;
-    double akk = fabs(Bk[kk][kk]);
-    int32_t kind = 1, piv = kk;          // kind 1: 1x1 at piv; kind 2: 2x2 (kk, piv)
-    if (lam == 0.0 || akk >= kBKAlpha * lam) {
-      kind = 1; piv = kk;
-    } else {
-      double vr = (lane >= kk && lane < w && lane != r) ? fabs(Bk[lane][r]) : -1.0;
-      double sig = warp_max(vr);
-      if (sig < 0) sig = 0.0;
-      if (akk * sig >= kBKAlpha * lam * lam) { kind = 1; piv = kk; }
-      else if (fabs(Bk[r][r]) >= kBKAlpha * sig) { kind = 1; piv = r; }
-      else { kind = 2; piv = r; }
+    // Bunch-Kaufman choice for column kk (warp 0; every other thread reads the result)
+    if (warp == 0) {
+      double v = (lane > kk && lane < w) ? fabs(Bk[lane][kk]) : -1.0;
+      double lam = warp_max(v);
+      unsigned ball = __ballot_sync(0xffffffffu, v == lam && lane > kk && lane < w);
+      int32_t r = ball ? __ffs(ball) - 1 : -1;
+      if (lam < 0) lam = 0.0;
+      double akk = fabs(Bk[kk][kk]);
+      int32_t kind = 1, piv = kk;          // kind 1: 1x1 at piv; kind 2: 2x2 (kk, piv)
+      if (lam == 0.0 || akk >= kBKAlpha * lam) {
+        kind = 1; piv = kk;
+      } else {
+        double vr = (lane >= kk && lane < w && lane != r) ? fabs(Bk[lane][r]) : -1.0;
+        double sig = warp_max(vr);
+        if (sig < 0) sig = 0.0;
+        if (akk * sig >= kBKAlpha * lam * lam) { kind = 1; piv = kk; }
+        else if (fabs(Bk[r][r]) >= kBKAlpha * sig) { kind = 1; piv = r; }
+        else { kind = 2; piv = r; }
+      }
+      if (lane == 0) { s_kind = kind; s_piv = piv; }
     }
+    __syncthreads();
+    const int32_t kind = s_kind, piv = s_piv;
     const int32_t dst = kind == 1 ? kk : kk + 1;
     if (piv != dst) {   // symmetric interchange of dst and piv in the full block copy
-      if (lane < w) { double tmp = Bk[lane][dst]; Bk[lane][dst] = Bk[lane][piv]; Bk[lane][piv] = tmp; }
-      __syncwarp();
-      if (lane < w) { double tmp = Bk[dst][lane]; Bk[dst][lane] = Bk[piv][lane]; Bk[piv][lane] = tmp; }
-      if (lane == 0) { int32_t tp = perm[dst]; perm[dst] = perm[piv]; perm[piv] = tp; }
-      __syncwarp();
+      if (tid < w) { double tmp = Bk[tid][dst]; Bk[tid][dst] = Bk[tid][piv]; Bk[tid][piv] = tmp; }
+      __syncthreads();
+      if (tid < w) { double tmp = Bk[dst][tid]; Bk[dst][tid] = Bk[piv][tid]; Bk[piv][tid] = tmp; }
+      if (tid == 0) { int32_t tp = perm[dst]; perm[dst] = perm[piv]; perm[piv] = tp; }
+      __syncthreads();
     }
+    const int32_t c0 = kk + kind;         // first column of the trailing block
     if (kind == 1) {
       const double d = Bk[kk][kk];
-      double la = 0.0;
-      if (lane > kk && lane < w) la = d != 0.0 ? Bk[lane][kk] / d : 0.0;
-      __syncwarp();
-      if (lane > kk && lane < w)
-        for (int32_t c = kk + 1; c < w; ++c) Bk[lane][c] -= la * Bk[c][kk];
-      __syncwarp();
-      if (lane > kk && lane < w) { Bk[lane][kk] = la; Bk[kk][lane] = la; }
-      if (lane == 0) { dd[kk] = d; de[kk] = 0.0; pt[kk] = 1; }
-      __syncwarp();
-      kk += 1;
+      if (tid > kk && tid < w) lv0[tid] = d != 0.0 ? Bk[tid][kk] / d : 0.0;
     } else {
       const double a = Bk[kk][kk], bb = Bk[kk + 1][kk], c2 = Bk[kk + 1][kk + 1];
       const double det = a * c2 - bb * bb;
-      double l0 = 0.0, l1 = 0.0;
-      if (lane > kk + 1 && lane < w) {
-        double w0 = Bk[lane][kk], w1 = Bk[lane][kk + 1];
-        l0 = (c2 * w0 - bb * w1) / det;
-        l1 = (a * w1 - bb * w0) / det;
+      if (tid > kk + 1 && tid < w) {
+        const double w0 = Bk[tid][kk], w1 = Bk[tid][kk + 1];
+        lv0[tid] = (c2 * w0 - bb * w1) / det;
+        lv1[tid] = (a * w1 - bb * w0) / det;
       }
-      __syncwarp();
-      if (lane > kk + 1 && lane < w)
-        for (int32_t c = kk + 2; c < w; ++c) Bk[lane][c] -= l0 * Bk[c][kk] + l1 * Bk[c][kk + 1];
-      __syncwarp();
-      if (lane > kk + 1 && lane < w) {
-        Bk[lane][kk] = l0; Bk[kk][lane] = l0;
-        Bk[lane][kk + 1] = l1; Bk[kk + 1][lane] = l1;
+    }
+    __syncthreads();
+    // trailing update of the block, rows and columns [c0, w): thread (row lane, columns warp + 4j)
+    if (lane >= c0 && lane < w) {
+      if (kind == 1) {
+        const double l0 = lv0[lane];
+        for (int32_t c = c0 + warp; c < w; c += kPanelThreads / 32) Bk[lane][c] -= l0 * Bk[c][kk];
+      } else {
+        const double l0 = lv0[lane], l1 = lv1[lane];
+        for (int32_t c = c0 + warp; c < w; c += kPanelThreads / 32) Bk[lane][c] -= l0 * Bk[c][kk] + l1 * Bk[c][kk + 1];
       }
-      if (lane == 0) {
-        dd[kk] = a; dd[kk + 1] = c2; de[kk] = bb; de[kk + 1] = 0.0;
+    }
+    __syncthreads();
+    if (kind == 1) {
+      if (tid > kk && tid < w) { Bk[tid][kk] = lv0[tid]; Bk[kk][tid] = lv0[tid]; }
+      if (tid == 0) { dd[kk] = Bk[kk][kk]; de[kk] = 0.0; pt[kk] = 1; }
+    } else {
+      if (tid > kk + 1 && tid < w) {
+        Bk[tid][kk] = lv0[tid]; Bk[kk][tid] = lv0[tid];
+        Bk[tid][kk + 1] = lv1[tid]; Bk[kk + 1][tid] = lv1[tid];
+      }
+      if (tid == 0) {
+        dd[kk] = Bk[kk][kk]; dd[kk + 1] = Bk[kk + 1][kk + 1]; de[kk] = Bk[kk + 1][kk]; de[kk + 1] = 0.0;
         pt[kk] = 2; pt[kk + 1] = 0;
       }
-      __syncwarp();
-      kk += 2;
+    }
+    __syncthreads();
+    kk += kind;
+  }
+  double* L11 = W.L11 + static_cast<int64_t>(b) * kPanel * kPanel;
+  for (int32_t e = tid; e < w * kPanel; e += kPanelThreads) {
+    const int32_t c = e / kPanel, r = e % kPanel;
+    if (r < w) {
+      const double val = (r > c) ? ((pt[c] == 2 && r == c + 1) ? 0.0 : Bk[r][c]) : (r == c ? 1.0 : 0.0);
+      L11[c * kPanel + r] = val;
     }
   }
-  __syncwarp();
-  double* L11 = W.L11 + static_cast<int64_t>(b) * kPanel * kPanel;
-  for (int32_t c = 0; c < w; ++c) {
-    double val = 0.0;
-    if (lane > c && lane < w) val = (pt[c] == 2 && lane == c + 1) ? 0.0 : Bk[lane][c];
-    if (lane < w) L11[c * kPanel + lane] = (lane == c) ? 1.0 : (lane > c ? val : 0.0);
+  if (tid < w) {
+    W.Dblk[b * 2 * kPanel + tid] = dd[tid];
+    W.Dblk[b * 2 * kPanel + kPanel + tid] = de[tid];
+    W.pt[b * kPanel + tid] = pt[tid];
+    W.pi[b * kPanel + tid] = perm[tid];
+    W.colmax[b * kPanel + tid] = 0ull;
   }
-  if (lane < w) {
-    W.Dblk[b * 2 * kPanel + lane] = dd[lane];
-    W.Dblk[b * 2 * kPanel + kPanel + lane] = de[lane];
-    W.pt[b * kPanel + lane] = pt[lane];
-    W.pi[b * kPanel + lane] = perm[lane];
-    W.colmax[b * kPanel + lane] = 0ull;
-  }
-  if (lane == 0) W.w[b] = w;
+  if (tid == 0) W.w[b] = w;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(32) lf_panel_kernel(FrontTables T, FactorSlot 
 __global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, FactorSlot S, LargeWork W,
                                                           Batch B) {
   __shared__ double L11s[kPanel][kPanel + 1];
-  __shared__ double dd[kPanel], de[kPanel];
+  __shared__ double dd[kPanel], r0[kPanel], r1[kPanel], r2[kPanel];
   __shared__ int8_t pt[kPanel];
   __shared__ int32_t pi[kPanel];
   __shared__ double red[kRowTile / 32][kPanel];
@@ -273,10 +290,23 @@ __global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, FactorS
   for (int32_t e = threadIdx.x; e < kPanel * kPanel; e += blockDim.x)
     L11s[e % kPanel][e / kPanel] = L11[e];
   if (threadIdx.x < kPanel) {
-    dd[threadIdx.x] = W.Dblk[b * 2 * kPanel + threadIdx.x];
-    de[threadIdx.x] = W.Dblk[b * 2 * kPanel + kPanel + threadIdx.x];
-    pt[threadIdx.x] = W.pt[b * kPanel + threadIdx.x];
-    pi[threadIdx.x] = W.pi[b * kPanel + threadIdx.x];
+    // D^{-1} of the block once per CTA: 1/d for a 1x1 pivot, the three entries of the inverse
+    // [c2 -b; -b a] / det for a 2x2 pivot (kept at its first index)
+    const int32_t c = threadIdx.x;
+    const double d0 = W.Dblk[b * 2 * kPanel + c];
+    dd[c] = d0;
+    pt[c] = W.pt[b * kPanel + c];
+    pi[c] = W.pi[b * kPanel + c];
+    r0[c] = r1[c] = r2[c] = 0.0;
+    if (pt[c] == 1) {
+      r0[c] = d0 != 0.0 ? 1.0 / d0 : 0.0;
+    } else if (pt[c] == 2 && c + 1 < kPanel) {
+      const double a = d0, c2 = W.Dblk[b * 2 * kPanel + c + 1], bb = W.Dblk[b * 2 * kPanel + kPanel + c];
+      const double inv = 1.0 / (a * c2 - bb * bb);
+      r0[c] = c2 * inv;
+      r1[c] = -bb * inv;
+      r2[c] = a * inv;
+    }
   }
   __syncthreads();
   const double* L = S.F + T.front_off[t];
@@ -305,14 +335,11 @@ __global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, FactorS
     for (int32_t c = 0; c < kPanel; ++c) {
       if (c < w) {
         if (pt[c] == 1) {
-          const double d = dd[c];
-          f[c] = d != 0.0 ? f[c] / d : (f[c] == 0.0 ? 0.0 : INFINITY);
+          f[c] = dd[c] != 0.0 ? f[c] * r0[c] : (f[c] == 0.0 ? 0.0 : INFINITY);
         } else if (pt[c] == 2 && c + 1 < kPanel) {
-          const double a = dd[c], c2 = dd[c + 1], bb = de[c];
-          const double det = a * c2 - bb * bb;
           const double y0 = f[c], y1 = f[c + 1];
-          f[c] = (y0 * c2 - y1 * bb) / det;
-          f[c + 1] = (y1 * a - y0 * bb) / det;
+          f[c] = fma(y0, r0[c], y1 * r1[c]);
+          f[c + 1] = fma(y1, r2[c], y0 * r1[c]);
         }
       }
     }
@@ -797,7 +824,7 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       int64_t steps = (max_p + kPanel - 1) / kPanel + 1;
       while (true) {
         for (int64_t it = 0; it < steps; ++it) {
-          KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B));
+          KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, kPanelThreads, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_L21, st, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
           if (emul) {
@@ -817,7 +844,7 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
         }
         // one more panel call finalises fronts whose last block was accepted
-        KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, 32, 0, st>>>(F.T, F.S, F.W, B));
+        KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, kPanelThreads, 0, st>>>(F.T, F.S, F.W, B));
         if (cudaMemcpyAsync(F.h_done, F.W.done + e, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
           return KEP_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;

@@ -251,7 +251,7 @@ struct SolveLaunch {
   double* vfac;
   double* bnew;
   double* xnew;
-  double* partial;            // num_sms * 4 * (kSolveBlk + 1) doubles
+  double* partial;            // num_sms * 4 * (kSolveBlk + 1) doubles (shared by a level's fronts)
   const int32_t* h_nelim;     // pivots eliminated per front (host copy of the factor's counts)
   cudaStream_t stream;
   int num_sms;

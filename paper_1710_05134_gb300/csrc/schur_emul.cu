@@ -246,18 +246,39 @@ KEP_D int64_t tile_slots(int64_t nI, int64_t nJ) {
   }
   return n;
 }
-KEP_D bool tile_ij(int64_t t, int64_t nI, int64_t nJ, int64_t& I, int64_t& J) {
-  for (int64_t I0 = 0; I0 < nI; I0 += kBand) {
-    const int64_t I1 = min(I0 + kBand, nI);
-    const int64_t cnt = (I1 - I0) * min(4 * I1, nJ);
-    if (t < cnt) {
-      J = t / (I1 - I0);
-      I = I0 + t % (I1 - I0);
+// Slot t -> tile (I, J) in closed form (32-bit): the first bands are 8 high and 32 (b + 1) wide
+// (prefix 128 b (b + 1)), the following 8-high bands are nJ wide, and a last band may be lower.
+KEP_D bool tile_ij(int t, int nI, int nJ, int& I, int& J) {
+  const int nfull = min(nI / 8, nJ / 32);
+  const int pf = 128 * nfull * (nfull + 1);
+  if (t < pf) {
+    int b = static_cast<int>((sqrtf(1.0f + static_cast<float>(t) / 32.0f) - 1.0f) * 0.5f);
+    while (b > 0 && 128 * b * (b + 1) > t) --b;
+    while (128 * (b + 1) * (b + 2) <= t) ++b;
+    const int r = t - 128 * b * (b + 1);
+    J = r >> 3;
+    I = 8 * b + (r & 7);
+    return J < 4 * (I + 1);
+  }
+  t -= pf;
+  int I0 = 8 * nfull;
+  if (32 * (nfull + 1) > nJ) {
+    const int nb2 = (nI - I0) / 8;
+    if (t < nb2 * 8 * nJ) {
+      const int bb = t / (8 * nJ), rr = t - bb * 8 * nJ;
+      J = rr >> 3;
+      I = I0 + 8 * bb + (rr & 7);
       return J < 4 * (I + 1);
     }
-    t -= cnt;
+    t -= nb2 * 8 * nJ;
+    I0 += 8 * nb2;
   }
-  return false;
+  if (I0 >= nI) return false;
+  const int h = nI - I0, w = min(4 * nI, nJ);
+  if (t >= h * w) return false;
+  J = t / h;
+  I = I0 + t % h;
+  return J < 4 * (I + 1);
 }
 
 // C - (hi 2^32 + lo) 2^scale for |hi|, |lo| < 2^52.  The integer V = hi 2^32 + lo is brought to
@@ -340,13 +361,13 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   const int KS = (r + 15) / 16;               // 16-column steps
   const int NH = (KS + kHalf - 1) / kHalf;    // accumulation halves
   const int64_t h = v.m - s, w = ce - s;
-  const int64_t nI = (h + kTM - 1) / kTM, nJ = (w + kTN - 1) / kTN;
-  const int64_t nslots = tile_slots(nI, nJ);
+  const int nI = static_cast<int>((h + kTM - 1) / kTM), nJ = static_cast<int>((w + kTN - 1) / kTN);
+  const int nslots = static_cast<int>(tile_slots(nI, nJ));
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // tensor-core work issued (i-block I has min(4I + 4, nJ) tiles), and the FP64 update it
     // stands for (2 r per updated entry)
     const int64_t c = min(nI, nJ / 4);
-    const int64_t ntiles = 2 * c * (c + 1) + (nI - c) * nJ;
+    const int64_t ntiles = 2 * c * (c + 1) + (nI - c) * static_cast<int64_t>(nJ);
     atomicAdd(&flops[KC_FLUSH_TC],
               static_cast<unsigned long long>(2ll * kTM * (kSlices * (kSlices + 1) / 2) * kTN * 16 * KS * ntiles));
     atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (w * h - w * (w - 1) / 2)));
@@ -376,8 +397,8 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
     if (lane == 0) {
       int64_t f = 0;
       bool ok = true;
-      for (int64_t slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
-        int64_t I, J;
+      for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
+        int I, J;
         if (!tile_ij(slot, nI, nJ, I, J)) continue;
         for (int kk = 0; kk < KS; ++kk, ++f) {
           const int st = static_cast<int>(f % kStages);
@@ -404,8 +425,8 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
       const uint32_t s0 = tc::smem_addr(sbase);
       int64_t f = 0, u = 0;                     // steps, half-window accumulations issued
       bool ok = true;
-      for (int64_t slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
-        int64_t I, J;
+      for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
+        int I, J;
         if (!tile_ij(slot, nI, nJ, I, J)) continue;
         for (int hh = 0; hh < NH && ok; ++hh, ++u) {
           const int buf = static_cast<int>(u & 1);
@@ -448,8 +469,8 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
     const uint32_t trow = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
     int64_t u = 0;
     bool ok = true;
-    for (int64_t slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
-      int64_t I, J;
+    for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
+      int I, J;
       if (!tile_ij(slot, nI, nJ, I, J)) continue;
       // this thread's row and its entries of C (column stride cs from the entry of column j0; the
       // columns of a tile lie on one side of p except at one j-block of the front); they are

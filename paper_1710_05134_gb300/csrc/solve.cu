@@ -29,6 +29,9 @@ KEP_D int32_t fwd_block(const int8_t* piv, int32_t k0, int32_t nel) {
 __global__ void __launch_bounds__(kSolveThreads) sv_fwd_kernel(FrontTables T, FactorSlot S,
                                                                const int32_t* lf, const double* bnew,
                                                                double* vasm, double* vfac) {
+  __shared__ double Lb[kBlk + 1][kBlk + 2];   // diagonal block, [column][row]
+  __shared__ double y[kBlk + 1];
+  __shared__ int8_t pb[kBlk + 1];
   const int32_t t = lf[blockIdx.x];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in;
@@ -62,25 +65,32 @@ __global__ void __launch_bounds__(kSolveThreads) sv_fwd_kernel(FrontTables T, Fa
   while (k0 < nel) {
     const int32_t kb = fwd_block(piv, k0, nel);
     const int32_t k1 = k0 + kb;
+    // the block's triangle, right-hand side and pivot types in shared memory
+    for (int32_t e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int32_t c = e / kb, a = e % kb;
+      Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
+    }
+    for (int32_t c = threadIdx.x; c < kb; c += blockDim.x) { y[c] = vf[k0 + c]; pb[c] = piv[k0 + c]; }
+    __syncthreads();
     if (warp == 0) {
-      for (int32_t c = k0; c < k1;) {
-        if (piv[c] == 2) {
-          const double y0 = vf[c], y1 = vf[c + 1];
-          for (int32_t a = c + 2 + lane; a < k1; a += 32)
-            vf[a] -= L[static_cast<int64_t>(c) * ld + a] * y0 + L[static_cast<int64_t>(c + 1) * ld + a] * y1;
+      for (int32_t c = 0; c < kb;) {
+        if (pb[c] == 2) {
+          const double y0 = y[c], y1 = y[c + 1];
+          for (int32_t a = c + 2 + lane; a < kb; a += 32) y[a] -= Lb[c][a] * y0 + Lb[c + 1][a] * y1;
           c += 2;
         } else {
-          const double y0 = vf[c];
-          for (int32_t a = c + 1 + lane; a < k1; a += 32) vf[a] -= L[static_cast<int64_t>(c) * ld + a] * y0;
+          const double y0 = y[c];
+          for (int32_t a = c + 1 + lane; a < kb; a += 32) y[a] -= Lb[c][a] * y0;
           c += 1;
         }
         __syncwarp();
       }
     }
     __syncthreads();
+    for (int32_t c = threadIdx.x; c < kb; c += blockDim.x) vf[k0 + c] = y[c];
     for (int32_t a = k1 + threadIdx.x; a < m; a += blockDim.x) {
       double s = 0.0;
-      for (int32_t c = k0; c < k1; ++c) s += L[static_cast<int64_t>(c) * ld + a] * vf[c];
+      for (int32_t c = 0; c < kb; ++c) s += L[static_cast<int64_t>(k0 + c) * ld + a] * y[c];
       vf[a] -= s;
     }
     __syncthreads();
@@ -93,6 +103,9 @@ __global__ void __launch_bounds__(kSolveThreads) sv_bwd_kernel(FrontTables T, Fa
                                                                double* vfac) {
   __shared__ double red[kSolveThreads / 32][kBlk + 1];
   __shared__ double part[kBlk + 1];
+  __shared__ double Lb[kBlk + 1][kBlk + 2];   // diagonal block, [column][row]
+  __shared__ double xb[kBlk + 1];
+  __shared__ int8_t pb[kBlk + 1];
   const int32_t t = lf[blockIdx.x];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in;
@@ -144,30 +157,38 @@ __global__ void __launch_bounds__(kSolveThreads) sv_bwd_kernel(FrontTables T, Fa
       part[threadIdx.x] = s;
     }
     __syncthreads();
+    for (int32_t e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int32_t c = e / kb, a = e % kb;
+      Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
+    }
+    for (int32_t c = threadIdx.x; c < kb; c += blockDim.x) { xb[c] = vf[k0 + c]; pb[c] = piv[k0 + c]; }
+    __syncthreads();
     if (warp == 0) {
-      for (int32_t c = k1 - 1; c >= k0;) {
-        if (piv[c] == 0) {                    // second of a pair at (c-1, c)
+      for (int32_t c = kb - 1; c >= 0;) {
+        if (pb[c] == 0) {                     // second of a pair at (c-1, c)
           double s0 = 0.0, s1 = 0.0;
-          for (int32_t a = c + 1 + lane; a < k1; a += 32) {
-            s0 += L[static_cast<int64_t>(c - 1) * ld + a] * vf[a];
-            s1 += L[static_cast<int64_t>(c) * ld + a] * vf[a];
+          for (int32_t a = c + 1 + lane; a < kb; a += 32) {
+            s0 += Lb[c - 1][a] * xb[a];
+            s1 += Lb[c][a] * xb[a];
           }
           s0 = warp_sum(s0); s1 = warp_sum(s1);
           if (lane == 0) {
-            vf[c] -= part[c - k0] + s1;
-            vf[c - 1] -= part[c - 1 - k0] + s0;
+            xb[c] -= part[c] + s1;
+            xb[c - 1] -= part[c - 1] + s0;
           }
           c -= 2;
         } else {
           double s0 = 0.0;
-          for (int32_t a = c + 1 + lane; a < k1; a += 32) s0 += L[static_cast<int64_t>(c) * ld + a] * vf[a];
+          for (int32_t a = c + 1 + lane; a < kb; a += 32) s0 += Lb[c][a] * xb[a];
           s0 = warp_sum(s0);
-          if (lane == 0) vf[c] -= part[c - k0] + s0;
+          if (lane == 0) xb[c] -= part[c] + s0;
           c -= 1;
         }
         __syncwarp();
       }
     }
+    __syncthreads();
+    for (int32_t c = threadIdx.x; c < kb; c += blockDim.x) vf[k0 + c] = xb[c];
     __syncthreads();
     k1 = k0;
   }
@@ -177,7 +198,9 @@ __global__ void __launch_bounds__(kSolveThreads) sv_bwd_kernel(FrontTables T, Fa
 // ------------------------------------------------------------------------------------------
 // multi-block path for the largest fronts: the pivot range is cut into blocks of kSolveBlk
 // (boundaries moved by one where they would split a 2x2 pair); every block is one launch whose
-// CTAs all reproduce the small diagonal-block solve and then update their own rows.
+// CTAs all reproduce the small diagonal-block solve and then update their own rows.  All such
+// fronts of a level share the launches: grid.y = front (fronts[blockIdx.y]), grid.x = the CTAs of
+// one front.
 // ------------------------------------------------------------------------------------------
 KEP_D int32_t blk_start(const int8_t* piv, int32_t b, int32_t nel) {
   if (b <= 0) return 0;
@@ -187,8 +210,9 @@ KEP_D int32_t blk_start(const int8_t* piv, int32_t b, int32_t nel) {
 }
 
 // assembly of the front's right-hand side (children in order) and the pivot permutation
-__global__ void __launch_bounds__(1024) sv_big_prep_kernel(FrontTables T, FactorSlot S, int32_t t,
+__global__ void __launch_bounds__(1024) sv_big_prep_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
                                                            const double* bnew, double* vasm, double* vfac) {
+  const int32_t t = fronts[blockIdx.x];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in;
   const int32_t psym = T.p_sym[t];
@@ -215,9 +239,12 @@ __global__ void __launch_bounds__(1024) sv_big_prep_kernel(FrontTables T, Factor
 
 // forward block b: y(block) = L11^{-1} f(block) (every CTA), CTA 0 stores it in ysol; rows below
 // the block: f(a) -= L(a, block) y(block)
-__global__ void __launch_bounds__(256) sv_big_fwd_kernel(FrontTables T, FactorSlot S, int32_t t, int32_t b,
-                                                         double* vfac, double* ysol) {
+__global__ void __launch_bounds__(256) sv_big_fwd_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
+                                                         int32_t b, double* vfac, double* ysol) {
   __shared__ double y[kSolveBlk + 1];
+  __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
+  __shared__ int8_t pb[kSolveBlk + 1];
+  const int32_t t = fronts[blockIdx.y];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in;
   const int32_t nel = S.nelim[t];
@@ -229,19 +256,22 @@ __global__ void __launch_bounds__(256) sv_big_fwd_kernel(FrontTables T, FactorSl
   double* vf = vfac + T.vec_off[t];
   double* ys = ysol + T.vec_off[t];
   const int32_t kb = k1 - k0;
-  if (threadIdx.x < kb) y[threadIdx.x] = vf[k0 + threadIdx.x];
+  for (int32_t e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int32_t c = e / kb, a = e % kb;
+    Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
+  }
+  if (threadIdx.x < kb) { y[threadIdx.x] = vf[k0 + threadIdx.x]; pb[threadIdx.x] = piv[k0 + threadIdx.x]; }
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int32_t c = 0; c < kb;) {
-      if (piv[k0 + c] == 2) {
+      if (pb[c] == 2) {
         const double y0 = y[c], y1 = y[c + 1];
-        for (int32_t a = c + 2 + lane; a < kb; a += 32)
-          y[a] -= L[static_cast<int64_t>(k0 + c) * ld + k0 + a] * y0 + L[static_cast<int64_t>(k0 + c + 1) * ld + k0 + a] * y1;
+        for (int32_t a = c + 2 + lane; a < kb; a += 32) y[a] -= Lb[c][a] * y0 + Lb[c + 1][a] * y1;
         c += 2;
       } else {
         const double y0 = y[c];
-        for (int32_t a = c + 1 + lane; a < kb; a += 32) y[a] -= L[static_cast<int64_t>(k0 + c) * ld + k0 + a] * y0;
+        for (int32_t a = c + 1 + lane; a < kb; a += 32) y[a] -= Lb[c][a] * y0;
         c += 1;
       }
       __syncwarp();
@@ -257,8 +287,9 @@ __global__ void __launch_bounds__(256) sv_big_fwd_kernel(FrontTables T, FactorSl
 }
 
 // backward preparation: solution on the contribution rows, z = D^{-1} y on the pivots
-__global__ void sv_big_bwd_prep_kernel(FrontTables T, FactorSlot S, int32_t t, const double* xnew,
+__global__ void sv_big_bwd_prep_kernel(FrontTables T, FactorSlot S, const int32_t* fronts, const double* xnew,
                                        const double* ysol, double* vfac) {
+  const int32_t t = fronts[blockIdx.y];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in;
   const int32_t nel = S.nelim[t];
@@ -284,14 +315,19 @@ __global__ void sv_big_bwd_prep_kernel(FrontTables T, FactorSlot S, int32_t t, c
   }
 }
 
-// backward block b, part 1: per-CTA partial sums s_c = sum_{a >= k1} L(a, k0 + c) x(a); warp w owns
-// columns w, w + 8, ..., its lanes stride the CTA's rows
-__global__ void __launch_bounds__(256) sv_big_bwd_partial_kernel(FrontTables T, FactorSlot S, int32_t t,
-                                                                 int32_t b, const double* vfac, double* partial) {
+// backward block b, part 1: per-CTA partial sums s_c = sum_{a >= k1} L(a, k0 + c) x(a), stored
+// column-major (partial[c * gridDim.x + cta]); warp w owns columns w, w + 8, ..., its lanes stride
+// the CTA's rows
+__global__ void __launch_bounds__(256) sv_big_bwd_partial_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
+                                                                 int32_t step, const double* vfac, double* partial) {
   constexpr int kCols = (kSolveBlk + 1 + 7) / 8;
+  const int32_t t = fronts[blockIdx.y];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in;
   const int32_t nel = S.nelim[t];
+  const int32_t b = (nel + kSolveBlk - 1) / kSolveBlk - 1 - step;   // blocks from the last one down
+  if (b < 0) return;
+  partial += static_cast<int64_t>(blockIdx.y) * (kSolveBlk + 1) * gridDim.x;
   const int8_t* piv = S.piv + T.piv_off[t];
   const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
   const int32_t kb = k1 - k0;
@@ -314,54 +350,76 @@ __global__ void __launch_bounds__(256) sv_big_bwd_partial_kernel(FrontTables T, 
   for (int j = 0; j < kCols; ++j) {
     const int32_t c = warp + 8 * j;
     const double v = warp_sum(acc[j]);
-    if (lane == 0 && c < kb) partial[static_cast<int64_t>(blockIdx.x) * (kSolveBlk + 1) + c] = v;
+    if (lane == 0 && c < kb) partial[static_cast<int64_t>(c) * gridDim.x + blockIdx.x] = v;
   }
 }
 
 // backward block b, part 2 (one CTA): add the partials, solve the block's unit upper triangle
-__global__ void __launch_bounds__(128) sv_big_bwd_block_kernel(FrontTables T, FactorSlot S, int32_t t, int32_t b,
-                                                               int32_t nparts, const double* partial, double* vfac) {
+__global__ void __launch_bounds__(128) sv_big_bwd_block_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
+                                                               int32_t step, int32_t nparts, const double* partial,
+                                                               double* vfac) {
   __shared__ double part[kSolveBlk + 1];
-  const int32_t d_in = S.d_in[t];
-  (void)d_in;
+  __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
+  __shared__ double xb[kSolveBlk + 1];
+  __shared__ int8_t pb[kSolveBlk + 1];
+  const int32_t t = fronts[blockIdx.x];
   const int32_t nel = S.nelim[t];
+  const int32_t b = (nel + kSolveBlk - 1) / kSolveBlk - 1 - step;
+  if (b < 0) return;
+  partial += static_cast<int64_t>(blockIdx.x) * (kSolveBlk + 1) * nparts;
   const int8_t* piv = S.piv + T.piv_off[t];
   const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
   const int32_t kb = k1 - k0;
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
   double* vf = vfac + T.vec_off[t];
+  for (int32_t e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+    const int32_t c = e / kb, a = e % kb;
+    Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
+  }
+  {  // column sums of the partials: warp w takes columns w, w + 4, ..., its lanes the CTAs
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int32_t c = warp; c < kb; c += blockDim.x / 32) {
+      double s = 0.0;
+      for (int32_t q = lane; q < nparts; q += 32) s += partial[static_cast<int64_t>(c) * nparts + q];
+      s = warp_sum(s);
+      if (lane == 0) part[c] = s;
+    }
+  }
   if (threadIdx.x < kb) {
-    double s = 0.0;
-    for (int32_t q = 0; q < nparts; ++q) s += partial[static_cast<int64_t>(q) * (kSolveBlk + 1) + threadIdx.x];
-    part[threadIdx.x] = s;
+    xb[threadIdx.x] = vf[k0 + threadIdx.x];
+    pb[threadIdx.x] = piv[k0 + threadIdx.x];
   }
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    for (int32_t c = k1 - 1; c >= k0;) {
-      if (piv[c] == 0) {
+    for (int32_t c = kb - 1; c >= 0;) {
+      if (pb[c] == 0) {
         double s0 = 0.0, s1 = 0.0;
-        for (int32_t a = c + 1 + lane; a < k1; a += 32) {
-          s0 += L[static_cast<int64_t>(c - 1) * ld + a] * vf[a];
-          s1 += L[static_cast<int64_t>(c) * ld + a] * vf[a];
+        for (int32_t a = c + 1 + lane; a < kb; a += 32) {
+          s0 += Lb[c - 1][a] * xb[a];
+          s1 += Lb[c][a] * xb[a];
         }
         s0 = warp_sum(s0); s1 = warp_sum(s1);
-        if (lane == 0) { vf[c] -= part[c - k0] + s1; vf[c - 1] -= part[c - 1 - k0] + s0; }
+        if (lane == 0) { xb[c] -= part[c] + s1; xb[c - 1] -= part[c - 1] + s0; }
         c -= 2;
       } else {
         double s0 = 0.0;
-        for (int32_t a = c + 1 + lane; a < k1; a += 32) s0 += L[static_cast<int64_t>(c) * ld + a] * vf[a];
+        for (int32_t a = c + 1 + lane; a < kb; a += 32) s0 += Lb[c][a] * xb[a];
         s0 = warp_sum(s0);
-        if (lane == 0) vf[c] -= part[c - k0] + s0;
+        if (lane == 0) xb[c] -= part[c] + s0;
         c -= 1;
       }
       __syncwarp();
     }
   }
+  __syncthreads();
+  if (threadIdx.x < kb) vf[k0 + threadIdx.x] = xb[threadIdx.x];
 }
 
-__global__ void sv_big_scatter_kernel(FrontTables T, FactorSlot S, int32_t t, const double* vfac, double* xnew) {
+__global__ void sv_big_scatter_kernel(FrontTables T, FactorSlot S, const int32_t* fronts, const double* vfac,
+                                      double* xnew) {
+  const int32_t t = fronts[blockIdx.y];
   const int32_t nel = S.nelim[t];
   const double* vf = vfac + T.vec_off[t];
   const int32_t* rv = S.rowvar + T.vec_off[t];
@@ -390,16 +448,28 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   cudaStream_t st = L.stream;
   const int g = L.num_sms * 4;
   KEP_LAUNCH(L.timer, KC_PERM, st, gather_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, b, L.bnew));
-  for (int32_t l = 0; l < P.nlevels; ++l) {
-    const int32_t lb = P.level_ptr[l], w = P.level_ptr[l + 1] - lb, nbig = P.level_nbig_solve[l];
+  // the level's multi-block fronts: their block count and CTAs per front (a uniform grid)
+  auto big_shape = [&](int32_t lb, int32_t nbig, int32_t& maxblk, int& gx) {
+    int64_t rows = 0;
+    maxblk = 0;
     for (int32_t i = 0; i < nbig; ++i) {
       const int32_t t = P.level_fronts[lb + i];
-      const int32_t nel = L.h_nelim[t];
-      KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st, sv_big_prep_kernel<<<1, 1024, 0, st>>>(L.T, L.S, t, L.bnew, L.vasm, L.vfac));
-      const int32_t rows = P.m_alloc[t];
-      const int grid = static_cast<int>(std::min<int64_t>(g, (rows + 255) / 256 + 1));
-      for (int32_t bb = 0; bb * kSolveBlk < nel; ++bb)
-        KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st, sv_big_fwd_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, bb, L.vfac, L.vasm));
+      rows = std::max<int64_t>(rows, P.m_alloc[t]);
+      maxblk = std::max(maxblk, (L.h_nelim[t] + kSolveBlk - 1) / kSolveBlk);
+    }
+    gx = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256 + 1, g / std::max(1, nbig))));
+  };
+  for (int32_t l = 0; l < P.nlevels; ++l) {
+    const int32_t lb = P.level_ptr[l], w = P.level_ptr[l + 1] - lb, nbig = P.level_nbig_solve[l];
+    if (nbig > 0) {
+      int32_t maxblk;
+      int gx;
+      big_shape(lb, nbig, maxblk, gx);
+      const int32_t* fr = L.d_level_fronts + lb;
+      KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st, sv_big_prep_kernel<<<nbig, 1024, 0, st>>>(L.T, L.S, fr, L.bnew, L.vasm, L.vfac));
+      for (int32_t bb = 0; bb < maxblk; ++bb)
+        KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st,
+                   sv_big_fwd_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, bb, L.vfac, L.vasm));
     }
     if (w > nbig)
       KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st,
@@ -408,20 +478,21 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   }
   for (int32_t l = P.nlevels - 1; l >= 0; --l) {
     const int32_t lb = P.level_ptr[l], w = P.level_ptr[l + 1] - lb, nbig = P.level_nbig_solve[l];
-    for (int32_t i = 0; i < nbig; ++i) {
-      const int32_t t = P.level_fronts[lb + i];
-      const int32_t nel = L.h_nelim[t];
-      const int32_t rows = P.m_alloc[t];
-      const int grid = static_cast<int>(std::min<int64_t>(g, (rows + 255) / 256 + 1));
-      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st, sv_big_bwd_prep_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, L.xnew, L.vasm, L.vfac));
-      const int32_t nblk = (nel + kSolveBlk - 1) / kSolveBlk;
-      for (int32_t bb = nblk - 1; bb >= 0; --bb) {
+    if (nbig > 0) {
+      int32_t maxblk;
+      int gx;
+      big_shape(lb, nbig, maxblk, gx);
+      const int32_t* fr = L.d_level_fronts + lb;
+      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
+                 sv_big_bwd_prep_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, L.xnew, L.vasm, L.vfac));
+      for (int32_t step = 0; step < maxblk; ++step) {
         KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
-                   sv_big_bwd_partial_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, bb, L.vfac, L.partial));
+                   sv_big_bwd_partial_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, step, L.vfac, L.partial));
         KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
-                   sv_big_bwd_block_kernel<<<1, 128, 0, st>>>(L.T, L.S, t, bb, grid, L.partial, L.vfac));
+                   sv_big_bwd_block_kernel<<<nbig, 128, 0, st>>>(L.T, L.S, fr, step, gx, L.partial, L.vfac));
       }
-      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st, sv_big_scatter_kernel<<<grid, 256, 0, st>>>(L.T, L.S, t, L.vfac, L.xnew));
+      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
+                 sv_big_scatter_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, L.vfac, L.xnew));
     }
     if (w > nbig)
       KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
