@@ -80,7 +80,14 @@ typedef struct {
   const double* start_vectors;/* optional host array of 2n: v_1 (Algorithm 2) then v~_1
                                  (Algorithm 3); NULL draws them from a counter-based generator */
   uint64_t seed;              /* seed of that generator */
+  int32_t init;               /* initial interval: KEP_INIT_LANCZOS (Algorithm 2, default) or
+                                 KEP_INIT_GERSHGORIN (an interval holding the whole spectrum,
+                                 the variant of Section 4.2) */
+  int32_t nshift;             /* shifts per Algorithm 1' step: 1 bisection (default), s > 1
+                                 multisection into s + 1 equal parts */
 } kep_params;
+
+enum { KEP_INIT_LANCZOS = 0, KEP_INIT_GERSHGORIN = 1 };
 
 /* Report of kep_kth_eigenpair. */
 typedef struct {
@@ -156,6 +163,14 @@ kep_status kep_set_stream(kep_ctx* ctx, void* stream);
 kep_status kep_factor(kep_ctx* ctx, double sigma, kep_inertia* out);
 
 /*
+ * kep_factor_multi - inertia of A - sigmas[i] B for ns shifts (the evaluations of one
+ * multisection step of Algorithm 1'); out[i] receives each; the factor of the last shift stays
+ * for kep_solve.  Shifts that are eigenvalues (exact zero pivot) keep their counts with
+ * zero > 0.  Errors: as kep_factor, KEP_ERR_INVALID for ns < 1 or null pointers.
+ */
+kep_status kep_factor_multi(kep_ctx* ctx, const double* sigmas, int32_t ns, kep_inertia* out);
+
+/*
  * kep_factor_pencil - as kep_factor for the matrix ca*A + cb*B (kep_factor(sigma) is
  * ca = 1, cb = -sigma; ca = 0, cb = 1 factors B, task (ii) of Section 4.3).
  */
@@ -193,6 +208,28 @@ kep_status kep_spmv(kep_ctx* ctx, const double* x, double* ax, double* bx, int p
  */
 kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, double* lambda,
                              double* x, kep_report* report);
+
+/*
+ * kep_set_values - new values of A and B on the pattern given to kep_analyze (same layout:
+ * a_val, b_val as there, host arrays).  The symbolic analysis is kept; the factors of the old
+ * values become invalid.  Errors: KEP_ERR_INVALID, KEP_ERR_CUDA.
+ */
+kep_status kep_set_values(kep_ctx* ctx, const double* a_val, const double* b_val);
+
+/*
+ * kep_grad - derivatives of an eigenvalue lambda of A x = lambda B x with respect to the stored
+ * values of A and B (Hellmann-Feynman theorem; the paper states the eigenpair problem of
+ * Section 2 and has no derivative counterpart): with s = x^T B x,
+ *   d_lambda_d_a[e] = lambda_bar * x_i x_j / s,   d_lambda_d_b[e] = -lambda * d_lambda_d_a[e]
+ * for every entry e = (i, j) in the layout of kep_analyze's a_val, each entry an independent
+ * variable; with KEP_PATTERN_LOWER an off-diagonal entry stands for (i, j) and (j, i) and gets
+ * twice that.  x: the eigenvector (any nonzero scaling; n doubles), lambda_bar: the factor the
+ * derivatives are multiplied by (the incoming gradient).  Either output may be NULL.  Vectors
+ * in ptr_kind memory.  Errors: KEP_ERR_INVALID (null pointers, x^T B x <= 0), KEP_ERR_NOMEM,
+ * KEP_ERR_CUDA.
+ */
+kep_status kep_grad(kep_ctx* ctx, double lambda, const double* x, double lambda_bar, double* d_lambda_d_a,
+                    double* d_lambda_d_b, int ptr_kind);
 
 /*
  * Kernel accounting.  Classes (index into the arrays): 0 assembly (zero, scatter, extend-add),

@@ -15,6 +15,9 @@ Routes (each pinned in tests/test_oracle_core.py against something other than it
                           Section 4.2).  Library routines (Cholesky, triangular solve, symmetric
                           eigensolver) serve as steps.  Pins: closed-form spectra; residual and
                           B-orthonormality of the returned vectors.
+* ``eig_grad``            derivatives of lambda_k with respect to the entries of A and B from the
+                          (c2) eigenvector (Hellmann-Feynman).  Pins: central finite differences of
+                          lambda_k under symmetric perturbations of single entries.
 * ``sband_eigs`` / ``diamond_bloch_eigs`` / diagonal: closed-form pencil spectra.
                           Pins: the s-band formula against a brute-force dense eigensolve at tiny
                           sizes; the Bloch spectrum likewise.
@@ -150,6 +153,16 @@ def gen_eig(A: np.ndarray, B: np.ndarray):
     lam, Y = np.linalg.eigh(C)
     X = sla.solve_triangular(L.T, Y, lower=False)
     return lam, X
+
+
+def eig_grad(A: np.ndarray, B: np.ndarray, k: int):
+    """Derivatives of lambda_k of A x = lambda B x (Hellmann-Feynman): with x the (c2) eigenvector,
+    B-normalized, d lambda / d A_ij = x_i x_j and d lambda / d B_ij = -lambda x_i x_j, every
+    entry an independent variable.  Returns (lambda_k, GA, GB) as dense matrices."""
+    lam, X = gen_eig(A, B)
+    x = X[:, k - 1]
+    G = np.outer(x, x)
+    return float(lam[k - 1]), G, -float(lam[k - 1]) * G
 
 
 def count_below(eigs: np.ndarray, sigma: float) -> int:

@@ -10,7 +10,14 @@ Algorithms of the paper, step by step and in its notation, on plain operators:
                           modified Ritz vectors x_{i,2} (Eq. 2.9), the error bound of Proposition 3
                           (Eq. 3.1), inclusion (3.3), disjointness (3.4), residual and relative
                           difference (Eq. 3.5) tests.
-  * ``three_stage``       Algorithm 4 (Section 3.4).
+  * ``three_stage``       Algorithm 4 (Section 3.4), optionally with the Gershgorin initial
+                          interval of the variant of Section 4.2 and multisection in Algorithm 1'.
+  * ``gershgorin_interval``          an interval holding the whole spectrum from Gershgorin bounds
+                          of A and B and the Rayleigh quotient (the reading the GPU path uses);
+    ``gershgorin_columns_interval``  the paper's construction: Gershgorin discs of the columns of
+                          B^{-1} A (Section 4.2, dense, small n).
+  * ``multisect_mmax``    Algorithm 1' with s points per step (s + 1 equal parts; s = 1 is
+                          bisection).
 
 Operators come from ``DenseOps`` (dense numpy, small n) or ``SparseOps`` (scipy sparse LU for
 solves, (c3) for inertia).  Library solves serve as steps; the method's arithmetic is here.
@@ -151,6 +158,60 @@ def bisect_mmax(ops, k: int, iv: Interval, m_max: int = 20) -> Interval:
     return Interval(lo, hi, nl, nu_u, hist)
 
 
+def multisect_mmax(ops, k: int, iv: Interval, m_max: int = 20, nshift: int = 1) -> Interval:
+    """Algorithm 1' with nshift shifts per step: [sigma_l, sigma_u) is cut into nshift + 1 equal
+    parts and the one with nu(left) < k <= nu(right) is kept, until nu_u - nu_l <= m_max.  With
+    nshift = 1 the shift is the midpoint (bisection)."""
+    lo, hi, nl, nu_u = iv.lower, iv.upper, iv.nu_lower, iv.nu_upper
+    hist = []
+    while nu_u - nl > m_max:
+        plo, phi, pnl, pnu = lo, hi, nl, nu_u
+        for q in range(1, nshift + 1):
+            s = 0.5 * (lo + hi) if nshift == 1 else lo + (hi - lo) * q / (nshift + 1)
+            nu = ops.nu(s)
+            hist.append((s, nu))
+            if k <= nu:
+                phi, pnu = s, nu
+                break
+            plo, pnl = s, nu
+        lo, hi, nl, nu_u = plo, phi, pnl, pnu
+    return Interval(lo, hi, nl, nu_u, hist)
+
+
+def gershgorin_interval(A, B, pad: float = 1e-12) -> Interval:
+    """An interval holding every eigenvalue of A x = lambda B x.
+
+    Each eigenvalue is a Rayleigh quotient x^T A x / x^T B x.  Gershgorin's theorem bounds the
+    spectra of A and B: loA <= x^T A x / x^T x <= hiA, 0 < loB <= x^T B x / x^T x <= hiB (B's
+    lower bound must be positive).  Hence lambda >= loA / (loB if loA < 0 else hiB) and
+    lambda <= hiA / (loB if hiA > 0 else hiB).  The ends are widened by pad * max(|lo|, |hi|, 1)
+    so that nu(lower) = 0 and nu(upper) = n."""
+    def bounds(M):
+        M = M.tocsr() if hasattr(M, "tocsr") else np.asarray(M)
+        d = M.diagonal() if hasattr(M, "diagonal") else np.diag(M)
+        r = np.asarray(abs(M).sum(axis=1)).ravel() - np.abs(d)
+        return float(np.min(d - r)), float(np.max(d + r))
+    loA, hiA = bounds(A)
+    loB, hiB = bounds(B)
+    if not loB > 0.0:
+        raise ValueError("B's Gershgorin lower bound is not positive")
+    lo = loA / (loB if loA < 0 else hiB)
+    hi = hiA / (loB if hiA > 0 else hiB)
+    w = pad * max(abs(lo), abs(hi), 1.0)
+    n = A.shape[0]
+    return Interval(lo - w, hi + w, 0, n, [])
+
+
+def gershgorin_columns_interval(A: np.ndarray, B: np.ndarray) -> tuple[float, float]:
+    """The construction of the Gershgorin variant of Section 4.2: the columns of C = B^{-1} A
+    (linear solves), then the union of the column discs |z - c_jj| <= sum_{i != j} |c_ij|, whose
+    real extent holds the spectrum of B^{-1} A."""
+    C = np.linalg.solve(np.asarray(B, dtype=np.float64), np.asarray(A, dtype=np.float64))
+    d = np.diag(C)
+    r = np.abs(C).sum(axis=0) - np.abs(d)
+    return float(np.min(d - r)), float(np.max(d + r))
+
+
 def bisect_straight(ops, k: int, lo: float, hi: float, rel_tol: float = 1e-14,
                     max_iter: int = 200):
     """Algorithm 1 with the stop (sigma_u - sigma_l)/max(|sigma_l|, |sigma_u|) < rel_tol of the
@@ -286,10 +347,12 @@ class ThreeStageResult:
 
 
 def three_stage(ops, k: int, v1: np.ndarray, vt1: np.ndarray, m_max: int = 20,
-                tau_res: float = 1e-10, tau_diff: float = 1e-10) -> ThreeStageResult:
-    """Algorithm 4: Algorithm 2, then Algorithm 1', then Algorithm 3."""
-    iv0 = lanczos_interval(ops, k, v1)
-    iv1 = bisect_mmax(ops, k, iv0, m_max)
+                tau_res: float = 1e-10, tau_diff: float = 1e-10, init: str = "lanczos",
+                nshift: int = 1) -> ThreeStageResult:
+    """Algorithm 4: Algorithm 2 (or the Gershgorin interval of the variant), then Algorithm 1'
+    (bisection, or multisection with nshift points), then Algorithm 3."""
+    iv0 = gershgorin_interval(ops.A, ops.B) if init == "gershgorin" else lanczos_interval(ops, k, v1)
+    iv1 = multisect_mmax(ops, k, iv0, m_max, nshift)
     res = si_lanczos_kth(ops, k, iv1, vt1, tau_res, tau_diff)
     return ThreeStageResult(lam=res.lam, x=res.x, initial=iv0, narrowed=iv1, kth=res,
                             nfactor=ops.nfactor)

@@ -417,7 +417,7 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
     for (int32_t t = 0; t < nt; ++t) cnt[t + 1] += cnt[t];
     P.ent_ptr = cnt;
     int64_t ne = cnt[nt];
-    P.ent_r.resize(ne); P.ent_c.resize(ne); P.ent_a.resize(ne); P.ent_b.resize(ne);
+    P.ent_r.resize(ne); P.ent_c.resize(ne); P.ent_a.resize(ne); P.ent_b.resize(ne); P.ent_src.resize(ne);
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
     for (int64_t i = 0; i < n; ++i) {
       int32_t I = P.iperm[i];
@@ -435,7 +435,7 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
           r = pp + static_cast<int32_t>(it - pc.begin());
         }
         int64_t o = fill[t]++;
-        P.ent_r[o] = r; P.ent_c[o] = J - pf; P.ent_a[o] = av[e]; P.ent_b[o] = bv[e];
+        P.ent_r[o] = r; P.ent_c[o] = J - pf; P.ent_a[o] = av[e]; P.ent_b[o] = bv[e]; P.ent_src[o] = e;
       }
     }
   }

@@ -218,6 +218,8 @@ void kep_default_params(kep_params* p) {
   p->max_si = 300;
   p->start_vectors = nullptr;
   p->seed = 0x5eed;
+  p->init = KEP_INIT_LANCZOS;
+  p->nshift = 1;
 }
 
 const char* kep_status_str(kep_status s) {
@@ -265,16 +267,19 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   const int64_t nnz = cnt[n];
   std::vector<int32_t> ci(nnz);
   std::vector<double> av(nnz), bv(nnz);
+  std::vector<int64_t> src(nnz);          // caller entry of each full-CSR position
+  std::vector<int64_t> in2csr(nnz_in);    // full-CSR position of each caller entry (before sorting)
   {
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
     for (int64_t i = 0; i < n; ++i)
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
         int64_t j = colind[e];
         int64_t o = fill[i]++;
-        ci[o] = static_cast<int32_t>(j); av[o] = a_val[e]; bv[o] = b_val[e];
+        ci[o] = static_cast<int32_t>(j); av[o] = a_val[e]; bv[o] = b_val[e]; src[o] = e;
+        in2csr[e] = o;
         if (lower && j != i) {
           int64_t o2 = fill[j]++;
-          ci[o2] = static_cast<int32_t>(i); av[o2] = a_val[e]; bv[o2] = b_val[e];
+          ci[o2] = static_cast<int32_t>(i); av[o2] = a_val[e]; bv[o2] = b_val[e]; src[o2] = e;
         }
       }
   }
@@ -289,12 +294,31 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
     for (int64_t e = e0; e < e1; ++e) idx[e - e0] = e;
     std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return ci[x] < ci[y]; });
     std::vector<int32_t> c2(e1 - e0); std::vector<double> a2(e1 - e0), b2(e1 - e0);
-    for (int64_t k = 0; k < e1 - e0; ++k) { c2[k] = ci[idx[k]]; a2[k] = av[idx[k]]; b2[k] = bv[idx[k]]; }
-    for (int64_t k = 0; k < e1 - e0; ++k) { ci[e0 + k] = c2[k]; av[e0 + k] = a2[k]; bv[e0 + k] = b2[k]; }
+    std::vector<int64_t> s2(e1 - e0);
+    for (int64_t k = 0; k < e1 - e0; ++k) {
+      c2[k] = ci[idx[k]]; a2[k] = av[idx[k]]; b2[k] = bv[idx[k]]; s2[k] = src[idx[k]];
+    }
+    for (int64_t k = 0; k < e1 - e0; ++k) {
+      ci[e0 + k] = c2[k]; av[e0 + k] = a2[k]; bv[e0 + k] = b2[k]; src[e0 + k] = s2[k];
+    }
     for (int64_t e = e0 + 1; e < e1; ++e) if (ci[e] == ci[e - 1]) return KEP_ERR_INVALID;
+  }
+  {
+    // the caller's entries' final positions: the slot in the entry's own row (the mirrored slot
+    // of a lower off-diagonal entry carries the same value)
+    std::vector<int64_t> rowof(nnz_in);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) rowof[e] = i;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = cnt[i]; p < cnt[i + 1]; ++p) {
+        const int64_t e = src[p];
+        if (rowof[e] == i) in2csr[e] = p | ((lower && colind[e] != i) ? (1ll << 62) : 0ll);
+      }
   }
   kep_ctx* c = new (std::nothrow) kep_ctx();
   if (!c) return KEP_ERR_NOMEM;
+  c->nnz_in = nnz_in;
+  c->lower_in = lower;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return KEP_ERR_CUDA; }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   std::string err;
@@ -315,7 +339,9 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   UP(c->d_perm, P.perm);
   UP(c->d_iperm, P.iperm);
   UP(c->d_rp, cnt); UP(c->d_ci, ci); UP(c->d_a, av); UP(c->d_b, bv);
+  UP(c->d_in2csr, in2csr);
 #undef UP
+  c->csr_src = std::move(src);
   FrontTables& T = c->T;
   T.nfronts = P.nfronts;
   T.first = first; T.p_sym = p_sym; T.m_sym = m_sym; T.parent = parent;
@@ -432,6 +458,15 @@ kep_status kep_spmv(kep_ctx* c, const double* x, double* ax, double* bx, int ptr
   if (st != KEP_OK) return st;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
   c->timer.collect();
+  return KEP_OK;
+}
+
+kep_status kep_factor_multi(kep_ctx* c, const double* sigmas, int32_t ns, kep_inertia* out) {
+  if (!c || !sigmas || !out || ns < 1) return KEP_ERR_INVALID;
+  for (int32_t i = 0; i < ns; ++i) {
+    const kep_status st = kep_factor(c, sigmas[i], &out[i]);
+    if (st != KEP_OK && st != KEP_ERR_SINGULAR) return st;
+  }
   return KEP_OK;
 }
 

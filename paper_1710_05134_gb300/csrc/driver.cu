@@ -28,6 +28,43 @@
 namespace kep {
 
 // ----------------------------------------------------------------------------------------------
+// Gershgorin bounds of A and B (full symmetric CSR): per block the extremes of a_ii -+ r_i and
+// b_ii -+ s_i (r_i, s_i the off-diagonal absolute row sums) as [4][nblocks] = min lo_A, max hi_A,
+// min lo_B, max hi_B
+// ----------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) gershgorin_kernel(int64_t n, const int64_t* rp, const int32_t* ci,
+                                                         const double* a, const double* b, double* out) {
+  __shared__ double red[4][8];
+  double loA = INFINITY, hiA = -INFINITY, loB = INFINITY, hiB = -INFINITY;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double da = 0.0, db = 0.0, ra = 0.0, rb = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      if (ci[p] == i) { da = a[p]; db = b[p]; }
+      else { ra += fabs(a[p]); rb += fabs(b[p]); }
+    }
+    loA = fmin(loA, da - ra); hiA = fmax(hiA, da + ra);
+    loB = fmin(loB, db - rb); hiB = fmax(hiB, db + rb);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    loA = fmin(loA, __shfl_xor_sync(0xffffffffu, loA, o));
+    hiA = fmax(hiA, __shfl_xor_sync(0xffffffffu, hiA, o));
+    loB = fmin(loB, __shfl_xor_sync(0xffffffffu, loB, o));
+    hiB = fmax(hiB, __shfl_xor_sync(0xffffffffu, hiB, o));
+  }
+  const int w = threadIdx.x / 32;
+  if (threadIdx.x % 32 == 0) { red[0][w] = loA; red[1][w] = hiA; red[2][w] = loB; red[3][w] = hiB; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < 8; ++q) {
+      red[0][0] = fmin(red[0][0], red[0][q]); red[1][0] = fmax(red[1][0], red[1][q]);
+      red[2][0] = fmin(red[2][0], red[2][q]); red[3][0] = fmax(red[3][0], red[3][q]);
+    }
+    for (int k = 0; k < 4; ++k) out[k * gridDim.x + blockIdx.x] = red[k][0];
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
 // symmetric tridiagonal eigenproblem: implicit QR steps with Wilkinson shifts, applied as Givens
 // rotations to a dense copy (m is at most a few hundred here), rotations accumulated into z
 // ----------------------------------------------------------------------------------------------
@@ -260,7 +297,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
         cudaMalloc(&d->u, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&d->u2, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&d->coef, sizeof(double) * cap) != cudaSuccess ||
-        cudaMalloc(&d->partial, sizeof(double) * std::max<int64_t>(2, cap) * d->nblocks) != cudaSuccess) {
+        cudaMalloc(&d->partial, sizeof(double) * std::max<int64_t>(4, cap) * d->nblocks) != cudaSuccess) {
       c->driver_release();
       return KEP_ERR_NOMEM;
     }
@@ -274,13 +311,40 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   if (prm.start_vectors) std::memcpy(h_start.data(), prm.start_vectors, sizeof(double) * 2 * n);
   else { gaussian_vector(prm.seed, n, h_start.data()); gaussian_vector(prm.seed + 1, n, h_start.data() + n); }
 
-  // ---------------- stage 1: Algorithm 2 ----------------
   auto t0 = clock_::now();
+  double lo = 0, hi = 0;
+  int64_t nl = 0, nh = n;
+  double nrm = 0;
+  std::vector<double> alpha, beta;
+  if (prm.init == KEP_INIT_GERSHGORIN) {
+    // ---------------- stage 1, variant: an interval holding the whole spectrum ----------------
+    // Every eigenvalue is a Rayleigh quotient x^T A x / x^T B x; Gershgorin bounds of A and of B
+    // (B's lower bound positive) bound it: lambda >= loA / (loA < 0 ? loB : hiB) and
+    // lambda <= hiA / (hiA > 0 ? loB : hiB).  nu there is 0 and n without a factorization.
+    const int nb = d->nblocks;
+    KEP_LAUNCH(&c->timer, KC_VEC, c->stream,
+               gershgorin_kernel<<<nb, 256, 0, c->stream>>>(n, c->d_rp, c->d_ci, c->d_a, c->d_b, d->partial));
+    std::vector<double> g(4 * static_cast<size_t>(nb));
+    CTRY(cudaMemcpyAsync(g.data(), d->partial, sizeof(double) * 4 * nb, cudaMemcpyDeviceToHost, c->stream));
+    CTRY(cudaStreamSynchronize(c->stream));
+    double loA = INFINITY, hiA = -INFINITY, loB = INFINITY, hiB = -INFINITY;
+    for (int q = 0; q < nb; ++q) {
+      loA = std::min(loA, g[q]); hiA = std::max(hiA, g[nb + q]);
+      loB = std::min(loB, g[2 * nb + q]); hiB = std::max(hiB, g[3 * nb + q]);
+    }
+    if (!(loB > 0.0)) return KEP_ERR_INVALID;          // B not shown positive definite by its discs
+    lo = loA / (loA < 0 ? loB : hiB);
+    hi = hiA / (hiA > 0 ? loB : hiB);
+    const double pad = 1e-12 * std::max({std::fabs(lo), std::fabs(hi), 1.0});
+    lo -= pad;
+    hi += pad;
+    nl = 0;
+    nh = n;
+  } else {
+  // ---------------- stage 1: Algorithm 2 ----------------
   DTRY(R.factor_B());
   CTRY(cudaMemcpyAsync(d->V, h_start.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
-  double nrm = 0;
   DTRY(R.b_normalize(0, nrm));                        // v_1 := v_1 / ||v_1||_B
-  std::vector<double> alpha, beta;
   int64_t nu_prev = 0, nu_cur = 0;                    // nu^(0) := 0
   double sig_prev = 0, sig_cur = 0;
   bool bracketed = false;
@@ -310,19 +374,29 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     sig_prev = sig_cur;
   }
   if (!bracketed) return KEP_ERR_NOT_CONVERGED;
-  double lo = std::min(sig_prev, sig_cur), hi = std::max(sig_prev, sig_cur);
-  int64_t nl = std::min(nu_prev, nu_cur), nh = std::max(nu_prev, nu_cur);
+  lo = std::min(sig_prev, sig_cur); hi = std::max(sig_prev, sig_cur);
+  nl = std::min(nu_prev, nu_cur); nh = std::max(nu_prev, nu_cur);
+  }
   rep.init_lo = lo; rep.init_hi = hi; rep.init_nu_lo = nl; rep.init_nu_hi = nh;
   rep.t_stage[0] = seconds_since(t0);
 
-  // ---------------- stage 2: Algorithm 1' ----------------
+  // ---------------- stage 2: Algorithm 1' (bisection, or multisection with nshift points) ----------------
   t0 = clock_::now();
+  const int32_t ns = std::max(1, prm.nshift);
   while (nh - nl > prm.m_max) {
-    double s = 0.5 * (lo + hi);
-    int64_t nu = 0;
-    DTRY(R.nu_at(s, nu));
+    // points lo + (hi - lo) q / (ns + 1), q = 1..ns; keep the part [sigma_{q-1}, sigma_q) with
+    // nu(sigma_{q-1}) < k <= nu(sigma_q)
+    double plo = lo, phi = hi;
+    int64_t pnl = nl, pnh = nh;
+    for (int32_t q = 1; q <= ns; ++q) {
+      double s = ns == 1 ? 0.5 * (lo + hi) : lo + (hi - lo) * static_cast<double>(q) / (ns + 1);
+      int64_t nu = 0;
+      DTRY(R.nu_at(s, nu));
+      if (k <= nu) { phi = s; pnh = nu; break; }
+      plo = s; pnl = nu;
+    }
+    lo = plo; hi = phi; nl = pnl; nh = pnh;
     rep.n_bisect++;
-    if (k <= nu) { hi = s; nh = nu; } else { lo = s; nl = nu; }
     if (rep.n_bisect > 200) return KEP_ERR_CLUSTER;    // a multiple eigenvalue can stall the count
   }
   rep.sigma_lo = lo; rep.sigma_hi = hi; rep.nu_lo = nl; rep.nu_hi = nh;

@@ -23,6 +23,12 @@ struct kep_ctx {
   int32_t* d_ci = nullptr;
   double* d_a = nullptr;
   double* d_b = nullptr;
+  // the caller's layout (kep_analyze's CSR) against that pattern
+  int64_t nnz_in = 0;
+  bool lower_in = false;
+  std::vector<int64_t> csr_src;     // per full-CSR position: the caller's entry it came from
+  int64_t* d_in2csr = nullptr;      // per caller entry: its full-CSR position (bit 62: a lower
+                                    //   off-diagonal entry standing for both triangles)
   // factorization slots: 0 = the public "last factor" (kep_factor / kep_solve),
   // 1 = the factor of B kept by the eigenpair driver during stage 1
   kep::FactorSlot slot[2]{};

@@ -106,6 +106,7 @@ struct Plan {
   std::vector<int64_t> ent_ptr;     // original lower entries owned by front t
   std::vector<int32_t> ent_r, ent_c;// symbolic (row, col) positions inside the front
   std::vector<double> ent_a, ent_b; // A and B values of those entries
+  std::vector<int64_t> ent_src;     // position of each entry in the full symmetric CSR
   std::vector<int32_t> height;      // leaves 0
   int32_t nlevels = 0;
   std::vector<int32_t> level_ptr, level_fronts;   // fronts of each level, small ones first

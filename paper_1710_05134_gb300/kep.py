@@ -23,10 +23,11 @@ KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 # symbols declared in include/kep.h
 EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
-            "kep_set_timing_classes",
+            "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
             "kep_set_schur_mode"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
+KEP_INIT_LANCZOS, KEP_INIT_GERSHGORIN = 0, 1
 KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
                   "perm", "spmv", "vec", "slice", "flush_tc"]
 
@@ -55,7 +56,8 @@ class Info(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int64), ("tau_res", ctypes.c_double), ("tau_diff", ctypes.c_double),
                 ("max_lanczos", ctypes.c_int64), ("max_si", ctypes.c_int64),
-                ("start_vectors", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+                ("start_vectors", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("init", ctypes.c_int32), ("nshift", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -104,6 +106,9 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(Report)]
         L.kep_set_timing.argtypes = [P, I]
         L.kep_set_timing_classes.argtypes = [P, ctypes.c_uint]
+        L.kep_grad.argtypes = [P, D, P, D, P, P, I]
+        L.kep_set_values.argtypes = [P, P, P]
+        L.kep_factor_multi.argtypes = [P, P, ctypes.c_int32, P]
         L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
         L.kep_dense_inertia_noalloc.argtypes = [I64, P, P, I64, D, P, P]
         L.kep_dense_inertia_noalloc.restype = I
@@ -115,7 +120,7 @@ def lib() -> ctypes.CDLL:
         L.kep_status_str.restype = ctypes.c_char_p
         for name in ["kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
                      "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing", "kep_get_timing",
-                     "kep_set_timing_classes"]:
+                     "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi"]:
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -178,6 +183,7 @@ class Problem:
                              b.ctypes.data, flags, cp, ctypes.byref(h)), "kep_analyze")
         self._h = h
         self._stream = None
+        self.nnz = int(rowptr[-1])
 
     @classmethod
     def from_pencil(cls, p, **kw):
@@ -236,6 +242,38 @@ class Problem:
         d["flops"]["flush_fp64_equivalent"] = float(t.flush_fp64_equivalent_flops)
         return d
 
+    def factor_multi(self, sigmas):
+        """Inertia (neg, zero, pos, delayed) of A - sigma B for each shift of one multisection
+        step; the factor of the last shift stays for solve()."""
+        s = np.ascontiguousarray(sigmas, dtype=np.float64)
+        out = (Inertia * s.size)()
+        _check(lib().kep_factor_multi(self._h, s.ctypes.data, int(s.size), ctypes.byref(out)), "kep_factor_multi")
+        return [FactorResult(o.neg, o.zero, o.pos, o.delayed, KEP_OK) for o in out]
+
+    def set_values(self, a, b):
+        """New values of A and B on the analysed pattern (same layout as at construction)."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        if a.size != self.nnz or b.size != self.nnz:
+            raise ValueError("values must match the analysed pattern")
+        _check(lib().kep_set_values(self._h, a.ctypes.data, b.ctypes.data), "kep_set_values")
+
+    def grad(self, lam: float, x, lam_bar: float = 1.0):
+        """(d lambda / d a_vals, d lambda / d b_vals) in the layout of the analysed pattern
+        (Hellmann-Feynman), times lam_bar."""
+        if _is_device(x):
+            import torch
+            ga = torch.empty(self.nnz, dtype=torch.float64, device=x.device)
+            gb = torch.empty_like(ga)
+            _check(lib().kep_grad(self._h, float(lam), _dev_ptr(x), float(lam_bar), _dev_ptr(ga), _dev_ptr(gb),
+                                  KEP_DEVICE), "kep_grad")
+            return ga, gb
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        ga, gb = np.empty(self.nnz), np.empty(self.nnz)
+        _check(lib().kep_grad(self._h, float(lam), x.ctypes.data, float(lam_bar), ga.ctypes.data, gb.ctypes.data,
+                              KEP_HOST), "kep_grad")
+        return ga, gb
+
     def factor(self, sigma: float, *, allow_singular: bool = True) -> FactorResult:
         """LDL^T of A - sigma*B; .nu is the number of eigenvalues below sigma."""
         return self.factor_pencil(1.0, -float(sigma), allow_singular=allow_singular)
@@ -275,12 +313,16 @@ class Problem:
 
     def kth_eigenpair(self, k: int, *, m_max: int = 20, tau_res: float = 1e-10, tau_diff: float = 1e-10,
                       max_lanczos: int = 200, max_si: int = 300, start_vectors=None, seed: int = 0x5eed,
-                      want_vector: bool = True):
-        """Algorithm 4: (lambda_k, x_k (B-normalized), report dict)."""
+                      want_vector: bool = True, init: str = "lanczos", nshift: int = 1):
+        """Algorithm 4: (lambda_k, x_k (B-normalized), report dict).  init: "lanczos" (Algorithm 2)
+        or "gershgorin" (an interval holding the whole spectrum); nshift: shifts per Algorithm 1'
+        step (1 = bisection)."""
         prm = Params()
         lib().kep_default_params(ctypes.byref(prm))
         prm.m_max, prm.tau_res, prm.tau_diff = int(m_max), float(tau_res), float(tau_diff)
         prm.max_lanczos, prm.max_si, prm.seed = int(max_lanczos), int(max_si), int(seed)
+        prm.init = {"lanczos": KEP_INIT_LANCZOS, "gershgorin": KEP_INIT_GERSHGORIN}[init]
+        prm.nshift = int(nshift)
         sv = None
         if start_vectors is not None:
             sv = np.ascontiguousarray(start_vectors, dtype=np.float64).reshape(-1)
@@ -294,3 +336,37 @@ class Problem:
                                        x.ctypes.data if x is not None else None, ctypes.byref(rep)),
                "kep_kth_eigenpair")
         return lam.value, x, rep.asdict()
+
+
+class KthEigenvalue:
+    """lambda_k of A x = lambda B x as a differentiable function of the stored values of A and B
+    (torch.autograd; gradients by the Hellmann-Feynman theorem through kep_grad).
+
+        lam = KthEigenvalue.apply(problem, k, a_vals, b_vals)
+
+    a_vals, b_vals: float64 tensors in the layout of the problem's pattern; the forward pass loads
+    them with set_values and runs Algorithm 4 (kwargs of kth_eigenpair via problem.kth_kwargs)."""
+
+    @staticmethod
+    def _fn():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, problem, k, a_vals, b_vals):
+                problem.set_values(a_vals.detach().cpu().numpy(), b_vals.detach().cpu().numpy())
+                lam, x, _ = problem.kth_eigenpair(int(k), **getattr(problem, "kth_kwargs", {}))
+                ctx.problem, ctx.lam, ctx.x = problem, lam, x
+                return torch.tensor(lam, dtype=torch.float64, device=a_vals.device)
+
+            @staticmethod
+            def backward(ctx, lam_bar):
+                ga, gb = ctx.problem.grad(ctx.lam, ctx.x, float(lam_bar))
+                dev = lam_bar.device
+                return (None, None, torch.from_numpy(ga).to(dev), torch.from_numpy(gb).to(dev))
+
+        return _F
+
+    @classmethod
+    def apply(cls, problem, k, a_vals, b_vals):
+        return cls._fn().apply(problem, k, a_vals, b_vals)

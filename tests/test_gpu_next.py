@@ -1,0 +1,124 @@
+"""GPU parity of the next rows: Hellmann-Feynman derivatives (kep_grad, the torch autograd wrapper),
+new values on an analysed pattern (kep_set_values), the Gershgorin initial interval and
+multisection in Algorithm 4, and kep_factor_multi.
+
+References: the oracle's dense generalized eigensolver (c2) and its derivative formula (pinned by
+finite differences in test_oracle_next.py), and the oracle's Gershgorin interval."""
+import numpy as np
+import pytest
+
+from gen import make_pair
+from oracle import core, three_stage as ts
+from tests.gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kep():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def pen():
+    p = make_pair(3, 3, 2, seed=21)          # n = 576
+    A, B = p.A().toarray(), p.B().toarray()
+    lam, X = core.gen_eig(A, B)
+    return p, A, B, lam, X
+
+
+def _entries(p):
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    return rows, p.colind
+
+
+def test_grad_full_pattern(kep, pen):
+    p, A, B, lam, X = pen
+    k = p.k
+    with kep.Problem.from_pencil(p) as P:
+        lam_g, x, _ = P.kth_eigenpair(k)
+        ga, gb = P.grad(lam_g, x, 1.0)
+    _, GA, GB = core.eig_grad(A, B, k)
+    r, c = _entries(p)
+    scale = np.abs(GA).max()
+    assert np.abs(ga - GA[r, c]).max() <= 1e-8 * scale
+    assert np.abs(gb - GB[r, c]).max() <= 1e-8 * scale * max(1.0, abs(lam[k - 1]))
+    # lambda_bar scales both
+    with kep.Problem.from_pencil(p) as P:
+        ga3, _ = P.grad(lam_g, 2.0 * x, 3.0)   # any scaling of x
+    assert np.abs(ga3 - 3.0 * ga).max() <= 1e-12 * scale
+
+
+def test_grad_lower_pattern_device(kep, pen):
+    import torch
+    p, A, B, lam, X = pen
+    k = p.k + 3
+    rows, cols = _entries(p)
+    keep = cols <= rows
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=p.n))])
+    with kep.Problem(p.n, rp, cols[keep], p.a[keep], p.b[keep], p.coords, lower=True) as P:
+        lam_g, x, _ = P.kth_eigenpair(k)
+        ga, gb = P.grad(lam_g, torch.from_numpy(x).cuda(), 1.0)
+    _, GA, GB = core.eig_grad(A, B, k)
+    r, c = rows[keep], cols[keep]
+    want = GA[r, c] * np.where(r != c, 2.0, 1.0)
+    scale = np.abs(GA).max()
+    assert np.abs(ga.cpu().numpy() - want).max() <= 1e-8 * scale
+    assert np.abs(gb.cpu().numpy() + lam[k - 1] * want).max() <= 1e-8 * scale * max(1.0, abs(lam[k - 1]))
+
+
+def test_autograd_and_set_values(kep, pen):
+    import torch
+    p, A, B, lam, X = pen
+    k = p.k
+    a = torch.tensor(p.a, requires_grad=True)
+    b = torch.tensor(p.b, requires_grad=True)
+    with kep.Problem.from_pencil(p) as P:
+        lam_t = kep.KthEigenvalue.apply(P, k, a, b)
+        (2.0 * lam_t).backward()
+        assert abs(float(lam_t.detach()) - lam[k - 1]) <= 1e-10 * np.abs(A).sum(1).max()
+        _, GA, GB = core.eig_grad(A, B, k)
+        r, c = _entries(p)
+        scale = np.abs(GA).max()
+        assert np.abs(a.grad.numpy() - 2.0 * GA[r, c]).max() <= 1e-8 * scale
+        # new values on the same pattern: A -> 2 A doubles every eigenvalue (closed form)
+        P.set_values(2.0 * p.a, p.b)
+        lam2, _, _ = P.kth_eigenpair(k)
+        assert abs(lam2 - 2.0 * lam[k - 1]) <= 2e-10 * np.abs(A).sum(1).max()
+        sig = 2.0 * 0.5 * (lam[k - 1] + lam[k])
+        assert P.factor(sig).neg == core.count_below(2.0 * lam, sig)
+
+
+def test_gershgorin_multisection_driver(kep, pen):
+    p, A, B, lam, X = pen
+    k = p.k
+    nrm = np.abs(A).sum(1).max()
+    iv = ts.gershgorin_interval(A, B)
+    with kep.Problem.from_pencil(p) as P:
+        for nshift in (1, 8):
+            lam_g, x, rep = P.kth_eigenpair(k, init="gershgorin", nshift=nshift)
+            assert abs(lam_g - lam[k - 1]) <= 1e-10 * nrm
+            assert rep["init_nu_lo"] == 0 and rep["init_nu_hi"] == p.n
+            assert abs(rep["init_lo"] - iv.lower) <= 1e-12 * abs(iv.lower)
+            assert abs(rep["init_hi"] - iv.upper) <= 1e-12 * abs(iv.upper)
+            assert rep["nu_lo"] < k <= rep["nu_hi"] and rep["nu_hi"] - rep["nu_lo"] <= 20
+            assert core.count_below(lam, rep["sigma_lo"]) == rep["nu_lo"]
+            assert core.count_below(lam, rep["sigma_hi"]) == rep["nu_hi"]
+            if nshift == 8:
+                # the oracle's multisection from the same interval ends in the same place
+                r = ts.multisect_mmax(ts.DenseOps(A, B), k, iv, 20, 8)
+                assert (r.nu_lower, r.nu_upper) == (rep["nu_lo"], rep["nu_hi"])
+
+
+def test_factor_multi(kep, pen):
+    p, A, B, lam, X = pen
+    sig = core.certified_shifts(lam, 6, 1e-8 * np.abs(A).sum(1).max(), seed=4)
+    with kep.Problem.from_pencil(p) as P:
+        res = P.factor_multi(sig)
+        assert [r.neg for r in res] == [core.count_below(lam, s) for s in sig]
+        assert all(r.neg + r.zero + r.pos == p.n for r in res)
+        # the last factor stays for solve
+        rhs = np.random.default_rng(2).normal(size=p.n)
+        y = P.solve(rhs)
+        M = A - sig[-1] * B
+        assert np.linalg.norm(M @ y - rhs) <= 1e-11 * np.abs(M).sum(1).max() * np.linalg.norm(y)
