@@ -85,9 +85,15 @@ typedef struct {
                                  the variant of Section 4.2) */
   int32_t nshift;             /* shifts per Algorithm 1' step: 1 bisection (default), s > 1
                                  multisection into s + 1 equal parts */
+  int32_t solve_precision;    /* Algorithm 3's factor and solves: KEP_SOLVE_F64 (default) or
+                                 KEP_SOLVE_F32_IR (KEP_SCHUR_FP32 factor, every solve refined in
+                                 FP64 to a normwise backward error <= 1e-13; the inertia
+                                 factorizations of stages 1-2 stay FP64-accurate) */
+  int32_t reserved;           /* 0 */
 } kep_params;
 
 enum { KEP_INIT_LANCZOS = 0, KEP_INIT_GERSHGORIN = 1 };
+enum { KEP_SOLVE_F64 = 0, KEP_SOLVE_F32_IR = 1 };
 
 /* Report of kep_kth_eigenpair. */
 typedef struct {
@@ -105,6 +111,8 @@ typedef struct {
   int64_t n_si_iter;          /* Algorithm 3 iterations */
   int64_t si_iter_bound;      /* first Algorithm 3 iteration with inclusion and disjointness */
   double t_stage[3];          /* seconds spent in stages 1, 2, 3 */
+  int64_t n_refine;           /* refinement corrections in Algorithm 3 (KEP_SOLVE_F32_IR) */
+  double solve_berr;          /* largest final backward error of those solves */
 } kep_report;
 
 void kep_default_params(kep_params* p);
@@ -138,9 +146,13 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind,
  *                       into eight 8-bit pieces per entry (column balancing, per-row power-of-two
  *                       scales, exact FP32 level sums, exact int64 combination): as accurate as an
  *                       FP64 update, on the tensor pipe.
+ *   KEP_SCHUR_FP32      every Schur update in FP32 FMA (pivot blocks and L21 stay FP64): a
+ *                       reduced-precision factor (backward error near FP32 rounding) for
+ *                       kep_solve_refined; its inertia is that of a nearby matrix, so inertia
+ *                       counts should come from the other modes.
  * Takes effect at the next factorization.  Errors: KEP_ERR_INVALID.
  */
-enum { KEP_SCHUR_FP64 = 0, KEP_SCHUR_EMULATED = 1 };
+enum { KEP_SCHUR_FP64 = 0, KEP_SCHUR_EMULATED = 1, KEP_SCHUR_FP32 = 2 };
 kep_status kep_set_schur_mode(kep_ctx* ctx, int mode, int64_t min_front);
 
 /* Fill *info with the symbolic facts of ctx. */
@@ -185,6 +197,18 @@ kep_status kep_factor_pencil(kep_ctx* ctx, double ca, double cb, kep_inertia* ou
  * Returns KEP_ERR_INVALID if no factorization is present, KEP_ERR_SINGULAR if it had a zero pivot.
  */
 kep_status kep_solve(kep_ctx* ctx, const double* rhs, double* x, int64_t nrhs, int ptr_kind);
+
+/*
+ * kep_solve_refined - x = (ca*A + cb*B)^{-1} b by iterative refinement with the last factor
+ * (typically a KEP_SCHUR_FP32 one): x_0 = solve(b); r = b - M x_i in FP64 (sparse products);
+ * x_{i+1} = x_i + solve(r), until the normwise backward error
+ *   ||b - M x||_inf / (||M||_inf ||x||_inf + ||b||_inf),  ||M||_inf <= |ca| ||A||_inf + |cb| ||B||_inf,
+ * is <= tol or max_iter corrections were made.  One right-hand side (n doubles, ptr_kind memory).
+ * *iters (corrections made) and *berr (final backward error) may be NULL.  Returns
+ * KEP_ERR_NOT_CONVERGED if tol was not reached, KEP_ERR_INVALID without a valid factor.
+ */
+kep_status kep_solve_refined(kep_ctx* ctx, const double* rhs, double* x, int ptr_kind, double tol,
+                             int32_t max_iter, int32_t* iters, double* berr);
 
 /*
  * kep_spmv - ax = A x and bx = B x (the products of Eqs. 2.2 and 2.5), original numbering.

@@ -136,6 +136,7 @@ kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inert
   F.timer = &c->timer;
   F.flops = c->d_flops;
   F.emul_min = c->schur_mode == KEP_SCHUR_EMULATED ? c->emul_min_front : 0;
+  F.fp32_schur = c->schur_mode == KEP_SCHUR_FP32;
   F.emul_ws = nullptr;
   F.emul_cap_rows = 0;
   if (F.emul_min > 0) {
@@ -220,6 +221,8 @@ void kep_default_params(kep_params* p) {
   p->seed = 0x5eed;
   p->init = KEP_INIT_LANCZOS;
   p->nshift = 1;
+  p->solve_precision = KEP_SOLVE_F64;
+  p->reserved = 0;
 }
 
 const char* kep_status_str(kep_status s) {
@@ -317,6 +320,11 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   }
   kep_ctx* c = new (std::nothrow) kep_ctx();
   if (!c) return KEP_ERR_NOMEM;
+  for (int64_t i = 0; i < n; ++i) {
+    double r = 0.0;
+    for (int64_t p = cnt[i]; p < cnt[i + 1]; ++p) r += std::fabs(bv[p]);
+    c->norm_b_inf = std::max(c->norm_b_inf, r);
+  }
   c->nnz_in = nnz_in;
   c->lower_in = lower;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return KEP_ERR_CUDA; }
@@ -364,7 +372,7 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   if (cudaMemset(c->d_flops, 0, sizeof(unsigned long long) * (KC_COUNT + 1)) != cudaSuccess) { kep_destroy(c); return KEP_ERR_CUDA; }
   AL(c->d_bnew, P.n); AL(c->d_xnew, P.n);
   AL(c->d_solve_partial, static_cast<size_t>(c->num_sms) * 4 * (kSolveBlk + 1));
-  AL(c->d_io0, P.n); AL(c->d_io1, P.n); AL(c->d_io2, P.n);
+  AL(c->d_io0, P.n); AL(c->d_io1, P.n); AL(c->d_io2, P.n); AL(c->d_io3, P.n); AL(c->d_io4, P.n);
 #undef AL
   st = setup_memory(c);
   if (st != KEP_OK) { kep_destroy(c); return st; }
@@ -399,7 +407,8 @@ kep_status kep_set_stream(kep_ctx* c, void* stream) {
 }
 
 kep_status kep_set_schur_mode(kep_ctx* c, int mode, int64_t min_front) {
-  if (!c || (mode != KEP_SCHUR_FP64 && mode != KEP_SCHUR_EMULATED) || min_front < 1) return KEP_ERR_INVALID;
+  if (!c || (mode != KEP_SCHUR_FP64 && mode != KEP_SCHUR_EMULATED && mode != KEP_SCHUR_FP32) || min_front < 1)
+    return KEP_ERR_INVALID;
   c->schur_mode = mode;
   c->emul_min_front = min_front;
   return KEP_OK;
@@ -437,6 +446,113 @@ kep_status kep_solve(kep_ctx* c, const double* rhs, double* x, int64_t nrhs, int
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
   c->timer.collect();
   return KEP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void axpby_kernel(int64_t n, double a, const double* x, double b, double* y) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+__global__ void __launch_bounds__(256) absmax_kernel(int64_t n, const double* x, double* partial) {
+  __shared__ double red[8];
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    m = fmax(m, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+    partial[blockIdx.x] = fmax(m, red[0]);
+  }
+}
+}  // namespace
+
+// y = a x + b y on the device (ctx's stream)
+static kep_status vec_axpby_dev(kep_ctx* c, double a, const double* x, double b, double* y) {
+  const int64_t n = c->plan.n;
+  const int g = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->num_sms * 4, (n + 255) / 256)));
+  KEP_LAUNCH(&c->timer, KC_VEC, c->stream, axpby_kernel<<<g, 256, 0, c->stream>>>(n, a, x, b, y));
+  return cudaGetLastError() == cudaSuccess ? KEP_OK : KEP_ERR_CUDA;
+}
+
+// max |x_i| (synchronises the stream)
+static kep_status vec_norm_inf_dev(kep_ctx* c, const double* x, double* out) {
+  const int64_t n = c->plan.n;
+  const int g = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->num_sms * 4, (n + 255) / 256)));
+  KEP_LAUNCH(&c->timer, KC_VEC, c->stream, absmax_kernel<<<g, 256, 0, c->stream>>>(n, x, c->d_solve_partial));
+  std::vector<double> h(g);
+  if (cudaMemcpyAsync(h.data(), c->d_solve_partial, g * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  double m = 0.0;
+  for (double v : h) m = std::max(m, v);
+  *out = m;
+  return KEP_OK;
+}
+
+// y = (ca A + cb B) x for the pencil of the last factor (device vectors; t1: scratch)
+static kep_status pencil_apply(kep_ctx* c, const double* x, double* y, double* t1) {
+  KEP_TRY(ctx_spmv_dev(c, x, y, t1));
+  const FactorSlot& S = c->slot[0];
+  return vec_axpby_dev(c, S.cb, t1, S.ca, y);
+}
+
+// Iterative refinement with the factor in slot 0, device vectors (b is not modified; scratch:
+// d_io2, d_io3, d_io4).
+kep_status kep::ctx_solve_refined_dev(kep_ctx* c, const double* b, double* xd, double tol, int32_t max_iter,
+                                      int32_t* iters, double* berr) {
+  const FactorSlot& S = c->slot[0];
+  if (!c->slot_ready[0] || !S.valid) return KEP_ERR_INVALID;
+  double *r = c->d_io2, *t = c->d_io3, *dx = c->d_io4;
+  // ||M||_inf bound for the backward error: |ca| ||A||_inf + |cb| ||B||_inf
+  const double norm_m = std::fabs(S.ca) * c->plan.norm_a_inf + std::fabs(S.cb) * c->norm_b_inf;
+  KEP_TRY(ctx_solve_dev(c, 0, b, xd));
+  double bn;
+  KEP_TRY(vec_norm_inf_dev(c, b, &bn));
+  double eta = 0.0;
+  int32_t it = 0;
+  while (true) {
+    KEP_TRY(pencil_apply(c, xd, t, r));                  // t = M x
+    KEP_TRY(vec_axpby_dev(c, 1.0, b, -1.0, t));          // t = b - M x
+    double rn, xn;
+    KEP_TRY(vec_norm_inf_dev(c, t, &rn));
+    KEP_TRY(vec_norm_inf_dev(c, xd, &xn));
+    eta = rn / (norm_m * xn + bn);
+    if (!(eta > tol) || it >= max_iter) break;
+    KEP_TRY(ctx_solve_dev(c, 0, t, dx));                 // correction with the (reduced-precision) factor
+    KEP_TRY(vec_axpby_dev(c, 1.0, dx, 1.0, xd));
+    ++it;
+  }
+  if (iters) *iters = it;
+  if (berr) *berr = eta;
+  return std::isfinite(eta) && eta <= tol ? KEP_OK : KEP_ERR_NOT_CONVERGED;
+}
+
+extern "C" {
+
+kep_status kep_solve_refined(kep_ctx* c, const double* rhs, double* x, int ptr_kind, double tol, int32_t max_iter,
+                             int32_t* iters, double* berr) {
+  if (!c || !rhs || !x || tol < 0 || max_iter < 0) return KEP_ERR_INVALID;
+  if (ptr_kind != KEP_HOST && ptr_kind != KEP_DEVICE) return KEP_ERR_INVALID;
+  const int64_t n = c->plan.n;
+  cudaStream_t st = c->stream;
+  double *b = c->d_io0, *xd = c->d_io1;
+  if (cudaMemcpyAsync(b, rhs, n * sizeof(double), ptr_kind == KEP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                      st) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  const kep_status rs = ctx_solve_refined_dev(c, b, xd, tol, max_iter, iters, berr);
+  if (rs != KEP_OK && rs != KEP_ERR_NOT_CONVERGED) return rs;
+  if (cudaMemcpyAsync(x, xd, n * sizeof(double), ptr_kind == KEP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                      st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  c->timer.collect();
+  return rs;
 }
 
 kep_status kep_spmv(kep_ctx* c, const double* x, double* ax, double* bx, int ptr_kind) {

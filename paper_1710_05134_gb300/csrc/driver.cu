@@ -406,10 +406,25 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   t0 = clock_::now();
   const int64_t l = k - nl, mm = nh - nl;
   double sigma = 0.5 * (lo + hi);
+  const bool f32ir = prm.solve_precision == KEP_SOLVE_F32_IR;
   {
     int64_t nu_mid = 0;
-    DTRY(R.nu_at(sigma, nu_mid));                     // factor of A - sigma B kept in slot 0
+    const int mode = c->schur_mode;
+    if (f32ir) c->schur_mode = KEP_SCHUR_FP32;         // reduced-precision factor, refined solves
+    const kep_status fs = R.nu_at(sigma, nu_mid);     // factor of A - sigma B kept in slot 0
+    c->schur_mode = mode;
+    DTRY(fs);
   }
+  // w = (A - sigma B)^{-1} rhs with the factor in slot 0 (refined when it is a reduced one)
+  auto shifted_solve = [&](const double* rhs, double* out) -> kep_status {
+    if (!f32ir) return ctx_solve_dev(c, 0, rhs, out);
+    int32_t it = 0;
+    double be = 0.0;
+    const kep_status st = ctx_solve_refined_dev(c, rhs, out, 1e-13, 30, &it, &be);
+    rep.n_refine += it;
+    rep.solve_berr = std::max(rep.solve_berr, be);
+    return st;
+  };
   // v_1 = B^{-1} v~_1, so that ||v_1||_B = ||v~_1||_{B^{-1}}
   CTRY(cudaMemcpyAsync(d->u, h_start.data() + n, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
   DTRY(R.solve_B(d->u, d->V));
@@ -431,7 +446,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   for (int64_t j = 1; j <= prm.max_si && j + 1 < cap; ++j) {
     double* vj = R.col(d->V, j - 1);
     double* bvj = R.col(d->BV, j - 1);
-    DTRY(ctx_solve_dev(c, 0, bvj, d->w));             // w = (A - sigma B)^{-1} B v_j
+    DTRY(shifted_solve(bvj, d->w));                   // w = (A - sigma B)^{-1} B v_j
     double a = 0;
     DTRY(R.dots(bvj, 1, d->w, &a));                   // alpha~_j = (B v_j)^T w
     R.ops.axpby(-a, vj, 1.0, d->w);

@@ -620,11 +620,12 @@ struct Part {
 //                  window accepted (c0 = window start, c1 = its last accepted pivot + 1,
 //                  s = ce' = window end, ce = m), issued once per window ("flush").
 // 64 x 64 tiles, 256 threads with 4 x 4 FP64 register tiles, the pivot range in chunks of 32.
-template <bool WINDOW>
+// R: arithmetic of the tiles (double, or float for the reduced-precision factorization mode)
+template <bool WINDOW, typename R>
 __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot S, double* cbpool,
                                                        LargeWork W, Batch B, unsigned long long* flops) {
-  __shared__ double Ai[kPanel][kTile + 1];
-  __shared__ double Wj[kPanel][kTile + 1];
+  __shared__ R Ai[kPanel][kTile + 1];
+  __shared__ R Wj[kPanel][kTile + 1];
   const int32_t b = B.e0 + blockIdx.y;
   int32_t c0, c1, s, ce;
   if (WINDOW) {
@@ -671,11 +672,11 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot
     const int32_t bi = bj + static_cast<int32_t>(tile - stj);
     const int32_t I0 = P.lo(bi), I1 = P.hi(bi);
     const int32_t J0 = P.lo(bj), J1 = min(P.hi(bj), ce);
-    double acc[4][4];
+    R acc[4][4];
 #pragma unroll
     for (int32_t x = 0; x < 4; ++x)
 #pragma unroll
-      for (int32_t y = 0; y < 4; ++y) acc[x][y] = 0.0;
+      for (int32_t y = 0; y < 4; ++y) acc[x][y] = R(0);
     for (int32_t k0 = c0; k0 < c1; k0 += kPanel) {
       const int32_t kn = min(kPanel, c1 - k0);
       __syncthreads();
@@ -700,12 +701,12 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot
             }
           }
         }
-        Ai[cc][r] = ai;
-        Wj[cc][r] = wj;
+        Ai[cc][r] = static_cast<R>(ai);
+        Wj[cc][r] = static_cast<R>(wj);
       }
       __syncthreads();
       for (int32_t cc = 0; cc < kn; ++cc) {
-        double a[4], wv[4];
+        R a[4], wv[4];
 #pragma unroll
         for (int32_t x = 0; x < 4; ++x) a[x] = Ai[cc][ty + 16 * x];
 #pragma unroll
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot
 #pragma unroll
       for (int32_t x = 0; x < 4; ++x) {
         const int32_t i = I0 + ty + 16 * x;
-        if (i < I1 && i >= j) *v.at(i, j) -= acc[x][y];
+        if (i < I1 && i >= j) *v.at(i, j) -= static_cast<double>(acc[x][y]);
       }
     }
   }
@@ -833,13 +834,20 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
                                F.num_sms, F.timer, F.flops);
             launch_emul_update(false, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
                                F.num_sms, F.timer, F.flops);
+          } else if (F.fp32_schur) {
+            KEP_LAUNCH(F.timer, KC_UPDATE, st,
+                       lf_schur_kernel<true, float><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
+                                                                                     F.flops + KC_UPDATE));
+            KEP_LAUNCH(F.timer, KC_UPDATE, st,
+                       lf_schur_kernel<false, float><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
+                                                                                       F.flops + KC_UPDATE));
           } else {
             KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                       lf_schur_kernel<true><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
-                                                                              F.flops + KC_UPDATE));
+                       lf_schur_kernel<true, double><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
+                                                                                      F.flops + KC_UPDATE));
             KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                       lf_schur_kernel<false><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
-                                                                                F.flops + KC_UPDATE));
+                       lf_schur_kernel<false, double><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
+                                                                                        F.flops + KC_UPDATE));
           }
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
         }

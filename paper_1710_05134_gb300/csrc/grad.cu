@@ -116,11 +116,12 @@ extern "C" kep_status kep_set_values(kep_ctx* c, const double* a_val, const doub
   std::vector<int64_t> rp(n + 1);
   if (cudaMemcpy(rp.data(), c->d_rp, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
     return KEP_ERR_CUDA;
-  double norm = 0.0;
+  double norm = 0.0, norm_b = 0.0;
   for (int64_t i = 0; i < n; ++i) {
-    double r = 0.0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) r += std::fabs(av[p]);
+    double r = 0.0, rb = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) { r += std::fabs(av[p]); rb += std::fabs(bv[p]); }
     norm = std::max(norm, r);
+    norm_b = std::max(norm_b, rb);
   }
   const int64_t ne = static_cast<int64_t>(P.ent_src.size());
   for (int64_t o = 0; o < ne; ++o) {
@@ -134,6 +135,7 @@ extern "C" kep_status kep_set_values(kep_ctx* c, const double* a_val, const doub
       cudaMemcpy(const_cast<double*>(c->T.ent_b), P.ent_b.data(), ne * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return KEP_ERR_CUDA;
   P.norm_a_inf = norm;
+  c->norm_b_inf = norm_b;
   for (int s = 0; s < 2; ++s) c->slot[s].valid = false;   // factors of the old values are void
   return KEP_OK;
 }

@@ -49,6 +49,9 @@ struct kep_ctx {
   double* d_io0 = nullptr;
   double* d_io1 = nullptr;
   double* d_io2 = nullptr;
+  double* d_io3 = nullptr;
+  double* d_io4 = nullptr;
+  double norm_b_inf = 0;            // ||B||_inf
   double* d_solve_partial = nullptr;
   std::vector<int32_t> slot_nelim[2];   // pivots eliminated per front, per slot (host copy)
   kep::Timer timer;
@@ -65,4 +68,6 @@ namespace kep {
 kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out);
 kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x);
 kep_status ctx_spmv_dev(kep_ctx* c, const double* x, double* ax, double* bx);
+kep_status ctx_solve_refined_dev(kep_ctx* c, const double* b, double* x, double tol, int32_t max_iter,
+                                 int32_t* iters, double* berr);
 }  // namespace kep

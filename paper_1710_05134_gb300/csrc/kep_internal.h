@@ -237,6 +237,7 @@ struct FactorLaunch {
   int num_sms;
   Timer* timer;
   int64_t emul_min;         // fronts with m_alloc >= this use the tensor-core flush (0: never)
+  bool fp32_schur = false;  // Schur tiles in FP32 arithmetic (reduced-precision factor for refined solves)
   void* emul_ws;            // its workspace
   int64_t emul_cap_rows;
   unsigned long long* flops;   // per kernel class: algorithmic flops, counted on the device

@@ -23,11 +23,13 @@ KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 # symbols declared in include/kep.h
 EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
-            "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi",
+            "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi", "kep_solve_refined",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
             "kep_set_schur_mode"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
 KEP_INIT_LANCZOS, KEP_INIT_GERSHGORIN = 0, 1
+KEP_SOLVE_F64, KEP_SOLVE_F32_IR = 0, 1
+KEP_SCHUR_FP32 = 2
 KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
                   "perm", "spmv", "vec", "slice", "flush_tc"]
 
@@ -57,7 +59,8 @@ class Params(ctypes.Structure):
     _fields_ = [("m_max", ctypes.c_int64), ("tau_res", ctypes.c_double), ("tau_diff", ctypes.c_double),
                 ("max_lanczos", ctypes.c_int64), ("max_si", ctypes.c_int64),
                 ("start_vectors", ctypes.c_void_p), ("seed", ctypes.c_uint64),
-                ("init", ctypes.c_int32), ("nshift", ctypes.c_int32)]
+                ("init", ctypes.c_int32), ("nshift", ctypes.c_int32),
+                ("solve_precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -74,7 +77,8 @@ class Report(ctypes.Structure):
                 ("init_nu_lo", ctypes.c_int64), ("init_nu_hi", ctypes.c_int64),
                 ("n_factor", ctypes.c_int64), ("n_lanczos", ctypes.c_int64),
                 ("n_bisect", ctypes.c_int64), ("n_si_iter", ctypes.c_int64),
-                ("si_iter_bound", ctypes.c_int64), ("t_stage", ctypes.c_double * 3)]
+                ("si_iter_bound", ctypes.c_int64), ("t_stage", ctypes.c_double * 3),
+                ("n_refine", ctypes.c_int64), ("solve_berr", ctypes.c_double)]
 
     def asdict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_stage"}
@@ -109,6 +113,7 @@ def lib() -> ctypes.CDLL:
         L.kep_grad.argtypes = [P, D, P, D, P, P, I]
         L.kep_set_values.argtypes = [P, P, P]
         L.kep_factor_multi.argtypes = [P, P, ctypes.c_int32, P]
+        L.kep_solve_refined.argtypes = [P, P, P, I, D, ctypes.c_int32, P, P]
         L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
         L.kep_dense_inertia_noalloc.argtypes = [I64, P, P, I64, D, P, P]
         L.kep_dense_inertia_noalloc.restype = I
@@ -120,7 +125,8 @@ def lib() -> ctypes.CDLL:
         L.kep_status_str.restype = ctypes.c_char_p
         for name in ["kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
                      "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing", "kep_get_timing",
-                     "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi"]:
+                     "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi",
+                     "kep_solve_refined"]:
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
@@ -218,11 +224,29 @@ class Problem:
         self._stream = stream
         _check(lib().kep_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)), "kep_set_stream")
 
-    def set_schur_mode(self, emulated: bool, min_front: int = 4096):
+    def set_schur_mode(self, emulated: bool, min_front: int = 4096, *, fp32: bool = False):
         """Deferred Schur updates of fronts of order >= min_front on the tensor cores (FP64-accurate
-        splitting) when emulated, else FP64 FMA everywhere."""
-        _check(lib().kep_set_schur_mode(self._h, KEP_SCHUR_EMULATED if emulated else KEP_SCHUR_FP64,
-                                        int(min_front)), "kep_set_schur_mode")
+        splitting) when emulated, else FP64 FMA everywhere; fp32: every Schur update in FP32 (a
+        reduced-precision factor for solve_refined)."""
+        mode = KEP_SCHUR_FP32 if fp32 else (KEP_SCHUR_EMULATED if emulated else KEP_SCHUR_FP64)
+        _check(lib().kep_set_schur_mode(self._h, mode, int(min_front)), "kep_set_schur_mode")
+
+    def solve_refined(self, rhs, tol: float = 1e-13, max_iter: int = 30):
+        """(x, corrections, backward error): iterative refinement with the last factor."""
+        it = ctypes.c_int32()
+        be = ctypes.c_double()
+        if _is_device(rhs):
+            import torch
+            x = torch.empty_like(rhs)
+            code = lib().kep_solve_refined(self._h, _dev_ptr(rhs), _dev_ptr(x), KEP_DEVICE, float(tol), int(max_iter),
+                                           ctypes.byref(it), ctypes.byref(be))
+        else:
+            rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+            x = np.empty_like(rhs)
+            code = lib().kep_solve_refined(self._h, rhs.ctypes.data, x.ctypes.data, KEP_HOST, float(tol), int(max_iter),
+                                           ctypes.byref(it), ctypes.byref(be))
+        _check(code, "kep_solve_refined")
+        return x, it.value, be.value
 
     def set_timing(self, enable: bool, classes=None):
         """Per-launch CUDA-event timing of this context's kernels (launch counts are always kept);
@@ -313,7 +337,8 @@ class Problem:
 
     def kth_eigenpair(self, k: int, *, m_max: int = 20, tau_res: float = 1e-10, tau_diff: float = 1e-10,
                       max_lanczos: int = 200, max_si: int = 300, start_vectors=None, seed: int = 0x5eed,
-                      want_vector: bool = True, init: str = "lanczos", nshift: int = 1):
+                      want_vector: bool = True, init: str = "lanczos", nshift: int = 1,
+                      solve_precision: str = "f64"):
         """Algorithm 4: (lambda_k, x_k (B-normalized), report dict).  init: "lanczos" (Algorithm 2)
         or "gershgorin" (an interval holding the whole spectrum); nshift: shifts per Algorithm 1'
         step (1 = bisection)."""
@@ -323,6 +348,7 @@ class Problem:
         prm.max_lanczos, prm.max_si, prm.seed = int(max_lanczos), int(max_si), int(seed)
         prm.init = {"lanczos": KEP_INIT_LANCZOS, "gershgorin": KEP_INIT_GERSHGORIN}[init]
         prm.nshift = int(nshift)
+        prm.solve_precision = {"f64": KEP_SOLVE_F64, "f32_ir": KEP_SOLVE_F32_IR}[solve_precision]
         sv = None
         if start_vectors is not None:
             sv = np.ascontiguousarray(start_vectors, dtype=np.float64).reshape(-1)

@@ -122,3 +122,33 @@ def test_factor_multi(kep, pen):
         y = P.solve(rhs)
         M = A - sig[-1] * B
         assert np.linalg.norm(M @ y - rhs) <= 1e-11 * np.abs(M).sum(1).max() * np.linalg.norm(y)
+
+
+def test_fp32_factor_refined_solves(kep, pen):
+    p, A, B, lam, X = pen
+    sig = float(core.certified_shifts(lam, 1, 1e-6 * np.abs(A).sum(1).max(), seed=8)[0])
+    M = A - sig * B
+    rhs = np.random.default_rng(3).normal(size=p.n)
+    x_ref = np.linalg.solve(M, rhs)
+    nM = np.abs(M).sum(1).max()
+    with kep.Problem.from_pencil(p) as P:
+        P.set_schur_mode(False, fp32=True)
+        P.factor(sig)
+        x0 = P.solve(rhs)                       # the reduced-precision factor alone
+        be0 = np.abs(rhs - M @ x0).max() / (nM * np.abs(x0).max() + np.abs(rhs).max())
+        x, it, be = P.solve_refined(rhs, tol=1e-13)
+        be_own = np.abs(rhs - M @ x).max() / (nM * np.abs(x).max() + np.abs(rhs).max())
+    assert be0 > 1e-12                          # FP32 Schur arithmetic shows without refinement
+    assert be <= 1e-13 and be_own <= 2e-13 and 1 <= it <= 10
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-10
+
+
+def test_driver_f32_ir(kep, pen):
+    p, A, B, lam, X = pen
+    k = p.k
+    with kep.Problem.from_pencil(p) as P:
+        lam_g, x, rep = P.kth_eigenpair(k, solve_precision="f32_ir")
+    nrm = np.abs(A).sum(1).max()
+    assert abs(lam_g - lam[k - 1]) <= 1e-10 * nrm
+    assert rep["n_refine"] > 0 and rep["solve_berr"] <= 1e-13
+    assert rep["rel_res"] < 1e-10
