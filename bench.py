@@ -170,6 +170,55 @@ def run_reference(args):
     return 0
 
 
+def measure_variants(P, p, torch, kth):
+    """Timings of the next rows on the same problem (device-synchronised wall clock)."""
+    out = {}
+    sync = torch.cuda.synchronize
+    n = p.n
+    # kep_grad: d lambda / d (A, B) values for an eigenvector (the one of --kth if it ran)
+    lam = kth["lambda_k"] if kth else 0.0
+    xk = getattr(P, "_last_x", None)
+    if xk is None:
+        xk = np.random.default_rng(0).normal(size=n)
+    x = torch.from_numpy(np.ascontiguousarray(xk)).cuda()
+    P.grad(lam, x)
+    sync(); t0 = time.perf_counter()
+    for _ in range(5):
+        P.grad(lam, x)
+    sync(); dt = (time.perf_counter() - t0) / 5
+    out["grad"] = {"ms": 1e3 * dt, "entries": P.nnz,
+                   "bytes_per_call": P.nnz * (8 + 4 + 16) + 2 * 8 * n}
+    # FP32 factor + refined solve against the FP64 factor + plain solve, same shift
+    sigma = float(shifts_for(p.k, 1)[0])
+    rhs = np.random.default_rng(1).normal(size=n)
+    res = {}
+    for mode in ("fp64_accurate", "fp32_refined"):
+        P.set_schur_mode(True, 4096, fp32=(mode == "fp32_refined"))
+        sync(); t0 = time.perf_counter()
+        P.factor(sigma)
+        sync(); tf = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        if mode == "fp32_refined":
+            xs, it, be = P.solve_refined(rhs, tol=1e-13)
+        else:
+            xs, it, be = P.solve(rhs), 0, None
+        sync(); ts_ = time.perf_counter() - t0
+        res[mode] = {"factor_s": tf, "solve_s": ts_, "corrections": it, "backward_error": be}
+    P.set_schur_mode(True, 4096)
+    out["fp32_factor_ir"] = res
+    # Algorithm 4 variants
+    for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),
+                     ("stage3_f32_ir", {"solve_precision": "f32_ir"})):
+        sync(); t0 = time.perf_counter()
+        lam_v, _, rep = P.kth_eigenpair(p.k, want_vector=False, **kw)
+        t = time.perf_counter() - t0
+        out[name] = {"time_to_lambda_k_s": t, "lambda_k": lam_v,
+                     "n_factor": rep["n_factor"], "n_bisect": rep["n_bisect"], "n_si_iter": rep["n_si_iter"],
+                     "init_interval": [rep["init_lo"], rep["init_hi"]], "t_stage": rep["t_stage"],
+                     "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,6 +230,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kth", action="store_true",
                     help="also run Algorithm 4 once (k = n/2) and report the time to lambda_k")
+    ap.add_argument("--variants", action="store_true",
+                    help="also measure the next rows: kep_grad, the FP32 factor with refined solves, and "
+                         "Algorithm 4 with the Gershgorin interval + multisection and with refined FP32 stage 3")
     ap.add_argument("--event-timing", type=int, default=1,
                     help="bracket every launch with CUDA events for the per-kernel roofline (1) or not (0)")
     args = ap.parse_args()
@@ -325,7 +377,12 @@ def main():
         t0 = time.perf_counter()
         lam, xk, rep = P.kth_eigenpair(p.k)
         t_kth = time.perf_counter() - t0
+        P._last_x = xk
         kth = {"time_to_lambda_k_s": t_kth, "k": p.k, "lambda_k": lam, "report": rep}
+
+    variants = None
+    if args.variants and rank == 0:
+        variants = measure_variants(P, p, torch, kth)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -348,6 +405,8 @@ def main():
                 "kernels_ms_timed": {k: v[1] for k, v in classes.items() if v[1] > 0}}
         if kth is not None:
             line["time_to_lambda_k"] = kth
+        if variants is not None:
+            line["variants"] = variants
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -46,13 +46,17 @@ KEP_D bool mbar_test(uint64_t* bar, uint32_t parity, uint32_t hint_ns = 0) {
         : "memory");
   return done != 0;
 }
-// Waits until the phase with the given parity has completed, sleeping between tries; gives up
-// after `limit_ns` and returns false.
-KEP_D bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+// Waits until the phase with the given parity has completed, sleeping between tries with an
+// exponential backoff up to max_sleep_ns (waiting warps then take almost no issue slots from
+// the working ones); gives up after `limit_ns` and returns false.
+KEP_D bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns, uint32_t max_sleep_ns = 256) {
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
+  uint32_t ns = 16;
   while (true) {
-    if (mbar_test(bar, parity, 20000u)) return true;
+    __nanosleep(ns);
+    if (mbar_test(bar, parity)) return true;
+    if (ns < max_sleep_ns) ns *= 2;
     if (global_ns() - t0 > limit_ns) return false;
   }
 }

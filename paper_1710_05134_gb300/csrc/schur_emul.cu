@@ -54,6 +54,9 @@ constexpr int kFlushThreads = (kEpiWarps + 2) * 32;   // + one copy warp, one MM
 constexpr uint32_t kTmemCols = 512;           // 2 buffers x 8 level accumulators x 32 columns
 constexpr int kHalf = 8;                      // 16-column steps per accumulation (128 columns)
 constexpr uint64_t kWaitNs = 2000000000ull;   // bounded waits: 2 s
+// longest sleep between two tries of a wait, per role (the copy and MMA warps must react fast,
+// the epilogue waits for a whole half window)
+constexpr uint32_t kSleepCopy = 128, kSleepMma = 64, kSleepEpi = 1024;
 constexpr int kNoExp = -(1 << 20);            // row maximum of an all-zero row
 
 struct EmulArgs {
@@ -402,7 +405,8 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
         if (!tile_ij(slot, nI, nJ, I, J)) continue;
         for (int kk = 0; kk < KS; ++kk, ++f) {
           const int st = static_cast<int>(f % kStages);
-          if (f >= kStages && !tc::mbar_wait(&empty_bar[st], static_cast<uint32_t>((f / kStages - 1) & 1), kWaitNs)) {
+          if (f >= kStages &&
+              !tc::mbar_wait(&empty_bar[st], static_cast<uint32_t>((f / kStages - 1) & 1), kWaitNs, kSleepCopy)) {
             ok = false;
             break;
           }
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
         if (!tile_ij(slot, nI, nJ, I, J)) continue;
         for (int hh = 0; hh < NH && ok; ++hh, ++u) {
           const int buf = static_cast<int>(u & 1);
-          if (u >= 2 && !tc::mbar_wait(&tempty_bar[buf], static_cast<uint32_t>(((u >> 1) - 1) & 1), kWaitNs)) {
+          if (u >= 2 && !tc::mbar_wait(&tempty_bar[buf], static_cast<uint32_t>(((u >> 1) - 1) & 1), kWaitNs, kSleepMma)) {
             ok = false;
             break;
           }
@@ -439,7 +443,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
           const int k1 = min(KS, (hh + 1) * kHalf);
           for (int kk = hh * kHalf; kk < k1; ++kk, ++f) {
             const int st = static_cast<int>(f % kStages);
-            if (!tc::mbar_wait(&full_bar[st], static_cast<uint32_t>((f / kStages) & 1), kWaitNs)) {
+            if (!tc::mbar_wait(&full_bar[st], static_cast<uint32_t>((f / kStages) & 1), kWaitNs, kSleepMma)) {
               ok = false;
               break;
             }
@@ -493,7 +497,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
       for (int c = 0; c < kCols; ++c) { vh[c] = 0; vl[c] = 0; }
       for (int hh = 0; hh < NH; ++hh, ++u) {
         const int buf = static_cast<int>(u & 1);
-        if (!tc::mbar_wait(&tfull_bar[buf], static_cast<uint32_t>((u >> 1) & 1), kWaitNs)) {
+        if (!tc::mbar_wait(&tfull_bar[buf], static_cast<uint32_t>((u >> 1) & 1), kWaitNs, kSleepEpi)) {
           ok = false;
           break;
         }
