@@ -193,7 +193,7 @@ def measure_variants(P, p, torch, kth):
     rhs = np.random.default_rng(1).normal(size=n)
     res = {}
     for mode in ("fp64_accurate", "fp32_refined"):
-        P.set_schur_mode(True, 4096, fp32=(mode == "fp32_refined"))
+        P.set_schur_mode(True, 1024, fp32=(mode == "fp32_refined"))
         sync(); t0 = time.perf_counter()
         P.factor(sigma)
         sync(); tf = time.perf_counter() - t0
@@ -204,7 +204,7 @@ def measure_variants(P, p, torch, kth):
             xs, it, be = P.solve(rhs), 0, None
         sync(); ts_ = time.perf_counter() - t0
         res[mode] = {"factor_s": tf, "solve_s": ts_, "corrections": it, "backward_error": be}
-    P.set_schur_mode(True, 4096)
+    P.set_schur_mode(True, 1024)
     out["fp32_factor_ir"] = res
     # Algorithm 4 variants
     for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),

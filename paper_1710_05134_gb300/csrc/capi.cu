@@ -90,7 +90,9 @@ void release_memory(kep_ctx* c) {
   for (void* p : c->mem_allocs) cudaFree(p);
   c->mem_allocs.clear();
   c->emul_ws = nullptr;
-  c->emul_cap_rows = 0;
+  c->emul_bytes = 0;
+  c->d_emul_off = nullptr;
+  c->emul_min_planned = -1;
   for (int i = 0; i < 2; ++i) { c->slot_ready[i] = false; c->slot[i].valid = false; }
 }
 
@@ -138,22 +140,58 @@ kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inert
   F.emul_min = c->schur_mode == KEP_SCHUR_EMULATED ? c->emul_min_front : 0;
   F.fp32_schur = c->schur_mode == KEP_SCHUR_FP32;
   F.emul_ws = nullptr;
-  F.emul_cap_rows = 0;
+  F.d_emul_off = nullptr;
+  F.h_emul_end = nullptr;
   if (F.emul_min > 0) {
-    int64_t cap = 0;
-    for (int32_t t = 0; t < c->plan.nfronts; ++t)
-      if (c->plan.m_alloc[t] >= F.emul_min) cap = std::max<int64_t>(cap, c->plan.m_alloc[t]);
-    if (cap > 0) {
-      if (c->emul_cap_rows < cap) {
+    const Plan& P = c->plan;
+    if (c->emul_min_planned != F.emul_min) {
+      // batches of a level's fronts on the tensor-core path (consecutive in the level's
+      // decreasing order, at most emul_max_batch() and kEmulBudget bytes of workspace each) and
+      // each front's workspace offset inside its batch
+      constexpr int64_t kEmulBudget = 24ll << 30;
+      std::vector<int64_t> off(P.nfronts, 0);
+      c->h_emul_end.assign(P.nfronts, 0);
+      int64_t need = 0;
+      for (int32_t l = 0; l < P.nlevels; ++l) {
+        const int32_t lb = P.level_ptr[l], le = P.level_ptr[l + 1];
+        int32_t e = lb;
+        while (e < le) {
+          if (P.m_alloc[P.level_fronts[e]] < F.emul_min) { ++e; continue; }
+          const int32_t start = e;
+          int64_t bytes = 0;
+          while (e < le && P.m_alloc[P.level_fronts[e]] >= F.emul_min && e - start < emul_max_batch()) {
+            const int64_t fb = (static_cast<int64_t>(emul_workspace_bytes(P.m_alloc[P.level_fronts[e]])) + 255) / 256 * 256;
+            if (e > start && bytes + fb > kEmulBudget) break;
+            off[e] = bytes;
+            bytes += fb;
+            ++e;
+          }
+          c->h_emul_end[start] = e - lb;
+          need = std::max(need, bytes);
+        }
+      }
+      if (need > c->emul_bytes) {
         void* p = nullptr;
-        if (cudaMalloc(&p, emul_workspace_bytes(cap)) != cudaSuccess) return KEP_ERR_NOMEM;
-        if (cudaMemset(p, 0, emul_workspace_bytes(cap)) != cudaSuccess) return KEP_ERR_CUDA;
+        if (cudaMalloc(&p, need) != cudaSuccess) return KEP_ERR_NOMEM;
+        if (cudaMemset(p, 0, need) != cudaSuccess) return KEP_ERR_CUDA;
         c->mem_allocs.push_back(p);
         c->emul_ws = p;
-        c->emul_cap_rows = cap;
+        c->emul_bytes = need;
       }
+      if (!c->d_emul_off) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int64_t) * std::max<int32_t>(1, P.nfronts)) != cudaSuccess) return KEP_ERR_NOMEM;
+        c->mem_allocs.push_back(p);
+        c->d_emul_off = static_cast<int64_t*>(p);
+      }
+      if (cudaMemcpy(c->d_emul_off, off.data(), sizeof(int64_t) * P.nfronts, cudaMemcpyHostToDevice) != cudaSuccess)
+        return KEP_ERR_CUDA;
+      c->emul_min_planned = need > 0 ? F.emul_min : -2;
+    }
+    if (c->emul_bytes > 0 && c->emul_min_planned == F.emul_min) {
       F.emul_ws = c->emul_ws;
-      F.emul_cap_rows = c->emul_cap_rows;
+      F.d_emul_off = c->d_emul_off;
+      F.h_emul_end = c->h_emul_end.data();
     } else {
       F.emul_min = 0;
     }

@@ -780,7 +780,9 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       int32_t t0 = P.level_fronts[lb + e];
       int32_t e1;
       const bool emul = F.emul_min > 0 && P.m_alloc[t0] >= F.emul_min;
-      if (P.m_alloc[t0] > 4096 || emul) {
+      if (emul) {
+        e1 = F.h_emul_end[lb + e];   // the level's fronts on the tensor-core path, batched
+      } else if (P.m_alloc[t0] > 4096) {
         e1 = e + 1;
       } else {
         e1 = e + 1;                  // the rest of the level (sorted by size), stopping at a front
@@ -830,10 +832,10 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
           KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
           if (emul) {
             // in-window and trailing updates on the tensor cores (FP64-accurate splitting)
-            launch_emul_update(true, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
-                               F.num_sms, F.timer, F.flops);
-            launch_emul_update(false, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, F.emul_ws, F.emul_cap_rows, max_m, st,
-                               F.num_sms, F.timer, F.flops);
+            launch_emul_update(true, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, nb, F.emul_ws, F.d_emul_off + lb + e,
+                               max_m, st, F.num_sms, F.timer, F.flops);
+            launch_emul_update(false, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, nb, F.emul_ws, F.d_emul_off + lb + e,
+                               max_m, st, F.num_sms, F.timer, F.flops);
           } else if (F.fp32_schur) {
             KEP_LAUNCH(F.timer, KC_UPDATE, st,
                        lf_schur_kernel<true, float><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,

@@ -56,9 +56,12 @@ struct kep_ctx {
   std::vector<int32_t> slot_nelim[2];   // pivots eliminated per front, per slot (host copy)
   kep::Timer timer;
   int schur_mode = KEP_SCHUR_EMULATED;
-  int64_t emul_min_front = 4096;
-  void* emul_ws = nullptr;          // tensor-core flush workspace (in mem_allocs)
-  int64_t emul_cap_rows = 0;
+  int64_t emul_min_front = 1024;
+  void* emul_ws = nullptr;          // tensor-core update workspace (in mem_allocs)
+  int64_t emul_bytes = 0;           // its size
+  int64_t* d_emul_off = nullptr;    // per level position: workspace offset within its batch (in mem_allocs)
+  int64_t emul_min_planned = -1;    // min_front the batches below were formed for
+  std::vector<int32_t> h_emul_end;  // per level position starting a batch: the batch's end
   // eigenpair driver state (owned by driver.cu)
   void* driver = nullptr;
   void driver_release();

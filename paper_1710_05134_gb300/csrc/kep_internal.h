@@ -239,7 +239,8 @@ struct FactorLaunch {
   int64_t emul_min;         // fronts with m_alloc >= this use the tensor-core flush (0: never)
   bool fp32_schur = false;  // Schur tiles in FP32 arithmetic (reduced-precision factor for refined solves)
   void* emul_ws;            // its workspace
-  int64_t emul_cap_rows;
+  const int64_t* d_emul_off;      // per level position: byte offset of the front's workspace in its batch
+  const int32_t* h_emul_end;      // per level position starting a batch of such fronts: its end (level index)
   unsigned long long* flops;   // per kernel class: algorithmic flops, counted on the device
 };
 
@@ -263,8 +264,9 @@ struct SolveLaunch {
 kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, int* status_bits);
 size_t emul_workspace_bytes(int64_t cap_rows);
 void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
-                        const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
+                        const int32_t* lf, int32_t e0, int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint,
                         cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops);
+int32_t emul_max_batch();
 kep_status run_solve(SolveLaunch& L, const double* b, double* x);
 kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
                     const double* x, double* ya, double* yb, cudaStream_t st, int num_sms,

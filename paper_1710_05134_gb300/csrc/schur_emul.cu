@@ -80,6 +80,29 @@ KEP_D int64_t wdig_off(int a, int32_t q, int64_t row) {
 
 KEP_HD int64_t digit_pitch(int64_t cap_rows) { return (cap_rows + kTM - 1) / kTM * kTM + kTM; }
 
+// Workspace of one front (rows up to cap_rows): L digits, W digits, row exponents.
+KEP_HD EmulArgs emul_args(void* ws, int64_t cap_rows) {
+  EmulArgs E;
+  E.R = digit_pitch(cap_rows);
+  const int64_t plane = static_cast<int64_t>(kSlices) * kKB * E.R * 8;
+  E.Ls = static_cast<__nv_bfloat16*>(ws);
+  E.Ws = E.Ls + plane;
+  E.eL = reinterpret_cast<int32_t*>(E.Ws + plane);
+  E.eW = E.eL + E.R;
+  return E;
+}
+
+// A batch of fronts on the tensor-core path: entries e0 .. e0 + nb - 1 of the level's batch
+// arrays; entry e's workspace starts at ws + off[e] (bytes).
+struct EmulBatch {
+  unsigned char* ws;
+  const int64_t* off;
+  int32_t e0, nb;
+};
+KEP_D EmulArgs entry_args(const EmulBatch& B, int32_t e, int64_t cap_rows) {
+  return emul_args(B.ws + B.off[e], cap_rows);
+}
+
 KEP_D int bexp(double x) {                    // biased exponent field (0 for zero / subnormal)
   return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7ff);
 }
@@ -159,15 +182,18 @@ KEP_D bool emul_range(const LargeWork& W, int32_t b, int32_t m, int32_t& c0, int
 
 // Digits: per row, the scale exponents of the balanced L and W rows (W = L D formed on the fly),
 // then the digits of every entry of the update's columns (zero up to the next multiple of 16
-// columns).  Thread (row, half): the half's 8-column blocks; each 16-byte store holds one row's 8
-// digits of one slice and block, consecutive threads writing consecutive rows.
-constexpr int kSRows = 128;
+// columns).  A row is shared by NG threads (NG = 2, 4 or 8 from the update's width), thread g
+// taking the 8-column blocks g, g + NG, ...; each 16-byte store holds one row's 8 digits of one
+// slice and block, consecutive threads writing consecutive rows.
+constexpr int kSThreads = 256;
 template <bool kWin>
-__global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
-                                                       int32_t b, EmulArgs E) {
-  __shared__ int smx[2][2][kSRows];
+__global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
+                                                             EmulBatch BA) {
+  __shared__ int smx[2][kSThreads];
   __shared__ int su[kWindow];
+  const int32_t b = BA.e0 + blockIdx.y;
   const int32_t t = lf[b];
+  const EmulArgs E = entry_args(BA, blockIdx.y, T.m_alloc[t]);
   const int32_t m = T.m_sym[t] + S.d_in[t];
   int32_t c0, c1, s, ce;
   if (!emul_range<kWin>(W, b, m, c0, c1, s, ce)) return;
@@ -180,32 +206,39 @@ __global__ void __launch_bounds__(256) lf_slice_kernel(FrontTables T, FactorSlot
   for (int32_t c = threadIdx.x; c < r; c += blockDim.x) su[c] = balance_shift(Dd, De, pv, c0 + c);
   __syncthreads();
   const int32_t nq = (r + 15) / 16 * 2;          // 8-column blocks covering the padded window
+  const int NG = nq >= 8 ? 8 : (nq >= 4 ? 4 : 2);
+  const int RT = kSThreads / NG;                 // rows per pass
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
   const int64_t rows = m - s;
-  const int lr = threadIdx.x % kSRows, half = threadIdx.x / kSRows;
-  for (int64_t rb = static_cast<int64_t>(blockIdx.x) * kSRows; rb < rows; rb += static_cast<int64_t>(gridDim.x) * kSRows) {
+  const int lr = threadIdx.x % RT, g = threadIdx.x / RT;
+  for (int64_t rb = static_cast<int64_t>(blockIdx.x) * RT; rb < rows; rb += static_cast<int64_t>(gridDim.x) * RT) {
     const int64_t row = rb + lr;
     const bool ok = row < rows;
     int ex = kNoExp, ey = kNoExp;
     if (ok)
-      for (int32_t c = half; c < r; c += 2) {
-        const int u = su[c];
-        const int bx = bexp(L[static_cast<int64_t>(c0 + c) * ld + s + row]);
-        const int by = row < wrows ? bexp(wval(L, ld, s + row, c0 + c, Dd, De, pv)) : 0;
-        if (bx) ex = max(ex, bx - u);
-        if (by) ey = max(ey, by + u);
-      }
-    smx[0][half][lr] = ex;
-    smx[1][half][lr] = ey;
+      for (int32_t q = g; q < nq; q += NG)
+        for (int32_t c = q * 8; c < min(q * 8 + 8, r); ++c) {
+          const int u = su[c];
+          const int bx = bexp(L[static_cast<int64_t>(c0 + c) * ld + s + row]);
+          const int by = row < wrows ? bexp(wval(L, ld, s + row, c0 + c, Dd, De, pv)) : 0;
+          if (bx) ex = max(ex, bx - u);
+          if (by) ey = max(ey, by + u);
+        }
+    smx[0][threadIdx.x] = ex;
+    smx[1][threadIdx.x] = ey;
     __syncthreads();
-    const int mx = max(smx[0][0][lr], smx[0][1][lr]), my = max(smx[1][0][lr], smx[1][1][lr]);
+    int mx = kNoExp, my = kNoExp;
+    for (int q = 0; q < NG; ++q) {
+      mx = max(mx, smx[0][q * RT + lr]);
+      my = max(my, smx[1][q * RT + lr]);
+    }
     __syncthreads();
     const int el = mx != kNoExp ? mx - 1021 : 0;   // |x 2^-u| < 2^{el-1} along the row
     const int ew = my != kNoExp ? my - 1021 : 0;
     if (!ok) continue;
-    if (half == 0) { E.eL[row] = el; E.eW[row] = ew; }
-    for (int32_t q = half; q < nq; q += 2) {
+    if (g == 0) { E.eL[row] = el; E.eW[row] = ew; }
+    for (int32_t q = g; q < nq; q += NG) {
 #pragma unroll 1
       for (int which = 0; which < (row < wrows ? 2 : 1); ++which) {
         uint32_t pk[kSlices][4];
@@ -346,36 +379,65 @@ KEP_D void add_levels(const float (&x)[8], long long& vh, long long& vl) {
   }
 }
 
+constexpr int kMaxBatch = 512;              // fronts per tensor-core launch
+
 template <bool kWin>
 __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTables T, FactorSlot S, double* cbpool,
-                                                                       LargeWork W, const int32_t* lf, int32_t b,
-                                                                       EmulArgs E, unsigned long long* flops) {
+                                                                       LargeWork W, const int32_t* lf, EmulBatch BA,
+                                                                       unsigned long long* flops) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
   __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], drain_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
-  const int32_t t = lf[b];
-  const FrontView v = front_view(T, S, cbpool, t, S.d_in[t]);
-  int32_t c0, c1, s, ce;
-  if (!emul_range<kWin>(W, b, v.m, c0, c1, s, ce)) return;
-  const int32_t r = c1 - c0;
-  const int KS = (r + 15) / 16;               // 16-column steps
-  const int NH = (KS + kHalf - 1) / kHalf;    // accumulation halves
-  const int64_t h = v.m - s, w = ce - s;
-  const int nI = static_cast<int>((h + kTM - 1) / kTM), nJ = static_cast<int>((w + kTN - 1) / kTN);
-  const int nslots = static_cast<int>(tile_slots(nI, nJ));
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // tensor-core work issued (i-block I has min(4I + 4, nJ) tiles), and the FP64 update it
-    // stands for (2 r per updated entry)
-    const int64_t c = min(nI, nJ / 4);
-    const int64_t ntiles = 2 * c * (c + 1) + (nI - c) * static_cast<int64_t>(nJ);
-    atomicAdd(&flops[KC_FLUSH_TC],
-              static_cast<unsigned long long>(2ll * kTM * (kSlices * (kSlices + 1) / 2) * kTN * 16 * KS * ntiles));
-    atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (w * h - w * (w - 1) / 2)));
+  // per entry of the batch: tile-slot prefix, tile grid, 16-column steps, first row, end column
+  __shared__ int pre[kMaxBatch + 1];
+  __shared__ int enI[kMaxBatch], enJ[kMaxBatch], eKS[kMaxBatch], eS[kMaxBatch], eCE[kMaxBatch];
+  for (int e = threadIdx.x; e < BA.nb; e += blockDim.x) {
+    const int32_t b = BA.e0 + e, t = lf[b];
+    const int32_t m = T.m_sym[t] + S.d_in[t];
+    int32_t c0, c1, s, ce;
+    int nI = 0, nJ = 0, KS = 0, ns = 0;
+    if (emul_range<kWin>(W, b, m, c0, c1, s, ce)) {
+      const int32_t r = c1 - c0;
+      KS = (r + 15) / 16;
+      const int64_t h = m - s, w = ce - s;
+      nI = static_cast<int>((h + kTM - 1) / kTM);
+      nJ = static_cast<int>((w + kTN - 1) / kTN);
+      ns = static_cast<int>(tile_slots(nI, nJ));
+      if (blockIdx.x == 0) {
+        // tensor-core work issued (i-block I has min(4I + 4, nJ) tiles), and the FP64 update it
+        // stands for (2 r per updated entry)
+        const int64_t c = min(nI, nJ / 4);
+        const int64_t ntiles = 2 * c * (c + 1) + (nI - c) * static_cast<int64_t>(nJ);
+        atomicAdd(&flops[KC_FLUSH_TC],
+                  static_cast<unsigned long long>(2ll * kTM * (kSlices * (kSlices + 1) / 2) * kTN * 16 * KS * ntiles));
+        atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (w * h - w * (w - 1) / 2)));
+      }
+      eS[e] = s;
+      eCE[e] = ce;
+    }
+    enI[e] = nI; enJ[e] = nJ; eKS[e] = KS; pre[e + 1] = ns;
   }
-  if (blockIdx.x >= nslots) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    pre[0] = 0;
+    for (int e = 0; e < BA.nb; ++e) pre[e + 1] += pre[e];
+  }
+  __syncthreads();
+  const int nslots = pre[BA.nb];
+  if (static_cast<int>(blockIdx.x) >= nslots) return;
+  // slot -> (entry, tile): the entry is the last one whose prefix is <= slot (a nonempty one)
+  auto locate = [&](int slot, int& e, int& I, int& J) -> bool {
+    int lo = 0, hi = BA.nb - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (pre[mid] <= slot) lo = mid; else hi = mid - 1;
+    }
+    e = lo;
+    return tile_ij(slot - pre[e], enI[e], enJ[e], I, J);
+  };
   unsigned char* sbase =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -401,8 +463,10 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
       int64_t f = 0;
       bool ok = true;
       for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
-        int I, J;
-        if (!tile_ij(slot, nI, nJ, I, J)) continue;
+        int e, I, J;
+        if (!locate(slot, e, I, J)) continue;
+        const EmulArgs E = entry_args(BA, e, T.m_alloc[lf[BA.e0 + e]]);
+        const int KS = eKS[e];
         for (int kk = 0; kk < KS; ++kk, ++f) {
           const int st = static_cast<int>(f % kStages);
           if (f >= kStages &&
@@ -430,8 +494,9 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
       int64_t f = 0, u = 0;                     // steps, half-window accumulations issued
       bool ok = true;
       for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
-        int I, J;
-        if (!tile_ij(slot, nI, nJ, I, J)) continue;
+        int e, I, J;
+        if (!locate(slot, e, I, J)) continue;
+        const int KS = eKS[e], NH = (KS + kHalf - 1) / kHalf;
         for (int hh = 0; hh < NH && ok; ++hh, ++u) {
           const int buf = static_cast<int>(u & 1);
           if (u >= 2 && !tc::mbar_wait(&tempty_bar[buf], static_cast<uint32_t>(((u >> 1) - 1) & 1), kWaitNs, kSleepMma)) {
@@ -474,13 +539,18 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
     int64_t u = 0;
     bool ok = true;
     for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
-      int I, J;
-      if (!tile_ij(slot, nI, nJ, I, J)) continue;
+      int e, I, J;
+      if (!locate(slot, e, I, J)) continue;
+      const int32_t t = lf[BA.e0 + e];
+      const FrontView v = front_view(T, S, cbpool, t, S.d_in[t]);
+      const EmulArgs E = entry_args(BA, e, T.m_alloc[t]);
+      const int32_t s = eS[e], ce = eCE[e];
+      const int NH = (eKS[e] + kHalf - 1) / kHalf;
       // this thread's row and its entries of C (column stride cs from the entry of column j0; the
       // columns of a tile lie on one side of p except at one j-block of the front); they are
       // brought into L2 while the MMAs run
-      const int64_t i = s + I * kTM + quarter * 32 + lane;
-      const int64_t j0 = s + J * kTN + c_lo;
+      const int64_t i = s + static_cast<int64_t>(I) * kTM + quarter * 32 + lane;
+      const int64_t j0 = s + static_cast<int64_t>(J) * kTN + c_lo;
       const bool rowok = i < v.m && j0 <= i;
       const bool split = j0 < v.p && j0 + kCols > v.p;
       double* cp = rowok ? v.at(static_cast<int32_t>(i), static_cast<int32_t>(j0)) : nullptr;
@@ -512,11 +582,11 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
 #pragma unroll
           for (int g = 0; g < 8; ++g) tc::tmem_keep(x[g]);
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
+          for (int ee = 0; ee < 4; ++ee) {
             float xs[8];
 #pragma unroll
-            for (int g = 0; g < 8; ++g) xs[g] = __uint_as_float(x[g][e]);
-            add_levels(xs, vh[cg * 4 + e], vl[cg * 4 + e]);
+            for (int g = 0; g < 8; ++g) xs[g] = __uint_as_float(x[g][ee]);
+            add_levels(xs, vh[cg * 4 + ee], vl[cg * 4 + ee]);
           }
         }
         // this buffer is free for the MMAs of a later half window
@@ -548,17 +618,6 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   }
 }
 
-EmulArgs emul_args(void* ws, int64_t cap_rows) {
-  EmulArgs E;
-  E.R = digit_pitch(cap_rows);
-  const int64_t plane = static_cast<int64_t>(kSlices) * kKB * E.R * 8;
-  E.Ls = static_cast<__nv_bfloat16*>(ws);
-  E.Ws = E.Ls + plane;
-  E.eL = reinterpret_cast<int32_t*>(E.Ws + plane);
-  E.eW = E.eL + E.R;
-  return E;
-}
-
 }  // namespace
 
 size_t emul_workspace_bytes(int64_t cap_rows) {
@@ -566,10 +625,11 @@ size_t emul_workspace_bytes(int64_t cap_rows) {
   return 2ull * kSlices * kKB * R * 8 * sizeof(__nv_bfloat16) + 2ull * R * sizeof(int32_t) + 512;
 }
 
-// Window update (window = true) or flush for batch entry b (a front factored alone); the kernels
-// return at once unless the front has that update due this step.
+// Window update (window = true) or flush for the batch entries e0 .. e0 + nb - 1 (fronts on the
+// tensor-core path; entry e's workspace at ws + d_off[e]); the kernels skip entries without that
+// update this step.
 void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
-                        const int32_t* lf, int32_t b, void* ws, int64_t cap_rows, int64_t rows_hint,
+                        const int32_t* lf, int32_t e0, int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint,
                         cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops) {
   static bool attr_set = false;
   if (!attr_set) {
@@ -577,17 +637,24 @@ void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, 
     cudaFuncSetAttribute(lf_flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
     attr_set = true;
   }
-  const EmulArgs E = emul_args(ws, cap_rows);
-  const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + kSRows - 1) / kSRows, num_sms * 4)));
+  EmulBatch BA;
+  BA.ws = static_cast<unsigned char*>(ws);
+  BA.off = d_off;
+  BA.e0 = e0;
+  BA.nb = nb;
+  const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + 31) / 32,
+                                                                          std::max(1, num_sms * 8 / nb))));
   if (window) {
-    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<true><<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
+    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<true><<<dim3(gs, nb), kSThreads, 0, st>>>(T, S, W, lf, BA));
     KEP_LAUNCH(timer, KC_FLUSH_TC, st,
-               lf_flush_tc_kernel<true><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, b, E, flops));
+               lf_flush_tc_kernel<true><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, BA, flops));
   } else {
-    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<false><<<gs, 256, 0, st>>>(T, S, W, lf, b, E));
+    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<false><<<dim3(gs, nb), kSThreads, 0, st>>>(T, S, W, lf, BA));
     KEP_LAUNCH(timer, KC_FLUSH_TC, st,
-               lf_flush_tc_kernel<false><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, b, E, flops));
+               lf_flush_tc_kernel<false><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, BA, flops));
   }
 }
+
+int32_t emul_max_batch() { return kMaxBatch; }
 
 }  // namespace kep
