@@ -199,13 +199,16 @@ kep_status kep_factor_pencil(kep_ctx* ctx, double ca, double cb, kep_inertia* ou
 kep_status kep_solve(kep_ctx* ctx, const double* rhs, double* x, int64_t nrhs, int ptr_kind);
 
 /*
- * kep_solve_refined - x = (ca*A + cb*B)^{-1} b by iterative refinement with the last factor
- * (typically a KEP_SCHUR_FP32 one): x_0 = solve(b); r = b - M x_i in FP64 (sparse products);
- * x_{i+1} = x_i + solve(r), until the normwise backward error
+ * kep_solve_refined - x = (ca*A + cb*B)^{-1} b by GMRES-based iterative refinement with the last
+ * factor S (typically a KEP_SCHUR_FP32 one) as preconditioner: x_0 = solve(b); each outer step
+ * takes r = b - M x in FP64 (sparse products) and runs up to 20 right-preconditioned GMRES steps
+ * on M S^{-1} (one solve each), until the normwise backward error
  *   ||b - M x||_inf / (||M||_inf ||x||_inf + ||b||_inf),  ||M||_inf <= |ca| ||A||_inf + |cb| ||B||_inf,
- * is <= tol or max_iter corrections were made.  One right-hand side (n doubles, ptr_kind memory).
- * *iters (corrections made) and *berr (final backward error) may be NULL.  Returns
- * KEP_ERR_NOT_CONVERGED if tol was not reached, KEP_ERR_INVALID without a valid factor.
+ * is <= tol or max_iter GMRES steps were taken.  One right-hand side (n doubles, ptr_kind memory).
+ * The first call allocates a Krylov workspace of 41 n doubles, kept until kep_destroy.
+ * *iters (GMRES steps taken) and *berr (final backward error) may be NULL.  Returns
+ * KEP_ERR_NOT_CONVERGED if tol was not reached (x holds the last iterate), KEP_ERR_NOMEM if the
+ * workspace cannot be allocated, KEP_ERR_INVALID without a valid factor.
  */
 kep_status kep_solve_refined(kep_ctx* ctx, const double* rhs, double* x, int ptr_kind, double tol,
                              int32_t max_iter, int32_t* iters, double* berr);

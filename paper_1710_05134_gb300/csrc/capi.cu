@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "kep_ctx.h"
+#include "kep_vec.h"
 
 static_assert(KEP_NKCLASS == kep::KC_COUNT, "kernel class count");
 
@@ -541,12 +542,47 @@ static kep_status pencil_apply(kep_ctx* c, const double* x, double* y, double* t
 }
 
 // Iterative refinement with the factor in slot 0, device vectors (b is not modified; scratch:
-// d_io2, d_io3, d_io4).
+// d_io2, d_io3 and the context's Krylov workspace, allocated at first use).
+//
+// GMRES-based refinement (Carson and Higham, SIAM J. Sci. Comput. 39(6), 2017), in the right-
+// preconditioned flexible form (Saad, SIAM J. Sci. Comput. 14(2), 1993): every outer step takes
+// the residual r = b - M x in FP64 and runs up to kGmresRestart Arnoldi steps on M S^{-1}, S the
+// (reduced-precision) factor, with classical Gram-Schmidt applied twice and Givens rotations for
+// the least-squares problem; then x += Z y, Z = S^{-1} V.  Plain refinement, x += S^{-1} r, only
+// contracts while ||I - S^{-1} M|| < 1, which fails for the nearly singular shifted matrices of
+// Algorithm 3 (an eigenvalue within the factor's perturbation of sigma); S^{-1} M then has a few
+// outlying eigenvalues, and GMRES removes each in about one step.
+namespace {
+constexpr int kGmresRestart = 20;
+}
+
 kep_status kep::ctx_solve_refined_dev(kep_ctx* c, const double* b, double* xd, double tol, int32_t max_iter,
                                       int32_t* iters, double* berr) {
   const FactorSlot& S = c->slot[0];
   if (!c->slot_ready[0] || !S.valid) return KEP_ERR_INVALID;
-  double *r = c->d_io2, *t = c->d_io3, *dx = c->d_io4;
+  const int64_t n = c->plan.n;
+  constexpr int m = kGmresRestart;
+  const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->num_sms * 4, (n + 255) / 256)));
+  if (!c->d_krylov) {          // V: (m + 1) n, Z: m n, dot partials, coefficients
+    const size_t cnt = static_cast<size_t>(2 * m + 1) * n + static_cast<size_t>(nb) * (m + 1) + (m + 1);
+    double* p = nullptr;
+    if (cudaMalloc(&p, cnt * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return KEP_ERR_NOMEM; }
+    c->allocs.push_back(p);
+    c->d_krylov = p;
+  }
+  double* V = c->d_krylov;
+  double* Z = V + static_cast<size_t>(m + 1) * n;
+  double* part = Z + static_cast<size_t>(m) * n;
+  double* coef = part + static_cast<size_t>(nb) * (m + 1);
+  VecOps ops;
+  ops.n = n; ops.num_blocks = nb; ops.partial = part; ops.stream = c->stream; ops.timer = &c->timer;
+  auto host = [&](double* h, int cnt) -> kep_status {
+    if (cudaMemcpyAsync(h, coef, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    return KEP_OK;
+  };
+  double *r = c->d_io2, *t = c->d_io3;
   // ||M||_inf bound for the backward error: |ca| ||A||_inf + |cb| ||B||_inf
   const double norm_m = std::fabs(S.ca) * c->plan.norm_a_inf + std::fabs(S.cb) * c->norm_b_inf;
   KEP_TRY(ctx_solve_dev(c, 0, b, xd));
@@ -554,17 +590,71 @@ kep_status kep::ctx_solve_refined_dev(kep_ctx* c, const double* b, double* xd, d
   KEP_TRY(vec_norm_inf_dev(c, b, &bn));
   double eta = 0.0;
   int32_t it = 0;
+  std::vector<double> H(static_cast<size_t>(m + 1) * m), g(m + 1), cs(m), sn(m), h(m + 1), h2(m + 1), y(m);
   while (true) {
-    KEP_TRY(pencil_apply(c, xd, t, r));                  // t = M x
-    KEP_TRY(vec_axpby_dev(c, 1.0, b, -1.0, t));          // t = b - M x
+    KEP_TRY(pencil_apply(c, xd, r, t));                  // r = M x
+    KEP_TRY(vec_axpby_dev(c, 1.0, b, -1.0, r));          // r = b - M x
     double rn, xn;
-    KEP_TRY(vec_norm_inf_dev(c, t, &rn));
+    KEP_TRY(vec_norm_inf_dev(c, r, &rn));
     KEP_TRY(vec_norm_inf_dev(c, xd, &xn));
     eta = rn / (norm_m * xn + bn);
     if (!(eta > tol) || it >= max_iter) break;
-    KEP_TRY(ctx_solve_dev(c, 0, t, dx));                 // correction with the (reduced-precision) factor
-    KEP_TRY(vec_axpby_dev(c, 1.0, dx, 1.0, xd));
-    ++it;
+    ops.dots(r, n, 1, r, coef);
+    double beta2;
+    KEP_TRY(host(&beta2, 1));
+    const double beta = std::sqrt(beta2);
+    if (!(beta > 0.0) || !std::isfinite(beta)) break;
+    ops.axpby(1.0 / beta, r, 0.0, V);                   // v_0 = r / beta
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    // ||r||_inf <= ||r||_2: stop the inner steps once the 2-norm estimate meets the target
+    const double target = tol * (norm_m * xn + bn);
+    int k = 0;
+    for (int j = 0; j < m && it < max_iter; ++j) {
+      double* vj = V + static_cast<size_t>(j) * n;
+      double* zj = Z + static_cast<size_t>(j) * n;
+      double* w = V + static_cast<size_t>(j + 1) * n;
+      KEP_TRY(ctx_solve_dev(c, 0, vj, zj));              // z_j = S^{-1} v_j
+      KEP_TRY(pencil_apply(c, zj, w, t));                // w = M z_j
+      for (int pass = 0; pass < 2; ++pass) {             // classical Gram-Schmidt, twice
+        ops.dots(V, n, j + 1, w, coef);
+        KEP_TRY(host(pass == 0 ? h.data() : h2.data(), j + 1));
+        ops.combine(V, n, j + 1, coef, -1.0, 1.0, w);
+      }
+      for (int i = 0; i <= j; ++i) h[i] += h2[i];
+      ops.dots(w, n, 1, w, coef);
+      double hn2;
+      KEP_TRY(host(&hn2, 1));
+      const double hn = std::sqrt(hn2);
+      h[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {                      // earlier rotations
+        const double a0 = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = a0;
+      }
+      const double rr = std::hypot(h[j], h[j + 1]);
+      cs[j] = rr == 0.0 ? 1.0 : h[j] / rr;
+      sn[j] = rr == 0.0 ? 0.0 : h[j + 1] / rr;
+      h[j] = rr;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) H[static_cast<size_t>(j) * (m + 1) + i] = h[i];
+      ++it;
+      k = j + 1;
+      if (!(hn > 1e-300) || std::fabs(g[j + 1]) <= target) break;   // breakdown: the solution is exact
+      ops.axpby(0.0, w, 1.0 / hn, w);
+    }
+    if (k == 0) break;
+    for (int i = k - 1; i >= 0; --i) {                   // y = R^{-1} g (upper triangular)
+      double s = g[i];
+      for (int q = i + 1; q < k; ++q) s -= H[static_cast<size_t>(q) * (m + 1) + i] * y[q];
+      const double d = H[static_cast<size_t>(i) * (m + 1) + i];
+      y[i] = d != 0.0 ? s / d : 0.0;
+    }
+    if (cudaMemcpyAsync(coef, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    ops.combine(Z, n, k, coef, 1.0, 1.0, xd);            // x += Z y
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;   // y is host memory
   }
   if (iters) *iters = it;
   if (berr) *berr = eta;

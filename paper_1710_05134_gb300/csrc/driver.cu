@@ -420,7 +420,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     if (!f32ir) return ctx_solve_dev(c, 0, rhs, out);
     int32_t it = 0;
     double be = 0.0;
-    const kep_status st = ctx_solve_refined_dev(c, rhs, out, 1e-13, 30, &it, &be);
+    const kep_status st = ctx_solve_refined_dev(c, rhs, out, 1e-13, 100, &it, &be);
     rep.n_refine += it;
     rep.solve_berr = std::max(rep.solve_berr, be);
     return st;

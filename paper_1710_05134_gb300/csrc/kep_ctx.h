@@ -52,6 +52,7 @@ struct kep_ctx {
   double* d_io3 = nullptr;
   double* d_io4 = nullptr;
   double norm_b_inf = 0;            // ||B||_inf
+  double* d_krylov = nullptr;       // refinement workspace (in allocs; allocated at first use)
   double* d_solve_partial = nullptr;
   std::vector<int32_t> slot_nelim[2];   // pivots eliminated per front, per slot (host copy)
   kep::Timer timer;

@@ -231,8 +231,9 @@ class Problem:
         mode = KEP_SCHUR_FP32 if fp32 else (KEP_SCHUR_EMULATED if emulated else KEP_SCHUR_FP64)
         _check(lib().kep_set_schur_mode(self._h, mode, int(min_front)), "kep_set_schur_mode")
 
-    def solve_refined(self, rhs, tol: float = 1e-13, max_iter: int = 30):
-        """(x, corrections, backward error): iterative refinement with the last factor."""
+    def solve_refined(self, rhs, tol: float = 1e-13, max_iter: int = 100):
+        """(x, GMRES steps, backward error): GMRES-based iterative refinement preconditioned by the
+        last factor, to a normwise backward error <= tol."""
         it = ctypes.c_int32()
         be = ctypes.c_double()
         if _is_device(rhs):

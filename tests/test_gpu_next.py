@@ -143,6 +143,28 @@ def test_fp32_factor_refined_solves(kep, pen):
     assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-10
 
 
+def test_fp32_factor_refined_near_singular(kep, pen):
+    """A shift 1e-11 ||M|| from an eigenvalue, inside the FP32 factor's perturbation: plain
+    refinement stalls there, the GMRES-based refinement must still reach the backward error."""
+    p, A, B, lam, X = pen
+    j = p.k + 5
+    nrm = np.abs(A).sum(1).max()
+    sig = float(lam[j] + 1e-11 * nrm)
+    M = A - sig * B
+    nM = np.abs(M).sum(1).max()
+    rhs = np.random.default_rng(4).normal(size=p.n)
+    x_ref = np.linalg.solve(M, rhs)
+    with kep.Problem.from_pencil(p) as P:
+        P.set_schur_mode(False, fp32=True)
+        P.factor(sig)
+        x, it, be = P.solve_refined(rhs, tol=1e-13)
+    be_own = np.abs(rhs - M @ x).max() / (nM * np.abs(x).max() + np.abs(rhs).max())
+    assert be <= 1e-13 and be_own <= 2e-13 and 1 <= it <= 60
+    # the near-null direction dominates both solutions: their directions agree
+    cosang = abs(x @ x_ref) / (np.linalg.norm(x) * np.linalg.norm(x_ref))
+    assert cosang >= 1 - 1e-8
+
+
 def test_driver_f32_ir(kep, pen):
     p, A, B, lam, X = pen
     k = p.k
