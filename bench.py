@@ -248,6 +248,7 @@ def main():
 
     import torch
     import paper_1710_05134_gb300 as kep
+    from paper_1710_05134_gb300 import multishift
 
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
@@ -267,7 +268,9 @@ def main():
     gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
     b = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
     x = torch.empty_like(b)
-    shifts = shifts_for(p.k, args.warmup + args.steps + 8)
+    # each rank factors its own shifts (round-robin over one sequence): independent units, no
+    # collective on the data path
+    shifts = multishift.shard(shifts_for(p.k, world * (args.warmup + 2 * args.steps + 8)), rank, world)
 
     nus = []
 

@@ -1,0 +1,88 @@
+"""Independent shifts across ranks (one process per GPU).
+
+The evaluations of one multisection step of Algorithm 1' (Section 2.1: nu_sigma(A, B) from the
+inertia of A - sigma B, Sylvester's law) are independent factorizations.  They are partitioned
+across ranks round-robin; the only exchange is an all-gather of one int64 count per shift, after
+which every rank holds the same counts and takes the same sub-interval, so the ranks stay in step
+without any other communication.
+
+``count`` is any callable sigma -> nu (on a GPU: ``lambda s: problem.factor(s).neg``).  ``dist``
+is ``torch.distributed`` (initialised) or None for a single process."""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+
+def shard(items, rank: int, world: int) -> list:
+    """The items rank ``rank`` of ``world`` evaluates: positions rank, rank + world, ..."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    return list(items)[rank::world]
+
+
+def gather_counts(local: list[int], total: int, rank: int, world: int, dist=None) -> list[int]:
+    """Counts of all ``total`` shifts in shift order, from each rank's ``shard`` of them."""
+    if dist is None or world == 1:
+        if len(local) != total:
+            raise ValueError("a single rank must evaluate every shift")
+        return list(local)
+    import torch
+    per = (total + world - 1) // world
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    buf = torch.full((per,), -1, dtype=torch.int64, device=dev)
+    if local:
+        buf[:len(local)] = torch.tensor(local, dtype=torch.int64, device=dev)
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf)
+    out = [0] * total
+    for r in range(world):
+        vals = parts[r].cpu().tolist()
+        for j, q in enumerate(range(r, total, world)):
+            if vals[j] < 0:
+                raise RuntimeError(f"rank {r} sent no count for shift {q}")
+            out[q] = int(vals[j])
+    return out
+
+
+@dataclass
+class Bracket:
+    """[lower, upper) with nu(lower) = nu_lower < k <= nu_upper = nu(upper)."""
+    lower: float
+    upper: float
+    nu_lower: int
+    nu_upper: int
+    history: list = field(default_factory=list)   # (sigma, nu) of every evaluated shift
+
+
+def multisection_step(count, k: int, br: Bracket, nshift: int, rank: int = 0, world: int = 1,
+                      dist=None) -> Bracket:
+    """One step: [lower, upper) cut into nshift + 1 equal parts at sigma_q = lower + q (upper -
+    lower) / (nshift + 1), q = 1..nshift; keep the part whose ends bracket k."""
+    if nshift < 1:
+        raise ValueError("nshift >= 1")
+    lo, hi = br.lower, br.upper
+    sig = [lo + (hi - lo) * q / (nshift + 1) for q in range(1, nshift + 1)]
+    mine = shard(range(nshift), rank, world)
+    nus = gather_counts([int(count(sig[q])) for q in mine], nshift, rank, world, dist)
+    for a, b in zip(nus, nus[1:]):
+        if b < a:
+            raise RuntimeError("inertia counts are not monotone in sigma")
+    plo, pnl, phi, pnu = lo, br.nu_lower, hi, br.nu_upper
+    for s, nu in zip(sig, nus):
+        if k <= nu:
+            phi, pnu = s, nu
+            break
+        plo, pnl = s, nu
+    return Bracket(plo, phi, pnl, pnu, br.history + list(zip(sig, nus)))
+
+
+def multisection(count, k: int, br: Bracket, m_max: int = 20, nshift: int = 8, rank: int = 0,
+                 world: int = 1, dist=None, max_steps: int = 200) -> Bracket:
+    """Algorithm 1' with nshift shifts per step, until nu_upper - nu_lower <= m_max."""
+    if not br.nu_lower < k <= br.nu_upper:
+        raise ValueError("the bracket must hold k: nu_lower < k <= nu_upper")
+    for _ in range(max_steps):
+        if br.nu_upper - br.nu_lower <= m_max:
+            return br
+        br = multisection_step(count, k, br, nshift, rank, world, dist)
+    raise RuntimeError("multisection did not narrow the bracket (a cluster of eigenvalues?)")
