@@ -28,7 +28,7 @@ DIAMOND_A = 3.567  # lattice constant (Angstrom); the paper gives none, this one
 V_SSS, V_SPS, V_PPS, V_PPP = -5.0, 5.0, 6.0, -3.0
 ONSITE_S, ONSITE_P = -5.0, 1.0
 
-_STREAM_POS, _STREAM_ONSITE, _STREAM_VAC = 1, 2, 3
+_STREAM_POS, _STREAM_ONSITE, _STREAM_VAC, _STREAM_PHASE = 1, 2, 3, 4
 
 # Fractional positions of the 8 atoms of the conventional diamond cell.
 _BASIS = np.array([
@@ -39,12 +39,13 @@ _BASIS = np.array([
 
 @dataclass
 class Pencil:
-    """A symmetric pencil (A, B) in CSR form (both triangles stored, sorted columns)."""
+    """A symmetric (or, with complex values, Hermitian) pencil (A, B) in CSR form (both triangles
+    stored, sorted columns)."""
     n: int
     rowptr: np.ndarray      # int64, n+1
     colind: np.ndarray      # int32, nnz
-    a: np.ndarray           # float64, nnz
-    b: np.ndarray           # float64, nnz
+    a: np.ndarray           # float64 (complex128 for a Hermitian pencil), nnz
+    b: np.ndarray           # same dtype as a, nnz
     coords: np.ndarray | None = None   # float64 (n, 3): position of the atom owning each row
     box: np.ndarray | None = None      # float64 (3,): periodic box lengths
     k: int = 0                          # target index (1-based)
@@ -135,7 +136,8 @@ def sk_blocks(dvec: np.ndarray) -> np.ndarray:
 
 
 def _assemble(natom, ii, jj, hblk, sblk, onsite, sdiag):
-    """CSR (both triangles) from atom-pair blocks (i < j) and per-orbital diagonals."""
+    """CSR (both triangles) from atom-pair blocks (i < j) and per-orbital diagonals; the mirrored
+    block (j, i) holds the complex conjugate of block (i, j) transposed (plain transpose when real)."""
     n = 4 * natom
     oa = np.arange(4)
     # off-diagonal blocks (i, j) and mirrored (j, i)
@@ -143,8 +145,8 @@ def _assemble(natom, ii, jj, hblk, sblk, onsite, sdiag):
     cols = (4 * jj[:, None, None] + oa[None, None, :]) + 0 * oa[None, :, None]
     r_all = np.concatenate([rows.ravel(), cols.ravel(), np.arange(n)])
     c_all = np.concatenate([cols.ravel(), rows.ravel(), np.arange(n)])
-    a_all = np.concatenate([hblk.ravel(), hblk.ravel(), onsite])
-    b_all = np.concatenate([sblk.ravel(), sblk.ravel(), sdiag])
+    a_all = np.concatenate([hblk.ravel(), np.conj(hblk).ravel(), onsite])
+    b_all = np.concatenate([sblk.ravel(), np.conj(sblk).ravel(), sdiag])
     # the same pattern for A and B: sort by (row, col) once
     key = r_all * n + c_all
     o = np.argsort(key, kind="stable")
@@ -157,7 +159,7 @@ def _assemble(natom, ii, jj, hblk, sblk, onsite, sdiag):
 
 def make_pair(nx: int, ny: int, nz: int, *, seed: int = 0, jitter: float = 0.05,
               vacancies: int = 0, cutoff: float = 2.9, overlap: float = 0.1,
-              onsite_noise: float = 0.1, max_offdiag_rowsum: float = 0.9) -> Pencil:
+              onsite_noise: float = 0.1, max_offdiag_rowsum: float = 0.9, phases=None) -> Pencil:
     """Tight-binding pencil on an nx x ny x nz block of periodic conventional diamond cells.
 
     * positions: lattice sites, `vacancies` sites removed uniformly at random, then each
@@ -167,6 +169,11 @@ def make_pair(nx: int, ny: int, nz: int, *, seed: int = 0, jitter: float = 0.05,
     * B = I + S, S = -overlap * (hopping blocks), scaled down if needed so that every
       off-diagonal row sum of |B| is <= max_offdiag_rowsum (strict diagonal dominance, so B is SPD).
       The scale actually applied is in meta["overlap_scale"].
+    * phases (a Hermitian pencil, complex128 values): "peierls" multiplies the hopping and overlap
+      blocks of each atom pair (i < j) by e^{i theta_ij}, theta_ij ~ U(-pi, pi) drawn per pair
+      (block (j, i) gets e^{-i theta_ij}); an array of per-atom phases phi gives the pure gauge
+      theta_ij = phi_i - phi_j, whose spectrum equals that of the real pencil.  The magnitudes and
+      the pattern are those of the real pencil of the same seed.
     k = n/2 (the highest occupied state of a half-filled sp3 band, Appendix B).
     """
     pos, box = diamond_sites(nx, ny, nz)
@@ -192,11 +199,25 @@ def make_pair(nx: int, ny: int, nz: int, *, seed: int = 0, jitter: float = 0.05,
     rho = float(rowsum.max()) if rowsum.size else 0.0
     scale = 1.0 if rho < max_offdiag_rowsum else max_offdiag_rowsum / rho
     s = s * scale
+    if phases is not None:
+        if isinstance(phases, str):
+            if phases != "peierls":
+                raise ValueError("phases: 'peierls' or an array of per-atom phases")
+            theta = np.random.default_rng([seed, _STREAM_PHASE]).uniform(-np.pi, np.pi, ii.size)
+        else:
+            phi = np.asarray(phases, dtype=np.float64)
+            if phi.shape != (natom,):
+                raise ValueError("per-atom phases must have one value per atom")
+            theta = phi[ii] - phi[jj]
+        ph = np.exp(1j * theta)[:, None, None]
+        h = h * ph
+        s = s * ph
     n, rowptr, colind, a, b = _assemble(natom, ii, jj, h, s, onsite, np.ones(4 * natom))
     coords = np.repeat(pos, 4, axis=0)
     return Pencil(n=n, rowptr=rowptr, colind=colind, a=a, b=b, coords=coords, box=box, k=n // 2,
                   meta=dict(kind="diamond", cells=(nx, ny, nz), seed=seed, jitter=jitter,
                             vacancies=vacancies, cutoff=cutoff, overlap_scale=scale,
+                            phases=None if phases is None else (phases if isinstance(phases, str) else "gauge"),
                             natom=natom, npairs=int(ii.size)))
 
 

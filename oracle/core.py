@@ -143,26 +143,36 @@ def sparse_nu(pencil, sigma: float, **kw) -> int:
 def gen_eig(A: np.ndarray, B: np.ndarray):
     """(c2) all eigenpairs of A x = lambda B x, B-orthonormal X, ascending lambda.
 
-    Cholesky reduction as in the dense comparison solver of Section 4.2: B = L L^T,
-    C = L^{-1} A L^{-T}, C = Y diag(lam) Y^T, X = L^{-T} Y.  Raises LinAlgError if B is not SPD."""
-    A = np.asarray(A, dtype=np.float64); B = np.asarray(B, dtype=np.float64)
+    Cholesky reduction as in the dense comparison solver of Section 4.2: B = L L^H,
+    C = L^{-1} A L^{-H}, C = Y diag(lam) Y^H, X = L^{-H} Y.  Real symmetric or complex Hermitian
+    (A, B); raises LinAlgError if B is not positive definite."""
+    dt = np.complex128 if (np.iscomplexobj(A) or np.iscomplexobj(B)) else np.float64
+    A = np.asarray(A, dtype=dt); B = np.asarray(B, dtype=dt)
     L = np.linalg.cholesky(B)
-    T = sla.solve_triangular(L, A, lower=True)
-    C = sla.solve_triangular(L, T.T, lower=True)
-    C = 0.5 * (C + C.T)
+    T = sla.solve_triangular(L, A, lower=True)                 # L^{-1} A
+    C = sla.solve_triangular(L, T.conj().T, lower=True)        # L^{-1} A^H L^{-H} = L^{-1} A L^{-H}
+    C = 0.5 * (C + C.conj().T)
     lam, Y = np.linalg.eigh(C)
-    X = sla.solve_triangular(L.T, Y, lower=False)
+    X = sla.solve_triangular(L.conj().T, Y, lower=False)
     return lam, X
 
 
 def eig_grad(A: np.ndarray, B: np.ndarray, k: int):
     """Derivatives of lambda_k of A x = lambda B x (Hellmann-Feynman): with x the (c2) eigenvector,
-    B-normalized, d lambda / d A_ij = x_i x_j and d lambda / d B_ij = -lambda x_i x_j, every
-    entry an independent variable.  Returns (lambda_k, GA, GB) as dense matrices."""
+    B-normalized, every stored entry an independent variable, G^A_ij = x_i conj(x_j) and
+    G^B_ij = -lambda x_i conj(x_j), so that d lambda = sum_ij Re(conj(G_ij) dM_ij) (for real pencils
+    G^A_ij = x_i x_j).  Returns (lambda_k, GA, GB) as dense matrices."""
     lam, X = gen_eig(A, B)
     x = X[:, k - 1]
-    G = np.outer(x, x)
+    G = np.outer(x, x.conj())
     return float(lam[k - 1]), G, -float(lam[k - 1]) * G
+
+
+def hermitian_nu(A: np.ndarray, B: np.ndarray, sigma: float) -> int:
+    """nu_sigma(A, B) of a Hermitian pencil with B positive definite: the number of negative
+    eigenvalues of A - sigma B (Sylvester's law of inertia, Section 2.1), from the library
+    Hermitian eigenvalue routine."""
+    return int(np.count_nonzero(np.linalg.eigvalsh(np.asarray(A) - sigma * np.asarray(B)) < 0.0))
 
 
 def count_below(eigs: np.ndarray, sigma: float) -> int:
