@@ -138,6 +138,31 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind,
                        const double* coords, kep_ctx** out);
 
 /*
+ * kep_analyze_hermitian - as kep_analyze for a complex Hermitian pencil (A, B), B positive
+ * definite (the pencil of Eq. 1.1 with complex entries, e.g. tight-binding models with Peierls
+ * phases).
+ *
+ * a_val, b_val  complex values on the pattern, interleaved (re, im): 2*rowptr[n] doubles each.
+ *          Hermitian: with KEP_PATTERN_FULL the (j, i) entry must be the conjugate of (i, j); with
+ *          KEP_PATTERN_LOWER only col <= row is given and the upper triangle is its conjugate.
+ *          Diagonal entries must have zero imaginary part.
+ * The context holds the real symmetric embedding of order 2n, [[Re A, -Im A], [Im A, Re A]] and
+ * likewise for B, which has every eigenvalue of (A, B) twice.  On such a context:
+ *  - kep_factor / kep_factor_pencil / kep_factor_multi report the counts of (A, B) (half those of
+ *    the embedding); a count that is odd on the embedding (an eigenvalue within rounding of sigma)
+ *    is returned as KEP_ERR_SINGULAR;
+ *  - kep_solve, kep_solve_refined, kep_spmv and kep_grad take and return complex vectors of order n
+ *    interleaved (re, im) (2n doubles each; device pointers 16-byte aligned); kep_kth_eigenpair
+ *    takes k <= n and returns x_k interleaved with x^H B x = 1; its start vectors, when given, are
+ *    2 * 2n doubles of the embedding;
+ *  - kep_get_info reports the embedding (order 2n); kep_set_values returns KEP_ERR_INVALID.
+ * Errors: as kep_analyze; KEP_ERR_INVALID also for a diagonal entry with an imaginary part.
+ */
+kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                                 const double* a_val, const double* b_val, int flags,
+                                 const double* coords, kep_ctx** out);
+
+/*
  * Arithmetic of the deferred Schur update (the update of a front's trailing matrix with a window of
  * up to 256 pivots, Algorithm 1' factorization step).
  *   KEP_SCHUR_FP64      FP64 FMA tiles everywhere.
@@ -252,8 +277,10 @@ kep_status kep_set_values(kep_ctx* ctx, const double* a_val, const double* b_val
  * variable; with KEP_PATTERN_LOWER an off-diagonal entry stands for (i, j) and (j, i) and gets
  * twice that.  x: the eigenvector (any nonzero scaling; n doubles), lambda_bar: the factor the
  * derivatives are multiplied by (the incoming gradient).  Either output may be NULL.  Vectors
- * in ptr_kind memory.  Errors: KEP_ERR_INVALID (null pointers, x^T B x <= 0), KEP_ERR_NOMEM,
- * KEP_ERR_CUDA.
+ * in ptr_kind memory.  On a Hermitian context (kep_analyze_hermitian) x is complex (interleaved),
+ * s = x^H B x, and each output holds 2 doubles per entry: G_ij = lambda_bar * x_i conj(x_j) / s
+ * (and -lambda G_ij), so that d lambda = sum Re(conj(G_ij) dM_ij) (doubled for a lower off-diagonal
+ * entry).  Errors: KEP_ERR_INVALID (null pointers, x^T B x <= 0), KEP_ERR_NOMEM, KEP_ERR_CUDA.
  */
 kep_status kep_grad(kep_ctx* ctx, double lambda, const double* x, double lambda_bar, double* d_lambda_d_a,
                     double* d_lambda_d_b, int ptr_kind);

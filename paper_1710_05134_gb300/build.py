@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkep.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["analyze.cpp", "factor.cu", "solve.cu", "spmv.cu", "vec.cu", "capi.cu", "driver.cu", "noalloc.cu", "schur_emul.cu", "grad.cu"]
+SOURCES = ["analyze.cpp", "factor.cu", "solve.cu", "spmv.cu", "vec.cu", "capi.cu", "driver.cu", "noalloc.cu", "schur_emul.cu", "grad.cu", "hermitian.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -48,7 +48,6 @@ static kep_status dev_upload_mem(kep_ctx* c, const T** out, const std::vector<T>
   return KEP_OK;
 }
 
-#define KEP_TRY(x) do { kep_status _s = (x); if (_s != KEP_OK) return _s; } while (0)
 
 static kep_status alloc_slot(kep_ctx* c, int i) {
   if (c->slot_ready[i]) return KEP_OK;
@@ -116,6 +115,16 @@ kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* o
     if (st == KEP_ERR_POOL && (bits & ST_POOL) && attempt < 4) {
       KEP_TRY(replan(c, c->plan.slack_base * 4));
       continue;
+    }
+    if (c->herm_n && out && (st == KEP_OK || st == KEP_ERR_SINGULAR)) {
+      // the real embedding of a Hermitian pencil has every eigenvalue twice: its counts are
+      // twice those of the pencil.  An odd count means an eigenvalue within rounding of the shift
+      // (the pair's two copies fell on both sides), reported like an exact zero pivot.
+      const bool odd = (out->neg & 1) || (out->pos & 1);
+      out->neg /= 2;
+      out->pos /= 2;
+      out->zero = c->herm_n - out->neg - out->pos;
+      if (odd || out->zero > 0) st = KEP_ERR_SINGULAR;
     }
     return st;
   }
@@ -465,6 +474,7 @@ kep_status kep_factor_pencil(kep_ctx* c, double ca, double cb, kep_inertia* out)
 
 kep_status kep_solve(kep_ctx* c, const double* rhs, double* x, int64_t nrhs, int ptr_kind) {
   if (!c || !rhs || !x || nrhs < 0) return KEP_ERR_INVALID;
+  if (c->herm_n) return herm_solve(c, rhs, x, nrhs, ptr_kind);
   const int64_t n = c->plan.n;
   for (int64_t r = 0; r < nrhs; ++r) {
     const double* b = rhs + r * n;
@@ -667,6 +677,7 @@ kep_status kep_solve_refined(kep_ctx* c, const double* rhs, double* x, int ptr_k
                              int32_t* iters, double* berr) {
   if (!c || !rhs || !x || tol < 0 || max_iter < 0) return KEP_ERR_INVALID;
   if (ptr_kind != KEP_HOST && ptr_kind != KEP_DEVICE) return KEP_ERR_INVALID;
+  if (c->herm_n) return herm_solve_refined(c, rhs, x, ptr_kind, tol, max_iter, iters, berr);
   const int64_t n = c->plan.n;
   cudaStream_t st = c->stream;
   double *b = c->d_io0, *xd = c->d_io1;
@@ -685,6 +696,7 @@ kep_status kep_solve_refined(kep_ctx* c, const double* rhs, double* x, int ptr_k
 
 kep_status kep_spmv(kep_ctx* c, const double* x, double* ax, double* bx, int ptr_kind) {
   if (!c || !x || (!ax && !bx)) return KEP_ERR_INVALID;
+  if (c->herm_n) return herm_spmv(c, x, ax, bx, ptr_kind);
   const int64_t n = c->plan.n;
   kep_status st;
   if (ptr_kind == KEP_DEVICE) {

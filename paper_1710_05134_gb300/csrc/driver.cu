@@ -196,6 +196,7 @@ struct Run {
   kep_ctx* c;
   Driver* d;
   VecOps ops;
+  VecOps opsh;          // over the first herm_n rows (halves of an embedded Hermitian vector)
   int64_t n;
   double norm_a;
   kep_report rep{};
@@ -262,12 +263,32 @@ struct Run {
     return KEP_OK;
   }
 
-  // full reorthogonalization of w against V(:, 0:ncol) in the B inner product, twice
+  // full reorthogonalization of w against V(:, 0:ncol) in the B inner product, twice.  For a
+  // Hermitian pencil (vectors [re; im] of its real embedding) also against J V, J [u; v] = [-v; u]
+  // (multiplication by i): the complex Gram-Schmidt of the complex Lanczos process written in
+  // real arithmetic.  Without it rounding lets the second copy of each (doubled) eigenvalue of the
+  // embedding into the basis.
   kep_status reorth(int32_t ncol, double* wv, std::vector<double>& tmp) {
     tmp.resize(ncol);
+    std::vector<double> t2;
     for (int pass = 0; pass < 2; ++pass) {
       DTRY(dots(d->BV, ncol, wv, tmp.data()));
       DTRY(sub_combine(d->V, ncol, tmp.data(), wv));
+      if (c->herm_n) {
+        const int64_t h = c->herm_n;
+        t2.resize(ncol);
+        // (J BV_j) . w = BV_j(top) . w(bottom) - BV_j(bottom) . w(top)
+        opsh.dots(d->BV, n, ncol, wv + h, d->coef);
+        DTRY(to_host(tmp.data(), d->coef, ncol));
+        opsh.dots(d->BV + h, n, ncol, wv, d->coef);
+        DTRY(to_host(t2.data(), d->coef, ncol));
+        for (int32_t q = 0; q < ncol; ++q) tmp[q] -= t2[q];
+        // w -= (J V) h: w(top) += V(bottom) h, w(bottom) -= V(top) h
+        CTRY(cudaMemcpyAsync(d->coef, tmp.data(), sizeof(double) * ncol, cudaMemcpyHostToDevice, c->stream));
+        opsh.combine(d->V + h, n, ncol, d->coef, 1.0, 1.0, wv);
+        opsh.combine(d->V, n, ncol, d->coef, -1.0, 1.0, wv + h);
+        DTRY(sync());                                  // tmp (host) is reused by the next pass
+      }
     }
     return KEP_OK;
   }
@@ -278,8 +299,9 @@ struct Run {
 extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params* params, double* lambda,
                                         double* x_out, kep_report* report) {
   if (!c || !lambda) return KEP_ERR_INVALID;
-  const int64_t n = c->plan.n;
-  if (k < 1 || k > n) return KEP_ERR_INVALID;
+  const int64_t n = c->plan.n;                        // vector length (2 herm_n for a Hermitian pencil)
+  const int64_t n_eig = c->herm_n ? c->herm_n : n;    // eigenvalues counted by nu
+  if (k < 1 || k > n_eig) return KEP_ERR_INVALID;
   kep_params prm;
   if (params) prm = *params; else kep_default_params(&prm);
   if (prm.m_max < 1 || prm.max_lanczos < 2 || prm.max_si < 1) return KEP_ERR_INVALID;
@@ -306,6 +328,8 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   R.c = c; R.d = d; R.n = n; R.norm_a = c->plan.norm_a_inf;
   R.ops.n = n; R.ops.num_blocks = d->nblocks; R.ops.partial = d->partial; R.ops.stream = c->stream;
   R.ops.timer = &c->timer;
+  R.opsh = R.ops;
+  if (c->herm_n) R.opsh.n = c->herm_n;
   kep_report& rep = R.rep;
   std::vector<double> h_start(2 * n), tmp;
   if (prm.start_vectors) std::memcpy(h_start.data(), prm.start_vectors, sizeof(double) * 2 * n);
@@ -313,7 +337,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
 
   auto t0 = clock_::now();
   double lo = 0, hi = 0;
-  int64_t nl = 0, nh = n;
+  int64_t nl = 0, nh = n_eig;
   double nrm = 0;
   std::vector<double> alpha, beta;
   if (prm.init == KEP_INIT_GERSHGORIN) {
@@ -339,7 +363,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     lo -= pad;
     hi += pad;
     nl = 0;
-    nh = n;
+    nh = n_eig;
   } else {
   // ---------------- stage 1: Algorithm 2 ----------------
   DTRY(R.factor_B());
@@ -586,7 +610,14 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     rep.rel_res = std::sqrt(rr) / std::sqrt(xx);
     rep.rel_res_normwise = rep.rel_res / std::max(R.norm_a, 1e-300);
   }
-  if (x_out) DTRY(R.to_host(x_out, d->w, n));
+  if (x_out) {
+    if (c->herm_n) {                                   // [Re x; Im x] -> interleaved complex
+      DTRY(herm_to_interleaved(c, d->w, d->u));
+      DTRY(R.to_host(x_out, d->u, n));
+    } else {
+      DTRY(R.to_host(x_out, d->w, n));
+    }
+  }
   rep.t_stage[2] = seconds_since(t0);
   *lambda = rep.lambda;
   if (report) *report = rep;

@@ -3,9 +3,12 @@
 //   d lambda / d A_ij = x_i x_j / s,   d lambda / d B_ij = -lambda x_i x_j / s,
 // every stored entry taken as an independent variable; a lower-triangle entry of a
 // KEP_PATTERN_LOWER input stands for both (i, j) and (j, i) and receives the sum of the two.
+// For a Hermitian pencil (x complex, x^H B x = s): d lambda / d A_ij = x_i conj(x_j) / s and
+// d lambda / d B_ij = -lambda x_i conj(x_j) / s, so that d lambda = sum Re(conj(G_ij) dM_ij).
 // Also kep_set_values: new values of A and B on the pattern of kep_analyze.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "kep_ctx.h"
@@ -52,7 +55,70 @@ __global__ void __launch_bounds__(256) grad_kernel(int64_t n, int64_t nnz_in, co
   }
 }
 
+// Hermitian pencil: per caller entry (i, j), G = c x_i conj(x_j) (complex, interleaved), doubled
+// for a stored lower off-diagonal entry (it stands for (i, j) and its conjugate (j, i))
+__global__ void __launch_bounds__(256) herm_grad_kernel(int64_t nnz, const int32_t* hr, const int32_t* hc, bool lower,
+                                                        const double* x, double c, double lambda, double* ga,
+                                                        double* gb) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nnz;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t i = hr[e], j = hc[e];
+    const double xr = x[2 * i], xi = x[2 * i + 1], yr = x[2 * j], yi = x[2 * j + 1];
+    const double s = (lower && i != j) ? 2.0 * c : c;
+    const double gr = s * fma(xr, yr, xi * yi), gi = s * fma(xi, yr, -xr * yi);
+    if (ga) { ga[2 * e] = gr; ga[2 * e + 1] = gi; }
+    if (gb) { gb[2 * e] = -lambda * gr; gb[2 * e + 1] = -lambda * gi; }
+  }
+}
+
 }  // namespace
+
+kep_status herm_grad(kep_ctx* c, double lambda, const double* x, double lambda_bar, double* ga_out, double* gb_out,
+                     int ptr_kind) {
+  const int64_t N = c->plan.n, nnz = c->herm_nnz;
+  cudaStream_t st = c->stream;
+  const double* xd = x;                            // interleaved complex x on the device
+  if (ptr_kind == KEP_HOST) {
+    if (cudaMemcpyAsync(c->d_io3, x, N * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) return KEP_ERR_CUDA;
+    xd = c->d_io3;
+  } else if (reinterpret_cast<uintptr_t>(x) & 15) {
+    return KEP_ERR_INVALID;
+  }
+  // s = x^H B x = w^T B_r w for w = [Re x; Im x]
+  KEP_TRY(herm_to_blocked(c, xd, c->d_io0));
+  KEP_TRY(ctx_spmv_dev(c, c->d_io0, nullptr, c->d_io2));
+  const int nb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->num_sms * 4, (N + 255) / 256)));
+  double* part = c->d_solve_partial;
+  KEP_LAUNCH(&c->timer, KC_VEC, st, xbx_kernel<<<nb, 256, 0, st>>>(N, c->d_io0, c->d_io2, part));
+  std::vector<double> hp(nb);
+  if (cudaMemcpyAsync(hp.data(), part, nb * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return KEP_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;
+  double s = 0.0;
+  for (double v : hp) s += v;
+  if (!(s > 0.0) || !std::isfinite(s)) return KEP_ERR_INVALID;
+  double *ga = ga_out, *gb = gb_out, *stage = nullptr;
+  if (ptr_kind == KEP_HOST) {
+    if (cudaMalloc(&stage, sizeof(double) * std::max<int64_t>(1, 4 * nnz)) != cudaSuccess) return KEP_ERR_NOMEM;
+    ga = ga_out ? stage : nullptr;
+    gb = gb_out ? stage + 2 * nnz : nullptr;
+  }
+  const int ng = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->num_sms * 8, (nnz + 255) / 256)));
+  KEP_LAUNCH(&c->timer, KC_VEC, st,
+             herm_grad_kernel<<<ng, 256, 0, st>>>(nnz, c->d_hrow, c->d_hcol, c->herm_lower, xd, lambda_bar / s, lambda,
+                                                  ga, gb));
+  kep_status out = KEP_OK;
+  if (ptr_kind == KEP_HOST) {
+    if ((ga_out && cudaMemcpyAsync(ga_out, ga, 2 * nnz * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+        (gb_out && cudaMemcpyAsync(gb_out, gb, 2 * nnz * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess))
+      out = KEP_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) out = KEP_ERR_CUDA;
+  if (stage) cudaFree(stage);
+  c->timer.collect();
+  if (out == KEP_OK && cudaGetLastError() != cudaSuccess) out = KEP_ERR_CUDA;
+  return out;
+}
+
 }  // namespace kep
 
 using namespace kep;
@@ -61,6 +127,7 @@ extern "C" kep_status kep_grad(kep_ctx* c, double lambda, const double* x, doubl
                                double* d_lambda_d_b, int ptr_kind) {
   if (!c || !x || (!d_lambda_d_a && !d_lambda_d_b)) return KEP_ERR_INVALID;
   if (ptr_kind != KEP_HOST && ptr_kind != KEP_DEVICE) return KEP_ERR_INVALID;
+  if (c->herm_n) return herm_grad(c, lambda, x, lambda_bar, d_lambda_d_a, d_lambda_d_b, ptr_kind);
   const int64_t n = c->plan.n, nnz = c->nnz_in;
   cudaStream_t st = c->stream;
   const double* xd = x;
@@ -105,7 +172,7 @@ extern "C" kep_status kep_grad(kep_ctx* c, double lambda, const double* x, doubl
 }
 
 extern "C" kep_status kep_set_values(kep_ctx* c, const double* a_val, const double* b_val) {
-  if (!c || !a_val || !b_val) return KEP_ERR_INVALID;
+  if (!c || !a_val || !b_val || c->herm_n) return KEP_ERR_INVALID;   // real pencils only
   Plan& P = c->plan;
   const int64_t n = P.n, nnz = static_cast<int64_t>(c->csr_src.size());
   std::vector<double> av(nnz), bv(nnz);

@@ -6,6 +6,9 @@
 
 #include "kep_internal.h"
 
+// return a non-OK status to the caller
+#define KEP_TRY(x) do { kep_status _s = (x); if (_s != KEP_OK) return _s; } while (0)
+
 struct kep_ctx {
   int device = 0;
   int num_sms = 1;
@@ -29,6 +32,13 @@ struct kep_ctx {
   std::vector<int64_t> csr_src;     // per full-CSR position: the caller's entry it came from
   int64_t* d_in2csr = nullptr;      // per caller entry: its full-CSR position (bit 62: a lower
                                     //   off-diagonal entry standing for both triangles)
+  // a complex Hermitian pencil of order herm_n held as its real symmetric embedding of order
+  // 2 herm_n (kep_analyze_hermitian); 0 for a real pencil
+  int64_t herm_n = 0;
+  int64_t herm_nnz = 0;             // the caller's stored complex entries
+  bool herm_lower = false;
+  int32_t* d_hrow = nullptr;        // per caller entry: row, column (in allocs)
+  int32_t* d_hcol = nullptr;
   // factorization slots: 0 = the public "last factor" (kep_factor / kep_solve),
   // 1 = the factor of B kept by the eigenpair driver during stage 1
   kep::FactorSlot slot[2]{};
@@ -74,4 +84,14 @@ kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x);
 kep_status ctx_spmv_dev(kep_ctx* c, const double* x, double* ax, double* bx);
 kep_status ctx_solve_refined_dev(kep_ctx* c, const double* b, double* x, double tol, int32_t max_iter,
                                  int32_t* iters, double* berr);
+// Hermitian contexts: the public vector calls with complex vectors (interleaved re, im)
+kep_status herm_solve(kep_ctx* c, const double* rhs, double* x, int64_t nrhs, int ptr_kind);
+kep_status herm_spmv(kep_ctx* c, const double* x, double* ax, double* bx, int ptr_kind);
+kep_status herm_solve_refined(kep_ctx* c, const double* rhs, double* x, int ptr_kind, double tol, int32_t max_iter,
+                              int32_t* iters, double* berr);
+kep_status herm_grad(kep_ctx* c, double lambda, const double* x, double lambda_bar, double* ga, double* gb,
+                     int ptr_kind);
+// interleaved (re, im) complex vector of order herm_n <-> the embedding's [re; im] (device)
+kep_status herm_to_blocked(kep_ctx* c, const double* in, double* out);
+kep_status herm_to_interleaved(kep_ctx* c, const double* in, double* out);
 }  // namespace kep

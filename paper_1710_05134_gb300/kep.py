@@ -21,7 +21,7 @@ KEP_HOST, KEP_DEVICE = 0, 1
 KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 
 # symbols declared in include/kep.h
-EXPORTED = ["kep_default_params", "kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor",
+EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_get_info", "kep_set_stream", "kep_factor",
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
             "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi", "kep_solve_refined",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
@@ -146,10 +146,12 @@ def _is_device(x) -> bool:
     return hasattr(x, "is_cuda") and bool(x.is_cuda)
 
 
-def _dev_ptr(x) -> int:
+def _dev_ptr(x, complex_ok: bool = False) -> int:
     import torch
-    if x.dtype != torch.float64 or not x.is_contiguous():
-        raise ValueError("device vectors must be contiguous float64 CUDA tensors")
+    ok = (torch.float64, torch.complex128) if complex_ok else (torch.float64,)
+    if x.dtype not in ok or not x.is_contiguous():
+        raise ValueError("device vectors must be contiguous float64 (complex128 for a Hermitian "
+                         "pencil) CUDA tensors")
     return x.data_ptr()
 
 
@@ -167,7 +169,10 @@ class FactorResult:
 
 
 class Problem:
-    """A pencil (A, B) analysed once (ordering, tree, maps) and factored for any shift."""
+    """A pencil (A, B) analysed once (ordering, tree, maps) and factored for any shift.
+
+    Complex values make it a Hermitian pencil (kep_analyze_hermitian): vectors, eigenvectors and
+    derivatives are then complex128, and inertia counts are those of the complex pencil."""
 
     def __init__(self, n, rowptr, colind, a, b, coords=None, *, lower: bool = False,
                  graph_order: bool = False):
@@ -175,8 +180,10 @@ class Problem:
         self.n = int(n)
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         colind = np.ascontiguousarray(colind, dtype=np.int32)
-        a = np.ascontiguousarray(a, dtype=np.float64)
-        b = np.ascontiguousarray(b, dtype=np.float64)
+        self.hermitian = bool(np.iscomplexobj(a) or np.iscomplexobj(b))
+        self.vdtype = np.complex128 if self.hermitian else np.float64
+        a = np.ascontiguousarray(a, dtype=self.vdtype)
+        b = np.ascontiguousarray(b, dtype=self.vdtype)
         cp = None
         if coords is not None:
             coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1)
@@ -185,11 +192,18 @@ class Problem:
             cp = coords.ctypes.data_as(ctypes.c_void_p)
         flags = (KEP_PATTERN_LOWER if lower else KEP_PATTERN_FULL) | (KEP_ORDER_GRAPH if graph_order else 0)
         h = ctypes.c_void_p()
-        _check(L.kep_analyze(self.n, rowptr.ctypes.data, colind.ctypes.data, a.ctypes.data,
-                             b.ctypes.data, flags, cp, ctypes.byref(h)), "kep_analyze")
+        fn, name = (L.kep_analyze_hermitian, "kep_analyze_hermitian") if self.hermitian else (L.kep_analyze, "kep_analyze")
+        _check(fn(self.n, rowptr.ctypes.data, colind.ctypes.data, a.ctypes.data, b.ctypes.data, flags, cp,
+                  ctypes.byref(h)), name)
         self._h = h
         self._stream = None
         self.nnz = int(rowptr[-1])
+
+    def _dptr(self, x) -> int:
+        return _dev_ptr(x, complex_ok=self.hermitian)
+
+    def _host(self, x):
+        return np.ascontiguousarray(x, dtype=self.vdtype)
 
     @classmethod
     def from_pencil(cls, p, **kw):
@@ -239,10 +253,10 @@ class Problem:
         if _is_device(rhs):
             import torch
             x = torch.empty_like(rhs)
-            code = lib().kep_solve_refined(self._h, _dev_ptr(rhs), _dev_ptr(x), KEP_DEVICE, float(tol), int(max_iter),
+            code = lib().kep_solve_refined(self._h, self._dptr(rhs), self._dptr(x), KEP_DEVICE, float(tol), int(max_iter),
                                            ctypes.byref(it), ctypes.byref(be))
         else:
-            rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+            rhs = self._host(rhs)
             x = np.empty_like(rhs)
             code = lib().kep_solve_refined(self._h, rhs.ctypes.data, x.ctypes.data, KEP_HOST, float(tol), int(max_iter),
                                            ctypes.byref(it), ctypes.byref(be))
@@ -276,7 +290,10 @@ class Problem:
         return [FactorResult(o.neg, o.zero, o.pos, o.delayed, KEP_OK) for o in out]
 
     def set_values(self, a, b):
-        """New values of A and B on the analysed pattern (same layout as at construction)."""
+        """New values of A and B on the analysed pattern (same layout as at construction; real
+        pencils only)."""
+        if self.hermitian:
+            raise ValueError("set_values is for real pencils")
         a = np.ascontiguousarray(a, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         if a.size != self.nnz or b.size != self.nnz:
@@ -285,16 +302,17 @@ class Problem:
 
     def grad(self, lam: float, x, lam_bar: float = 1.0):
         """(d lambda / d a_vals, d lambda / d b_vals) in the layout of the analysed pattern
-        (Hellmann-Feynman), times lam_bar."""
+        (Hellmann-Feynman), times lam_bar; complex G_ij = lam_bar x_i conj(x_j) / x^H B x for a
+        Hermitian pencil."""
         if _is_device(x):
             import torch
-            ga = torch.empty(self.nnz, dtype=torch.float64, device=x.device)
+            ga = torch.empty(self.nnz, dtype=torch.complex128 if self.hermitian else torch.float64, device=x.device)
             gb = torch.empty_like(ga)
-            _check(lib().kep_grad(self._h, float(lam), _dev_ptr(x), float(lam_bar), _dev_ptr(ga), _dev_ptr(gb),
+            _check(lib().kep_grad(self._h, float(lam), self._dptr(x), float(lam_bar), self._dptr(ga), self._dptr(gb),
                                   KEP_DEVICE), "kep_grad")
             return ga, gb
-        x = np.ascontiguousarray(x, dtype=np.float64)
-        ga, gb = np.empty(self.nnz), np.empty(self.nnz)
+        x = self._host(x)
+        ga, gb = np.empty(self.nnz, dtype=self.vdtype), np.empty(self.nnz, dtype=self.vdtype)
         _check(lib().kep_grad(self._h, float(lam), x.ctypes.data, float(lam_bar), ga.ctypes.data, gb.ctypes.data,
                               KEP_HOST), "kep_grad")
         return ga, gb
@@ -316,9 +334,9 @@ class Problem:
             import torch
             x = torch.empty_like(rhs) if out is None else out
             nrhs = 1 if rhs.dim() == 1 else rhs.shape[0]
-            _check(lib().kep_solve(self._h, _dev_ptr(rhs), _dev_ptr(x), nrhs, KEP_DEVICE), "kep_solve")
+            _check(lib().kep_solve(self._h, self._dptr(rhs), self._dptr(x), nrhs, KEP_DEVICE), "kep_solve")
             return x
-        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        rhs = self._host(rhs)
         x = np.empty_like(rhs) if out is None else out
         nrhs = 1 if rhs.ndim == 1 else rhs.shape[0]
         _check(lib().kep_solve(self._h, rhs.ctypes.data, x.ctypes.data, nrhs, KEP_HOST), "kep_solve")
@@ -329,9 +347,9 @@ class Problem:
         if _is_device(x):
             import torch
             ax, bx = torch.empty_like(x), torch.empty_like(x)
-            _check(lib().kep_spmv(self._h, _dev_ptr(x), _dev_ptr(ax), _dev_ptr(bx), KEP_DEVICE), "kep_spmv")
+            _check(lib().kep_spmv(self._h, self._dptr(x), self._dptr(ax), self._dptr(bx), KEP_DEVICE), "kep_spmv")
             return ax, bx
-        x = np.ascontiguousarray(x, dtype=np.float64)
+        x = self._host(x)
         ax, bx = np.empty_like(x), np.empty_like(x)
         _check(lib().kep_spmv(self._h, x.ctypes.data, ax.ctypes.data, bx.ctypes.data, KEP_HOST), "kep_spmv")
         return ax, bx
@@ -353,11 +371,12 @@ class Problem:
         sv = None
         if start_vectors is not None:
             sv = np.ascontiguousarray(start_vectors, dtype=np.float64).reshape(-1)
-            if sv.size != 2 * self.n:
-                raise ValueError("start_vectors must hold 2n values")
+            nv = 2 * self.n if self.hermitian else self.n      # real vectors of the (embedded) pencil
+            if sv.size != 2 * nv:
+                raise ValueError(f"start_vectors must hold {2 * nv} values")
             prm.start_vectors = sv.ctypes.data
         lam = ctypes.c_double()
-        x = np.empty(self.n) if want_vector else None
+        x = np.empty(self.n, dtype=self.vdtype) if want_vector else None
         rep = Report()
         _check(lib().kep_kth_eigenpair(self._h, int(k), ctypes.byref(prm), ctypes.byref(lam),
                                        x.ctypes.data if x is not None else None, ctypes.byref(rep)),
