@@ -223,7 +223,43 @@ def measure_variants(P, p, torch, kth):
                      "n_factor": rep["n_factor"], "n_bisect": rep["n_bisect"], "n_si_iter": rep["n_si_iter"],
                      "init_interval": [rep["init_lo"], rep["init_hi"]], "t_stage": rep["t_stage"],
                      "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"]}
+    out["hermitian_mid"] = measure_hermitian(torch)
     return out
+
+
+def measure_hermitian(torch):
+    """A complex Hermitian pencil (the n = 49,768 generator with Peierls phases on every atom
+    pair), through the real embedding of order 2n: analysis, factorization, Algorithm 4 and the
+    complex derivatives."""
+    import paper_1710_05134_gb300 as kep
+    from gen import workload
+    sync = torch.cuda.synchronize
+    ph = workload("mid_peierls")
+    res = {"n": ph.n, "nnz": int(ph.rowptr[-1]), "k": ph.k}
+    t0 = time.perf_counter()
+    with kep.Problem.from_pencil(ph) as H:
+        res["analyze_s"] = time.perf_counter() - t0
+        inf = H.info
+        res.update(embedding_n=inf.n, max_front=inf.max_front, flops_per_factorization=inf.flops_factor)
+        H.factor(0.31)
+        sync(); t0 = time.perf_counter()
+        nus = [H.factor(0.30 + 0.013 * i).neg for i in range(3)]
+        sync(); res["factor_s"] = (time.perf_counter() - t0) / 3
+        res["nu"] = nus
+        t0 = time.perf_counter()
+        try:
+            lam, x, rep = H.kth_eigenpair(ph.k)
+        except Exception as exc:
+            res["kth_error"] = str(exc)
+            return res
+        res.update(time_to_lambda_k_s=time.perf_counter() - t0, lambda_k=lam, rel_res=rep["rel_res"],
+                   n_factor=rep["n_factor"], n_si_iter=rep["n_si_iter"])
+        xd = torch.from_numpy(x).cuda()
+        H.grad(lam, xd)
+        sync(); t0 = time.perf_counter()
+        H.grad(lam, xd)
+        sync(); res["grad_ms"] = 1e3 * (time.perf_counter() - t0)
+    return res
 
 
 def main():

@@ -294,6 +294,8 @@ def workload(name: str, seed: int = 0) -> Pencil:
                     131,072 atoms, n = 524,288, jitter 0.05 A.
     * ``mid``:      12x12x12 cells with 10 % vacancies (n = 49,768) for mid-size checks.
     * ``million``:  32x32x32 cells, 262,144 atoms, n = 1,048,576.
+    * ``mid_peierls``: the ``mid`` pencil with a Peierls phase e^{i theta}, theta ~ U(-pi, pi), on
+                    every atom pair (complex Hermitian, n = 49,768).
     """
     if name == "small":
         return make_pair(4, 4, 4, seed=seed)
@@ -301,6 +303,8 @@ def workload(name: str, seed: int = 0) -> Pencil:
         return make_pair(32, 32, 18, seed=seed, vacancies=16384)
     if name == "mid":
         return make_pair(12, 12, 12, seed=seed, vacancies=1382)
+    if name == "mid_peierls":
+        return make_pair(12, 12, 12, seed=seed, vacancies=1382, phases="peierls")
     if name == "million":
         return make_pair(32, 32, 32, seed=seed)
     if name.startswith("cells:"):
