@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         L.kep_default_params.argtypes = [ctypes.POINTER(Params)]
         L.kep_default_params.restype = None
         L.kep_analyze.argtypes = [I64, P, P, P, P, I, P, ctypes.POINTER(P)]
+        L.kep_analyze_hermitian.argtypes = [I64, P, P, P, P, I, P, ctypes.POINTER(P)]
         L.kep_get_info.argtypes = [P, ctypes.POINTER(Info)]
         L.kep_set_stream.argtypes = [P, P]
         L.kep_factor.argtypes = [P, D, ctypes.POINTER(Inertia)]
@@ -123,7 +124,7 @@ def lib() -> ctypes.CDLL:
         L.kep_destroy.restype = None
         L.kep_status_str.argtypes = [I]
         L.kep_status_str.restype = ctypes.c_char_p
-        for name in ["kep_analyze", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
+        for name in ["kep_analyze", "kep_analyze_hermitian", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
                      "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing", "kep_get_timing",
                      "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi",
                      "kep_solve_refined"]:

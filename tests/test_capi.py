@@ -37,3 +37,33 @@ def test_invalid_arguments_rejected_without_gpu():
         k.Problem(2, np.array([0, 2, 3]), np.array([0, 0, 1]), np.ones(3), np.ones(3))
     with pytest.raises(k.KepError):       # lower pattern with an upper entry
         k.Problem(2, np.array([0, 2, 3]), np.array([0, 1, 1]), np.ones(3), np.ones(3), lower=True)
+
+
+def test_every_binding_declares_its_argument_types():
+    """Each exported function is called with declared argument types: without them ctypes passes a
+    Python int (a 64-bit array address) as a 32-bit C int."""
+    import paper_1710_05134_gb300 as k
+    L = k.lib()
+    for name in k.EXPORTED:
+        assert getattr(L, name).argtypes is not None, name
+
+
+def test_hermitian_arguments_rejected_without_gpu():
+    """kep_analyze_hermitian checks the pattern and the real diagonal on the host; large arrays
+    (addresses above 4 GB) reach it intact."""
+    import numpy as np
+    import paper_1710_05134_gb300 as k
+    n = 300_000
+    rp = np.arange(n + 1, dtype=np.int64)
+    ci = np.arange(n, dtype=np.int32)
+    a = np.ones(n, dtype=np.complex128)
+    b = np.ones(n, dtype=np.complex128)
+    a[-1] = 1.0 + 0.5j                                   # a Hermitian diagonal must be real
+    with pytest.raises(k.KepError) as e:
+        k.Problem(n, rp, ci, a, b)
+    assert e.value.code == 1
+    ci2 = ci.copy()
+    ci2[-1] = n                                          # column out of range
+    with pytest.raises(k.KepError) as e:
+        k.Problem(n, rp, ci2, np.ones(n, complex), np.ones(n, complex))
+    assert e.value.code == 1
