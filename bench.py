@@ -116,12 +116,9 @@ def _measured_peaks():
 
 
 def flops_of(p) -> float:
-    """Symbolic factorization flops of the GPU plan for pencil p (host analysis only)."""
+    """Symbolic factorization flops of the GPU plan for pencil p (host analysis only, no device)."""
     import paper_1710_05134_gb300 as kep
-    P = kep.Problem.from_pencil(p)
-    f = P.info.flops_factor
-    P.close()
-    return f
+    return kep.symbolic_info(p.n, p.rowptr, p.colind, p.coords).flops_factor
 
 
 def cpu_oracle_sample(reps: int = 1):

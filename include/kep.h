@@ -184,6 +184,15 @@ kep_status kep_set_schur_mode(kep_ctx* ctx, int mode, int64_t min_front);
 kep_status kep_get_info(const kep_ctx* ctx, kep_info* info);
 
 /*
+ * kep_symbolic_info - the symbolic facts kep_analyze would compute for this pattern (ordering,
+ * assembly tree, #nzf and flop count of one factorization; Section 4.3 task (i)), on the host
+ * only: no device is needed and nothing is kept.  Arguments as kep_analyze without the values.
+ * Errors: KEP_ERR_INVALID for a malformed pattern.
+ */
+kep_status kep_symbolic_info(int64_t n, const int64_t* rowptr, const int32_t* colind, int flags,
+                             const double* coords, kep_info* info);
+
+/*
  * kep_set_stream - order all of ctx's device work on the given cudaStream_t (NULL: the legacy
  * default stream).  The stream must belong to the context's device.
  */

@@ -290,18 +290,27 @@ const char* kep_status_str(kep_status s) {
   return "unknown status";
 }
 
-kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* a_val,
-                       const double* b_val, int flags, const double* coords, kep_ctx** out) {
-  if (!out) return KEP_ERR_INVALID;
-  *out = nullptr;
-  if (n < 1 || n > INT32_MAX - 1 || !rowptr || !colind || !a_val || !b_val) return KEP_ERR_INVALID;
+}  // extern "C"
+
+namespace {
+// The caller's pattern as a full symmetric CSR with sorted rows (values of A and B carried along;
+// zeros when a_val / b_val are null), the caller entry of each position (src) and each caller
+// entry's position (in2csr; bit 62 marks a lower off-diagonal entry standing for both triangles).
+struct FullPattern {
+  std::vector<int64_t> cnt, src, in2csr;
+  std::vector<int32_t> ci;
+  std::vector<double> av, bv;
+};
+
+kep_status full_pattern(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* a_val,
+                        const double* b_val, bool lower, FullPattern& F) {
+  if (n < 1 || n > INT32_MAX - 1 || !rowptr || !colind) return KEP_ERR_INVALID;
   if (rowptr[0] != 0) return KEP_ERR_INVALID;
   for (int64_t i = 0; i < n; ++i)
     if (rowptr[i + 1] < rowptr[i]) return KEP_ERR_INVALID;
   const int64_t nnz_in = rowptr[n];
-  const bool lower = flags & KEP_PATTERN_LOWER;
-  // full symmetric pattern, sorted rows
-  std::vector<int64_t> cnt(n + 1, 0);
+  std::vector<int64_t>& cnt = F.cnt;
+  cnt.assign(n + 1, 0);
   for (int64_t i = 0; i < n; ++i)
     for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
       int64_t j = colind[e];
@@ -316,25 +325,27 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
     }
   for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
   const int64_t nnz = cnt[n];
-  std::vector<int32_t> ci(nnz);
-  std::vector<double> av(nnz), bv(nnz);
-  std::vector<int64_t> src(nnz);          // caller entry of each full-CSR position
-  std::vector<int64_t> in2csr(nnz_in);    // full-CSR position of each caller entry (before sorting)
+  std::vector<int32_t>& ci = F.ci;
+  std::vector<double>& av = F.av;
+  std::vector<double>& bv = F.bv;
+  std::vector<int64_t>& src = F.src;
+  std::vector<int64_t>& in2csr = F.in2csr;
+  ci.assign(nnz, 0); av.assign(nnz, 0.0); bv.assign(nnz, 0.0); src.assign(nnz, 0); in2csr.assign(nnz_in, 0);
   {
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
     for (int64_t i = 0; i < n; ++i)
       for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
         int64_t j = colind[e];
         int64_t o = fill[i]++;
-        ci[o] = static_cast<int32_t>(j); av[o] = a_val[e]; bv[o] = b_val[e]; src[o] = e;
+        const double a = a_val ? a_val[e] : 0.0, b = b_val ? b_val[e] : 0.0;
+        ci[o] = static_cast<int32_t>(j); av[o] = a; bv[o] = b; src[o] = e;
         in2csr[e] = o;
         if (lower && j != i) {
           int64_t o2 = fill[j]++;
-          ci[o2] = static_cast<int32_t>(i); av[o2] = a_val[e]; bv[o2] = b_val[e]; src[o2] = e;
+          ci[o2] = static_cast<int32_t>(i); av[o2] = a; bv[o2] = b; src[o2] = e;
         }
       }
   }
-  (void)nnz_in;
   std::vector<int64_t> idx;
   for (int64_t i = 0; i < n; ++i) {
     const int64_t e0 = cnt[i], e1 = cnt[i + 1];
@@ -366,6 +377,30 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
         if (rowof[e] == i) in2csr[e] = p | ((lower && colind[e] != i) ? (1ll << 62) : 0ll);
       }
   }
+  return KEP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* a_val,
+                       const double* b_val, int flags, const double* coords, kep_ctx** out) {
+  if (!out) return KEP_ERR_INVALID;
+  *out = nullptr;
+  if (!a_val || !b_val) return KEP_ERR_INVALID;
+  const bool lower = flags & KEP_PATTERN_LOWER;
+  FullPattern FP;
+  {
+    const kep_status ps = full_pattern(n, rowptr, colind, a_val, b_val, lower, FP);
+    if (ps != KEP_OK) return ps;
+  }
+  const int64_t nnz_in = rowptr[n];
+  std::vector<int64_t>& cnt = FP.cnt;
+  std::vector<int32_t>& ci = FP.ci;
+  std::vector<double>& av = FP.av;
+  std::vector<double>& bv = FP.bv;
+  std::vector<int64_t>& src = FP.src;
+  std::vector<int64_t>& in2csr = FP.in2csr;
   kep_ctx* c = new (std::nothrow) kep_ctx();
   if (!c) return KEP_ERR_NOMEM;
   for (int64_t i = 0; i < n; ++i) {
@@ -437,6 +472,27 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
 kep_status kep_get_info(const kep_ctx* c, kep_info* info) {
   if (!c || !info) return KEP_ERR_INVALID;
   const Plan& P = c->plan;
+  info->n = P.n;
+  info->nnz = P.nnz;
+  info->nfronts = P.nfronts;
+  info->nlevels = P.nlevels;
+  info->max_front = P.max_front;
+  info->nnz_factor = P.nnz_factor;
+  info->flops_factor = P.flops;
+  info->front_bytes = P.front_total * 8;
+  return KEP_OK;
+}
+
+kep_status kep_symbolic_info(int64_t n, const int64_t* rowptr, const int32_t* colind, int flags,
+                             const double* coords, kep_info* info) {
+  if (!info) return KEP_ERR_INVALID;
+  FullPattern FP;
+  const kep_status ps = full_pattern(n, rowptr, colind, nullptr, nullptr, (flags & KEP_PATTERN_LOWER) != 0, FP);
+  if (ps != KEP_OK) return ps;
+  Plan P;
+  std::string err;
+  const kep_status st = build_plan(n, FP.cnt, FP.ci, FP.av, FP.bv, coords, (flags & KEP_ORDER_GRAPH) != 0, 8, P, err);
+  if (st != KEP_OK) return st;
   info->n = P.n;
   info->nnz = P.nnz;
   info->nfronts = P.nfronts;

@@ -21,7 +21,7 @@ KEP_HOST, KEP_DEVICE = 0, 1
 KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
 
 # symbols declared in include/kep.h
-EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_get_info", "kep_set_stream", "kep_factor",
+EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_get_info", "kep_symbolic_info", "kep_set_stream", "kep_factor",
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
             "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi", "kep_solve_refined",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
         L.kep_analyze.argtypes = [I64, P, P, P, P, I, P, ctypes.POINTER(P)]
         L.kep_analyze_hermitian.argtypes = [I64, P, P, P, P, I, P, ctypes.POINTER(P)]
         L.kep_get_info.argtypes = [P, ctypes.POINTER(Info)]
+        L.kep_symbolic_info.argtypes = [I64, P, P, I, P, ctypes.POINTER(Info)]
         L.kep_set_stream.argtypes = [P, P]
         L.kep_factor.argtypes = [P, D, ctypes.POINTER(Inertia)]
         L.kep_factor_pencil.argtypes = [P, D, D, ctypes.POINTER(Inertia)]
@@ -124,13 +125,28 @@ def lib() -> ctypes.CDLL:
         L.kep_destroy.restype = None
         L.kep_status_str.argtypes = [I]
         L.kep_status_str.restype = ctypes.c_char_p
-        for name in ["kep_analyze", "kep_analyze_hermitian", "kep_get_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
+        for name in ["kep_analyze", "kep_analyze_hermitian", "kep_get_info", "kep_symbolic_info", "kep_set_stream", "kep_factor", "kep_factor_pencil",
                      "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing", "kep_get_timing",
                      "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi",
                      "kep_solve_refined"]:
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
+
+
+def symbolic_info(n, rowptr, colind, coords=None, *, lower: bool = False, graph_order: bool = False) -> Info:
+    """The symbolic facts (#nzf, flop count, fronts) of a pattern, computed on the host only."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    cp = None
+    if coords is not None:
+        coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1)
+        cp = coords.ctypes.data_as(ctypes.c_void_p)
+    flags = (KEP_PATTERN_LOWER if lower else KEP_PATTERN_FULL) | (KEP_ORDER_GRAPH if graph_order else 0)
+    inf = Info()
+    _check(lib().kep_symbolic_info(int(n), rowptr.ctypes.data, colind.ctypes.data, flags, cp, ctypes.byref(inf)),
+           "kep_symbolic_info")
+    return inf
 
 
 def status_str(code: int) -> str:

@@ -67,3 +67,41 @@ def test_hermitian_arguments_rejected_without_gpu():
     with pytest.raises(k.KepError) as e:
         k.Problem(n, rp, ci2, np.ones(n, complex), np.ones(n, complex))
     assert e.value.code == 1
+
+
+def test_symbolic_info_closed_form_without_gpu():
+    """A dense pattern of order m is one front: #nzf = m(m+1)/2 and the flop count is
+    sum_{i<m} (r^2 + r), r = m - 1 - i (the pivot's trailing update and its L column)."""
+    import numpy as np
+    import paper_1710_05134_gb300 as k
+    m = 40
+    rp = np.arange(0, m * m + 1, m, dtype=np.int64)
+    ci = np.tile(np.arange(m, dtype=np.int32), m)
+    inf = k.symbolic_info(m, rp, ci)
+    r = np.arange(m, dtype=np.float64)
+    assert inf.n == m and inf.nnz == m * m and inf.nfronts == 1 and inf.max_front == m
+    assert inf.nnz_factor == m * (m + 1) // 2
+    assert inf.flops_factor == float((r * r + r).sum())
+    # the lower triangle alone describes the same pattern
+    keep = ci <= np.repeat(np.arange(m), m)
+    rpl = np.concatenate([[0], np.cumsum(np.arange(1, m + 1))]).astype(np.int64)
+    inf2 = k.symbolic_info(m, rpl, ci[keep], lower=True)
+    assert (inf2.nnz_factor, inf2.flops_factor) == (inf.nnz_factor, inf.flops_factor)
+    with pytest.raises(k.KepError):
+        k.symbolic_info(m, rp, np.full(m * m, m, dtype=np.int32))
+
+
+def test_reference_arm_json_line():
+    """bench.py --impl reference times the oracle on the host (no device needed) and prints the
+    contract's line."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "small",
+                        "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["steps"] == 1 and line["warmup"] == 3

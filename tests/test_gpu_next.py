@@ -174,3 +174,13 @@ def test_driver_f32_ir(kep, pen):
     assert abs(lam_g - lam[k - 1]) <= 1e-10 * nrm
     assert rep["n_refine"] > 0 and rep["solve_berr"] <= 1e-13
     assert rep["rel_res"] < 1e-10
+
+
+def test_symbolic_info_matches_analysis(kep, pen):
+    """The host-only symbolic facts equal those of the context kep_analyze builds."""
+    p = pen[0]
+    sym = kep.symbolic_info(p.n, p.rowptr, p.colind, p.coords)
+    with kep.Problem.from_pencil(p) as P:
+        inf = P.info
+    for f in ("n", "nnz", "nfronts", "nlevels", "max_front", "nnz_factor", "flops_factor", "front_bytes"):
+        assert getattr(sym, f) == getattr(inf, f), f
