@@ -167,8 +167,16 @@ def run_reference(args):
     return 0
 
 
-def measure_variants(P, p, torch, kth):
+VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "gershgorin_multisection8", "stage3_f32_ir",
+            "hermitian_mid")
+
+
+def measure_variants(P, p, torch, kth, which="all"):
     """Timings of the next rows on the same problem (device-synchronised wall clock)."""
+    want = set(VARIANTS) if which == "all" else set(which.split(","))
+    unknown = want - set(VARIANTS)
+    if unknown:
+        raise ValueError(f"unknown variants {sorted(unknown)}")
     out = {}
     sync = torch.cuda.synchronize
     n = p.n
@@ -177,15 +185,44 @@ def measure_variants(P, p, torch, kth):
     xk = getattr(P, "_last_x", None)
     if xk is None:
         xk = np.random.default_rng(0).normal(size=n)
-    x = torch.from_numpy(np.ascontiguousarray(xk)).cuda()
-    P.grad(lam, x)
-    sync(); t0 = time.perf_counter()
-    for _ in range(5):
+    if "grad" in want:
+        x = torch.from_numpy(np.ascontiguousarray(xk)).cuda()
         P.grad(lam, x)
-    sync(); dt = (time.perf_counter() - t0) / 5
-    out["grad"] = {"ms": 1e3 * dt, "entries": P.nnz,
-                   "bytes_per_call": P.nnz * (8 + 4 + 16) + 2 * 8 * n}
-    # FP32 factor + refined solve against the FP64 factor + plain solve, same shift
+        sync(); t0 = time.perf_counter()
+        for _ in range(5):
+            P.grad(lam, x)
+        sync(); dt = (time.perf_counter() - t0) / 5
+        out["grad"] = {"ms": 1e3 * dt, "entries": P.nnz,
+                       "bytes_per_call": P.nnz * (8 + 4 + 16) + 2 * 8 * n}
+    if "fp32_factor_ir" in want:
+        out["fp32_factor_ir"] = measure_fp32_factor(P, p, torch)
+    if "two_shifts_in_flight" in want:
+        out["two_shifts_in_flight"] = measure_two_in_flight(P, p, torch)
+    # Algorithm 4 variants
+    for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),
+                     ("stage3_f32_ir", {"solve_precision": "f32_ir"})):
+        if name not in want:
+            continue
+        sync(); t0 = time.perf_counter()
+        try:
+            lam_v, _, rep = P.kth_eigenpair(p.k, want_vector=False, **kw)
+        except Exception as exc:       # e.g. refinement that does not reach its tolerance
+            out[name] = {"error": str(exc), "seconds": time.perf_counter() - t0}
+            continue
+        t = time.perf_counter() - t0
+        out[name] = {"time_to_lambda_k_s": t, "lambda_k": lam_v,
+                     "n_factor": rep["n_factor"], "n_bisect": rep["n_bisect"], "n_si_iter": rep["n_si_iter"],
+                     "init_interval": [rep["init_lo"], rep["init_hi"]], "t_stage": rep["t_stage"],
+                     "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"]}
+    if "hermitian_mid" in want:
+        out["hermitian_mid"] = measure_hermitian(torch)
+    return out
+
+
+def measure_fp32_factor(P, p, torch):
+    """FP32 factor + refined solve against the FP64-accurate factor + plain solve, same shift."""
+    sync = torch.cuda.synchronize
+    n = p.n
     sigma = float(shifts_for(p.k, 1)[0])
     rhs = np.random.default_rng(1).normal(size=n)
     res = {}
@@ -205,23 +242,43 @@ def measure_variants(P, p, torch, kth):
         sync(); ts_ = time.perf_counter() - t0
         res[mode] = {"factor_s": tf, "solve_s": ts_, "corrections": it, "backward_error": be}
     P.set_schur_mode(True, 1024)
-    out["fp32_factor_ir"] = res
-    # Algorithm 4 variants
-    for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),
-                     ("stage3_f32_ir", {"solve_precision": "f32_ir"})):
+    return res
+
+
+def measure_two_in_flight(P, p, torch):
+    """Four shifts factored one after another on one context, then two at a time on two contexts
+    of the same pattern (own streams, own host threads): the latency-bound pivot kernels of one
+    factorization overlap the tensor-core updates of the other."""
+    import paper_1710_05134_gb300 as kep
+    from paper_1710_05134_gb300 import multishift
+    sync = torch.cuda.synchronize
+    sig = [0.30 + 0.013 * i for i in range(4)]
+    res = {"shifts": len(sig)}
+    Q = None
+    try:
+        Q = kep.Problem.from_pencil(p)
+        sq = torch.cuda.Stream()
+        Q.set_stream(sq)
+        Q.factor(0.29)                               # the second context's allocations, untimed
         sync(); t0 = time.perf_counter()
+        nu_seq = [P.factor(s).neg for s in sig]
+        sync(); res["sequential_s"] = time.perf_counter() - t0
+        cc = multishift.ConcurrentCounter([lambda s: P.factor(s).neg, lambda s: Q.factor(s).neg])
         try:
-            lam_v, _, rep = P.kth_eigenpair(p.k, want_vector=False, **kw)
-        except Exception as exc:       # e.g. refinement that does not reach its tolerance
-            out[name] = {"error": str(exc), "seconds": time.perf_counter() - t0}
-            continue
-        t = time.perf_counter() - t0
-        out[name] = {"time_to_lambda_k_s": t, "lambda_k": lam_v,
-                     "n_factor": rep["n_factor"], "n_bisect": rep["n_bisect"], "n_si_iter": rep["n_si_iter"],
-                     "init_interval": [rep["init_lo"], rep["init_hi"]], "t_stage": rep["t_stage"],
-                     "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"]}
-    out["hermitian_mid"] = measure_hermitian(torch)
-    return out
+            sync(); t0 = time.perf_counter()
+            nu_con = cc.count_many(sig)
+            sync(); res["two_in_flight_s"] = time.perf_counter() - t0
+        finally:
+            cc.close()
+        res["speedup"] = res["sequential_s"] / res["two_in_flight_s"]
+        res["counts_equal"] = nu_seq == nu_con
+        res["nu"] = nu_con
+    except Exception as exc:                         # e.g. the second context does not fit
+        res["error"] = str(exc)
+    finally:
+        if Q is not None:
+            Q.close()
+    return res
 
 
 def measure_hermitian(torch):
@@ -270,9 +327,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kth", action="store_true",
                     help="also run Algorithm 4 once (k = n/2) and report the time to lambda_k")
-    ap.add_argument("--variants", action="store_true",
-                    help="also measure the next rows: kep_grad, the FP32 factor with refined solves, and "
-                         "Algorithm 4 with the Gershgorin interval + multisection and with refined FP32 stage 3")
+    ap.add_argument("--variants", nargs="?", const="all", default=None,
+                    help="also measure the next rows (all, or a comma list of: grad, fp32_factor_ir, "
+                         "two_shifts_in_flight, gershgorin_multisection8, stage3_f32_ir, hermitian_mid)")
     ap.add_argument("--event-timing", type=int, default=1,
                     help="bracket every launch with CUDA events for the per-kernel roofline (1) or not (0)")
     args = ap.parse_args()
@@ -425,7 +482,7 @@ def main():
 
     variants = None
     if args.variants and rank == 0:
-        variants = measure_variants(P, p, torch, kth)
+        variants = measure_variants(P, p, torch, kth, args.variants)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -631,12 +631,14 @@ size_t emul_workspace_bytes(int64_t cap_rows) {
 void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
                         const int32_t* lf, int32_t e0, int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint,
                         cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  // once per process (a function-local static is initialised once even when contexts on several
+  // host threads get here together)
+  static const bool attr_set = [] {
     cudaFuncSetAttribute(lf_flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
     cudaFuncSetAttribute(lf_flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   EmulBatch BA;
   BA.ws = static_cast<unsigned char*>(ws);
   BA.off = d_off;

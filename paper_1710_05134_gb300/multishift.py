@@ -55,15 +55,17 @@ class Bracket:
 
 
 def multisection_step(count, k: int, br: Bracket, nshift: int, rank: int = 0, world: int = 1,
-                      dist=None) -> Bracket:
+                      dist=None, count_many=None) -> Bracket:
     """One step: [lower, upper) cut into nshift + 1 equal parts at sigma_q = lower + q (upper -
-    lower) / (nshift + 1), q = 1..nshift; keep the part whose ends bracket k."""
+    lower) / (nshift + 1), q = 1..nshift; keep the part whose ends bracket k.  count_many (a list
+    of shifts -> their counts, e.g. ConcurrentCounter.count_many) replaces one-at-a-time count."""
     if nshift < 1:
         raise ValueError("nshift >= 1")
     lo, hi = br.lower, br.upper
     sig = [lo + (hi - lo) * q / (nshift + 1) for q in range(1, nshift + 1)]
     mine = shard(range(nshift), rank, world)
-    nus = gather_counts([int(count(sig[q])) for q in mine], nshift, rank, world, dist)
+    local = count_many([sig[q] for q in mine]) if count_many else [int(count(sig[q])) for q in mine]
+    nus = gather_counts([int(v) for v in local], nshift, rank, world, dist)
     for a, b in zip(nus, nus[1:]):
         if b < a:
             raise RuntimeError("inertia counts are not monotone in sigma")
@@ -77,12 +79,42 @@ def multisection_step(count, k: int, br: Bracket, nshift: int, rank: int = 0, wo
 
 
 def multisection(count, k: int, br: Bracket, m_max: int = 20, nshift: int = 8, rank: int = 0,
-                 world: int = 1, dist=None, max_steps: int = 200) -> Bracket:
+                 world: int = 1, dist=None, max_steps: int = 200, count_many=None) -> Bracket:
     """Algorithm 1' with nshift shifts per step, until nu_upper - nu_lower <= m_max."""
     if not br.nu_lower < k <= br.nu_upper:
         raise ValueError("the bracket must hold k: nu_lower < k <= nu_upper")
     for _ in range(max_steps):
         if br.nu_upper - br.nu_lower <= m_max:
             return br
-        br = multisection_step(count, k, br, nshift, rank, world, dist)
+        br = multisection_step(count, k, br, nshift, rank, world, dist, count_many)
     raise RuntimeError("multisection did not narrow the bracket (a cluster of eigenvalues?)")
+
+
+class ConcurrentCounter:
+    """Several shifts in flight on one device: one context (``Problem``) per in-flight shift, each
+    on its own stream and driven from its own host thread (the library calls release the GIL), so
+    that one factorization's latency-bound pivot steps overlap another's tensor-core updates.
+    ``counters`` are callables sigma -> nu, one per context.  ``count_many`` evaluates a list of
+    shifts and returns their counts in order."""
+
+    def __init__(self, counters):
+        from concurrent.futures import ThreadPoolExecutor
+        if not counters:
+            raise ValueError("at least one counter")
+        self.counters = list(counters)
+        self.pool = ThreadPoolExecutor(max_workers=len(self.counters))
+
+    def count_many(self, sigmas) -> list[int]:
+        sigmas = list(sigmas)
+        k = len(self.counters)
+        # context j evaluates shifts j, j + k, ... in order (each context is used by one thread)
+        def run(j):
+            return [(q, int(self.counters[j](sigmas[q]))) for q in range(j, len(sigmas), k)]
+        out = [0] * len(sigmas)
+        for fut in [self.pool.submit(run, j) for j in range(k)]:
+            for q, nu in fut.result():
+                out[q] = nu
+        return out
+
+    def close(self):
+        self.pool.shutdown(wait=True)

@@ -119,3 +119,39 @@ def test_rank_failure_is_reported():
     res = _run("fail")
     assert res[1][0] == "error" and "fails before the exchange" in res[1][1]
     assert res[0][0] == "error"                             # the peer's collective errored, no hang
+
+
+def test_concurrent_counter_keeps_shift_order():
+    """Several contexts evaluating one step's shifts from their own threads give the counts in
+    shift order, no context used by two threads at once, and the same bracket as one context."""
+    import threading
+    import time
+    lam = _pencil()
+    lock = threading.Lock()
+    active, peak, calls = {}, {}, {}
+
+    def make(j):
+        def count(s):
+            with lock:
+                active[j] = active.get(j, 0) + 1
+                peak[j] = max(peak.get(j, 0), active[j])
+                calls[j] = calls.get(j, 0) + 1
+            time.sleep(0.001)
+            with lock:
+                active[j] -= 1
+            return int(np.searchsorted(lam, s, side="left"))
+        return count
+
+    cc = ms.ConcurrentCounter([make(0), make(1)])
+    try:
+        sig = list(np.linspace(-2.0, 2.0, 9))
+        assert cc.count_many(sig) == [int(np.searchsorted(lam, s, side="left")) for s in sig]
+        got = ms.multisection(None, K, ms.Bracket(-10.0, 10.0, 0, N), m_max=MMAX, nshift=NSHIFT,
+                              count_many=cc.count_many)
+    finally:
+        cc.close()
+    single = ms.multisection(_Ops(lam).nu, K, ms.Bracket(-10.0, 10.0, 0, N), m_max=MMAX, nshift=NSHIFT)
+    assert (got.lower, got.upper, got.nu_lower, got.nu_upper) == (single.lower, single.upper, single.nu_lower,
+                                                                   single.nu_upper)
+    # every context served, none by two threads at once
+    assert set(calls) == {0, 1} and max(peak.values()) == 1
