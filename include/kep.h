@@ -155,7 +155,8 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind,
  *    interleaved (re, im) (2n doubles each; device pointers 16-byte aligned); kep_kth_eigenpair
  *    takes k <= n and returns x_k interleaved with x^H B x = 1; its start vectors, when given, are
  *    2 * 2n doubles of the embedding;
- *  - kep_get_info reports the embedding (order 2n); kep_set_values returns KEP_ERR_INVALID.
+ *  - kep_set_values takes complex values in this call's layout (diagonal imaginary parts zero);
+ *    kep_get_info reports the embedding (order 2n).
  * Errors: as kep_analyze; KEP_ERR_INVALID also for a diagonal entry with an imaginary part.
  */
 kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, const int32_t* colind,
@@ -272,8 +273,9 @@ kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, 
 
 /*
  * kep_set_values - new values of A and B on the pattern given to kep_analyze (same layout:
- * a_val, b_val as there, host arrays).  The symbolic analysis is kept; the factors of the old
- * values become invalid.  Errors: KEP_ERR_INVALID, KEP_ERR_CUDA.
+ * a_val, b_val as there, host arrays; complex interleaved for kep_analyze_hermitian).  The
+ * symbolic analysis is kept; the factors of the old values become invalid.  Errors:
+ * KEP_ERR_INVALID, KEP_ERR_CUDA.
  */
 kep_status kep_set_values(kep_ctx* ctx, const double* a_val, const double* b_val);
 

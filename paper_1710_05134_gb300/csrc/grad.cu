@@ -172,7 +172,13 @@ extern "C" kep_status kep_grad(kep_ctx* c, double lambda, const double* x, doubl
 }
 
 extern "C" kep_status kep_set_values(kep_ctx* c, const double* a_val, const double* b_val) {
-  if (!c || !a_val || !b_val || c->herm_n) return KEP_ERR_INVALID;   // real pencils only
+  if (!c || !a_val || !b_val) return KEP_ERR_INVALID;
+  return c->herm_n ? herm_set_values(c, a_val, b_val) : set_values_real(c, a_val, b_val);
+}
+
+// the caller's values (kep_analyze layout) into the full CSR, the per-front entry lists and the
+// norms; the factors of the old values become invalid
+kep_status kep::set_values_real(kep_ctx* c, const double* a_val, const double* b_val) {
   Plan& P = c->plan;
   const int64_t n = P.n, nnz = static_cast<int64_t>(c->csr_src.size());
   std::vector<double> av(nnz), bv(nnz);

@@ -134,7 +134,7 @@ extern "C" kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, co
   const int64_t nnz_in = rowptr[n];
   // every entry of the full Hermitian matrix: (row, col, a, b); a stored lower off-diagonal entry
   // also gives (col, row) with the conjugate values
-  struct Ent { int32_t r, c; double ar, ai, br, bi; };
+  struct Ent { int32_t r, c; double ar, ai, br, bi; int64_t e; bool mir; };
   std::vector<Ent> full;
   full.reserve(static_cast<size_t>(lower ? 2 * nnz_in : nnz_in));
   std::vector<int32_t> hrow(nnz_in), hcol(nnz_in);
@@ -146,8 +146,9 @@ extern "C" kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, co
       if (j == i && (ai != 0.0 || bi != 0.0)) return KEP_ERR_INVALID;   // a Hermitian diagonal is real
       hrow[e] = static_cast<int32_t>(i);
       hcol[e] = static_cast<int32_t>(j);
-      full.push_back({static_cast<int32_t>(i), static_cast<int32_t>(j), ar, ai, br, bi});
-      if (lower && j != i) full.push_back({static_cast<int32_t>(j), static_cast<int32_t>(i), ar, -ai, br, -bi});
+      full.push_back({static_cast<int32_t>(i), static_cast<int32_t>(j), ar, ai, br, bi, e, false});
+      if (lower && j != i)
+        full.push_back({static_cast<int32_t>(j), static_cast<int32_t>(i), ar, -ai, br, -bi, e, true});
     }
   // the embedding, row by row (kep_analyze sorts each row and rejects duplicates)
   const int64_t N = 2 * n;
@@ -160,18 +161,23 @@ extern "C" kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, co
   const int64_t nnz = cnt[N];
   std::vector<int32_t> ci(nnz);
   std::vector<double> av(nnz), bv(nnz);
+  std::vector<int64_t> emb_src(nnz);
+  std::vector<int8_t> emb_part(nnz);
   {
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
-    auto put = [&](int64_t row, int64_t col, double a, double b) {
+    // part: which value of the caller's entry lands here (0 Re, +1 Im, -1 -Im)
+    auto put = [&](int64_t row, int64_t col, double a, double b, int64_t e, int8_t part) {
       const int64_t o = fill[row]++;
       ci[o] = static_cast<int32_t>(col); av[o] = a; bv[o] = b;
+      emb_src[o] = e; emb_part[o] = part;
     };
     for (const Ent& t : full) {
-      put(t.r, t.c, t.ar, t.br);                  // Re block, top left
-      put(n + t.r, n + t.c, t.ar, t.br);          // Re block, bottom right
+      put(t.r, t.c, t.ar, t.br, t.e, 0);                              // Re block, top left
+      put(n + t.r, n + t.c, t.ar, t.br, t.e, 0);                      // Re block, bottom right
       if (t.r != t.c) {
-        put(t.r, n + t.c, -t.ai, -t.bi);          // -Im block, top right
-        put(n + t.r, t.c, t.ai, t.bi);            // Im block, bottom left
+        // (a mirrored entry holds the conjugate: its imaginary part is -Im of the caller's)
+        put(t.r, n + t.c, -t.ai, -t.bi, t.e, t.mir ? 1 : -1);         // -Im block, top right
+        put(n + t.r, t.c, t.ai, t.bi, t.e, t.mir ? -1 : 1);           // Im block, bottom left
       }
     }
   }
@@ -188,6 +194,8 @@ extern "C" kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, co
   c->herm_n = n;
   c->herm_nnz = nnz_in;
   c->herm_lower = lower;
+  c->herm_emb_src = std::move(emb_src);
+  c->herm_emb_part = std::move(emb_part);
   for (int q = 0; q < 2; ++q) {
     int32_t* d = nullptr;
     const std::vector<int32_t>& h = q == 0 ? hrow : hcol;
@@ -205,4 +213,24 @@ extern "C" kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, co
   }
   *out = c;
   return KEP_OK;
+}
+
+// New complex values on a Hermitian context: the embedding's values from the map kept at analysis
+kep_status kep::herm_set_values(kep_ctx* c, const double* a_val, const double* b_val) {
+  std::vector<int32_t> hr(c->herm_nnz), hc(c->herm_nnz);
+  if (c->herm_nnz &&
+      (cudaMemcpy(hr.data(), c->d_hrow, sizeof(int32_t) * c->herm_nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
+       cudaMemcpy(hc.data(), c->d_hcol, sizeof(int32_t) * c->herm_nnz, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return KEP_ERR_CUDA;
+  for (int64_t e = 0; e < c->herm_nnz; ++e)
+    if (hr[e] == hc[e] && (a_val[2 * e + 1] != 0.0 || b_val[2 * e + 1] != 0.0)) return KEP_ERR_INVALID;
+  const size_t m = c->herm_emb_src.size();
+  std::vector<double> av(m), bv(m);
+  for (size_t o = 0; o < m; ++o) {
+    const int64_t e = c->herm_emb_src[o];
+    const int8_t part = c->herm_emb_part[o];
+    av[o] = part == 0 ? a_val[2 * e] : part * a_val[2 * e + 1];
+    bv[o] = part == 0 ? b_val[2 * e] : part * b_val[2 * e + 1];
+  }
+  return set_values_real(c, av.data(), bv.data());
 }

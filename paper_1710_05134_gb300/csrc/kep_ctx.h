@@ -39,6 +39,8 @@ struct kep_ctx {
   bool herm_lower = false;
   int32_t* d_hrow = nullptr;        // per caller entry: row, column (in allocs)
   int32_t* d_hcol = nullptr;
+  std::vector<int64_t> herm_emb_src;  // per entry given to the real analysis: the caller's entry
+  std::vector<int8_t> herm_emb_part;  //   and the part it holds: 0 Re, +1 Im, -1 -Im
   // factorization slots: 0 = the public "last factor" (kep_factor / kep_solve),
   // 1 = the factor of B kept by the eigenpair driver during stage 1
   kep::FactorSlot slot[2]{};
@@ -91,6 +93,8 @@ kep_status herm_solve_refined(kep_ctx* c, const double* rhs, double* x, int ptr_
                               int32_t* iters, double* berr);
 kep_status herm_grad(kep_ctx* c, double lambda, const double* x, double lambda_bar, double* ga, double* gb,
                      int ptr_kind);
+kep_status set_values_real(kep_ctx* c, const double* a_val, const double* b_val);
+kep_status herm_set_values(kep_ctx* c, const double* a_val, const double* b_val);
 // interleaved (re, im) complex vector of order herm_n <-> the embedding's [re; im] (device)
 kep_status herm_to_blocked(kep_ctx* c, const double* in, double* out);
 kep_status herm_to_interleaved(kep_ctx* c, const double* in, double* out);

@@ -307,12 +307,10 @@ class Problem:
         return [FactorResult(o.neg, o.zero, o.pos, o.delayed, KEP_OK) for o in out]
 
     def set_values(self, a, b):
-        """New values of A and B on the analysed pattern (same layout as at construction; real
-        pencils only)."""
-        if self.hermitian:
-            raise ValueError("set_values is for real pencils")
-        a = np.ascontiguousarray(a, dtype=np.float64)
-        b = np.ascontiguousarray(b, dtype=np.float64)
+        """New values of A and B on the analysed pattern (same layout and dtype as at
+        construction)."""
+        a = self._host(a)
+        b = self._host(b)
         if a.size != self.nnz or b.size != self.nnz:
             raise ValueError("values must match the analysed pattern")
         _check(lib().kep_set_values(self._h, a.ctypes.data, b.ctypes.data), "kep_set_values")
@@ -407,8 +405,11 @@ class KthEigenvalue:
 
         lam = KthEigenvalue.apply(problem, k, a_vals, b_vals)
 
-    a_vals, b_vals: float64 tensors in the layout of the problem's pattern; the forward pass loads
-    them with set_values and runs Algorithm 4 (kwargs of kth_eigenpair via problem.kth_kwargs)."""
+    a_vals, b_vals: float64 tensors (complex128 for a Hermitian problem) in the layout of the
+    problem's pattern; the forward pass loads them with set_values and runs Algorithm 4 (kwargs of
+    kth_eigenpair via problem.kth_kwargs).  For complex values the gradient is
+    d lambda / d Re + i d lambda / d Im of each stored entry (PyTorch's convention for a real
+    output)."""
 
     @staticmethod
     def _fn():

@@ -124,3 +124,34 @@ def test_fp32_factor_refined_solve(kep, hpen):
     assert be <= 1e-13 and be_own <= 4e-13 and 1 <= it <= 30
     x_ref = np.linalg.solve(M, rhs)
     assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-10
+
+
+def test_autograd_and_new_values(kep, hpen):
+    """KthEigenvalue on complex values: lambda_k and its gradient (d/dRe + i d/dIm of each stored
+    entry) against the oracle; set_values with doubled A doubles lambda_k; conjugated values (the
+    transposed pencil) keep it; an imaginary diagonal is rejected."""
+    import torch
+    p, A, B, lam, X = hpen
+    k = p.k
+    nrm = np.abs(A).sum(1).max()
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    _, GA, GB = core.eig_grad(A, B, k)
+    scale = np.abs(GA).max()
+    with kep.Problem.from_pencil(p) as P:
+        a = torch.tensor(p.a, requires_grad=True)
+        b = torch.tensor(p.b, requires_grad=True)
+        lk = kep.KthEigenvalue.apply(P, k, a, b)
+        lk.backward()
+        assert abs(lk.item() - lam[k - 1]) <= 1e-10 * nrm
+        assert a.grad.dtype == torch.complex128
+        assert np.abs(a.grad.numpy() - GA[rows, p.colind]).max() <= 1e-8 * scale
+        assert np.abs(b.grad.numpy() - GB[rows, p.colind]).max() <= 1e-8 * scale * max(1.0, abs(lam[k - 1]))
+        P.set_values(2.0 * p.a, p.b)
+        assert abs(P.kth_eigenpair(k, want_vector=False)[0] - 2.0 * lam[k - 1]) <= 2e-10 * nrm
+        P.set_values(np.conj(p.a), np.conj(p.b))
+        assert abs(P.kth_eigenpair(k, want_vector=False)[0] - lam[k - 1]) <= 1e-10 * nrm
+        bad = p.a.copy()
+        bad[np.flatnonzero(rows == p.colind)[3]] += 0.5j
+        with pytest.raises(kep.KepError) as e:
+            P.set_values(bad, p.b)
+        assert e.value.code == kep.KEP_ERR_INVALID
