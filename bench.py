@@ -227,7 +227,7 @@ def measure_fp32_factor(P, p, torch):
     rhs = np.random.default_rng(1).normal(size=n)
     res = {}
     for mode in ("fp64_accurate", "fp32_refined"):
-        P.set_schur_mode(True, 1024, fp32=(mode == "fp32_refined"))
+        P.set_schur_mode(True, fp32=(mode == "fp32_refined"))
         sync(); t0 = time.perf_counter()
         P.factor(sigma)
         sync(); tf = time.perf_counter() - t0
@@ -241,7 +241,7 @@ def measure_fp32_factor(P, p, torch):
             xs, it, be = P.solve(rhs), 0, None
         sync(); ts_ = time.perf_counter() - t0
         res[mode] = {"factor_s": tf, "solve_s": ts_, "corrections": it, "backward_error": be}
-    P.set_schur_mode(True, 1024)
+    P.set_schur_mode(True)
     return res
 
 

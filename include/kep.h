@@ -167,7 +167,7 @@ kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, const int32_t
  * Arithmetic of the deferred Schur update (the update of a front's trailing matrix with a window of
  * up to 256 pivots, Algorithm 1' factorization step).
  *   KEP_SCHUR_FP64      FP64 FMA tiles everywhere.
- *   KEP_SCHUR_EMULATED  (default, min_front = 1024) fronts of order >= min_front form the
+ *   KEP_SCHUR_EMULATED  (default, min_front = 512) fronts of order >= min_front form the
  *                       update from bf16 tensor-core products of an exact splitting of L and L*D
  *                       into eight 8-bit pieces per entry (column balancing, per-row power-of-two
  *                       scales, exact FP32 level sums, exact int64 combination): as accurate as an

@@ -69,7 +69,7 @@ struct kep_ctx {
   std::vector<int32_t> slot_nelim[2];   // pivots eliminated per front, per slot (host copy)
   kep::Timer timer;
   int schur_mode = KEP_SCHUR_EMULATED;
-  int64_t emul_min_front = 1024;
+  int64_t emul_min_front = 512;
   void* emul_ws = nullptr;          // tensor-core update workspace (in mem_allocs)
   int64_t emul_bytes = 0;           // its size
   int64_t* d_emul_off = nullptr;    // per level position: workspace offset within its batch (in mem_allocs)

@@ -255,7 +255,7 @@ class Problem:
         self._stream = stream
         _check(lib().kep_set_stream(self._h, ctypes.c_void_p(int(handle) if handle else 0)), "kep_set_stream")
 
-    def set_schur_mode(self, emulated: bool, min_front: int = 1024, *, fp32: bool = False):
+    def set_schur_mode(self, emulated: bool, min_front: int = 512, *, fp32: bool = False):
         """Deferred Schur updates of fronts of order >= min_front on the tensor cores (FP64-accurate
         splitting) when emulated, else FP64 FMA everywhere; fp32: every Schur update in FP32 (a
         reduced-precision factor for solve_refined)."""
