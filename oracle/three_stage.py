@@ -22,7 +22,7 @@ Algorithms of the paper, step by step and in its notation, on plain operators:
 Operators come from ``DenseOps`` (dense numpy, small n) or ``SparseOps`` (scipy sparse LU for
 solves, (c3) for inertia).  Library solves serve as steps; the method's arithmetic is here.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
   * random start vectors are N(0, 1) entries; callers may pass them in (the GPU path takes the same);
   * "with reorthogonalization" = full classical Gram-Schmidt applied twice, in the inner product the
     decomposition is orthonormal in (B for Eq. 2.2, B^{-1} for Eq. 2.5);
