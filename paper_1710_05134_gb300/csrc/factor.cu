@@ -825,7 +825,15 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       const int gx_upd = grid_cap(tb * (tb + 1) / 2, per_front_upd);
       const int gx_win = grid_cap(tb * (kWindow / kTile + 1), per_front_upd);
       int64_t steps = (max_p + kPanel - 1) / kPanel + 1;
+      // a guard, not a tuning knob: every step eliminates or moves on from a block, and a column
+      // that fails the threshold is retried at most once per pass over the remaining columns
+      // before it is delayed, so a level takes at most about (blocks)^2 steps
+      const int64_t blocks = (max_p + kPanel - 1) / kPanel + 2;
+      const int64_t step_cap = 64 + 2 * blocks * blocks;
+      int64_t steps_done = 0;
       while (true) {
+        if (steps_done > step_cap) return KEP_ERR_NOT_CONVERGED;
+        steps_done += steps;
         for (int64_t it = 0; it < steps; ++it) {
           KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, kPanelThreads, 0, st>>>(F.T, F.S, F.W, B));
           KEP_LAUNCH(F.timer, KC_L21, st, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B));
