@@ -51,7 +51,10 @@ enum { KEP_HOST = 0, KEP_DEVICE = 1 };
 enum {
   KEP_PATTERN_FULL = 0,       /* CSR holds both triangles */
   KEP_PATTERN_LOWER = 1,      /* CSR holds the lower triangle (col <= row) only */
-  KEP_ORDER_GRAPH = 2         /* ignore coords; order by graph breadth-first levels */
+  KEP_ORDER_GRAPH = 2,        /* ignore coords; order by graph breadth-first levels */
+  KEP_ORDER_REFINED = 4       /* nested dissection with a search over balanced cuts on every
+                                 long axis and minimum-vertex-cover separators (slower analysis,
+                                 less fill; see kep_symbolic_info) */
 };
 
 /* Inertia of a factored matrix: counts of negative, zero and positive eigenvalues of D, and the
@@ -126,7 +129,7 @@ void kep_default_params(kep_params* p);
  * colind   column indices (int32, 0 <= c < n); no duplicates within a row.
  * a_val, b_val  values of A and B on that pattern (double, rowptr[n] each).  Both must be
  *          symmetric; with KEP_PATTERN_LOWER only entries with colind <= row are given.
- * flags    KEP_PATTERN_FULL / KEP_PATTERN_LOWER, optionally | KEP_ORDER_GRAPH.
+ * flags    KEP_PATTERN_FULL / KEP_PATTERN_LOWER, optionally | KEP_ORDER_GRAPH, | KEP_ORDER_REFINED.
  * coords   optional 3n doubles (x, y, z of the atom owning each row; an ordering hint only).
  * out      receives the new context.
  * Computes the nested-dissection ordering, the assembly tree, front structures and index maps

@@ -10,6 +10,11 @@
 //     breadth-first level from a pseudo-peripheral vertex); the vertex separator is the lighter
 //     of the two one-sided boundaries of that cut.  Periodic boundaries need no special case:
 //     the wrap-around edges are part of the cut, so their boundary joins the separator.
+//     Refined variant (option): several balanced cut positions on every long axis are tried, and
+//     each cut's separator is a minimum-weight vertex cover of the bipartite graph of cut edges
+//     (by Koenig's theorem a minimum cut of the unit-network src -> side 1 -> side 2 -> sink,
+//     found with Dinic's max-flow algorithm); the cut with the lightest separator, weighted by
+//     its imbalance, is taken.
 //  3. Assembly tree: every ND node is one front whose fully-summed variables are the node's
 //     variables; its contribution-block rows are its later neighbours plus its children's
 //     contribution rows; its parent is the front owning the smallest of those rows.
@@ -19,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 
 #include "kep_internal.h"
@@ -144,6 +150,7 @@ struct ND {
   const Quotient& q;
   const double* coords;          // per row (n x 3) or null
   int64_t leaf_weight;
+  bool refined = false;          // cut search and minimum-vertex-cover separators
   std::vector<std::vector<int32_t>> nodes;   // supernodes of each ND node, post-order
   std::vector<int32_t> tag, side, level, queue;
   int32_t gen = 0;
@@ -184,9 +191,159 @@ struct ND {
     nodes.push_back(S);
   }
 
+  // Minimum-weight vertex cover of the bipartite graph of cut edges between X (side 1) and Y
+  // (side 2) inside the piece marked g: max flow from src through x (capacity w_x), x -> y for
+  // every cut edge (unbounded), y (capacity w_y) to sink; the cover is the set of X vertices not
+  // reachable from src in the residual graph plus the Y vertices that are.
+  std::vector<int32_t> min_cover(const std::vector<int32_t>& X, const std::vector<int32_t>& Y, int32_t g) {
+    const int32_t nx = static_cast<int32_t>(X.size()), ny = static_cast<int32_t>(Y.size());
+    const int32_t src = nx + ny, snk = nx + ny + 1, N = nx + ny + 2;
+    std::vector<int32_t>& pos = level;               // scratch: position of each Y vertex
+    for (int32_t i = 0; i < ny; ++i) pos[Y[i]] = nx + i;
+    struct Edge { int32_t to; int64_t cap; };
+    std::vector<Edge> es;
+    std::vector<std::vector<int32_t>> adj(N);
+    auto add = [&](int32_t a, int32_t b, int64_t cap) {
+      adj[a].push_back(static_cast<int32_t>(es.size())); es.push_back({b, cap});
+      adj[b].push_back(static_cast<int32_t>(es.size())); es.push_back({a, 0});
+    };
+    const int64_t kInf = int64_t(1) << 40;
+    for (int32_t i = 0; i < nx; ++i) add(src, i, q.w[X[i]]);
+    for (int32_t i = 0; i < ny; ++i) add(nx + i, snk, q.w[Y[i]]);
+    for (int32_t i = 0; i < nx; ++i)
+      for (int64_t e = q.qrp[X[i]]; e < q.qrp[X[i] + 1]; ++e) {
+        const int32_t u = q.qci[e];
+        if (tag[u] == g && side[u] == 2) add(i, pos[u], kInf);
+      }
+    std::vector<int32_t> dist(N), it(N), bq;
+    auto layer = [&]() {
+      std::fill(dist.begin(), dist.end(), -1);
+      bq.assign(1, src); dist[src] = 0;
+      for (size_t h = 0; h < bq.size(); ++h)
+        for (int32_t ei : adj[bq[h]])
+          if (es[ei].cap > 0 && dist[es[ei].to] < 0) { dist[es[ei].to] = dist[bq[h]] + 1; bq.push_back(es[ei].to); }
+      return dist[snk] >= 0;
+    };
+    // augmenting paths are src -> x -> y -> sink: the recursion is at most three deep
+    std::function<int64_t(int32_t, int64_t)> push = [&](int32_t v, int64_t f) -> int64_t {
+      if (v == snk) return f;
+      for (int32_t& i = it[v]; i < static_cast<int32_t>(adj[v].size()); ++i) {
+        Edge& e = es[adj[v][i]];
+        if (e.cap > 0 && dist[e.to] == dist[v] + 1) {
+          const int64_t d = push(e.to, std::min(f, e.cap));
+          if (d > 0) { e.cap -= d; es[adj[v][i] ^ 1].cap += d; return d; }
+        }
+      }
+      return 0;
+    };
+    while (layer()) {
+      std::fill(it.begin(), it.end(), 0);
+      while (push(src, kInf) > 0) {}
+    }
+    std::vector<char> reach(N, 0);
+    bq.assign(1, src); reach[src] = 1;
+    for (size_t h = 0; h < bq.size(); ++h)
+      for (int32_t ei : adj[bq[h]])
+        if (es[ei].cap > 0 && !reach[es[ei].to]) { reach[es[ei].to] = 1; bq.push_back(es[ei].to); }
+    std::vector<int32_t> cover;
+    for (int32_t i = 0; i < nx; ++i) if (!reach[i]) cover.push_back(X[i]);
+    for (int32_t i = 0; i < ny; ++i) if (reach[nx + i]) cover.push_back(Y[i]);
+    return cover;
+  }
+
+  // the one-sided boundaries of the cut S1 | S2 (side[] set) inside the piece marked g
+  void boundaries(const std::vector<int32_t>& S1, const std::vector<int32_t>& S2, int32_t g,
+                  std::vector<int32_t>& B1, std::vector<int32_t>& B2) {
+    B1.clear(); B2.clear();
+    for (int32_t s : S1)
+      for (int64_t e = q.qrp[s]; e < q.qrp[s + 1]; ++e) {
+        int32_t u = q.qci[e];
+        if (tag[u] == g && side[u] == 2) { B1.push_back(s); break; }
+      }
+    for (int32_t s : S2)
+      for (int64_t e = q.qrp[s]; e < q.qrp[s + 1]; ++e) {
+        int32_t u = q.qci[e];
+        if (tag[u] == g && side[u] == 1) { B2.push_back(s); break; }
+      }
+  }
+
+  // Refined split of S (marked g, weight W): sort keys of every axis at least half as long as the
+  // longest (or the breadth-first levels), cut positions with 42-58 % of the weight on the first
+  // side, minimum-vertex-cover separators; the cut minimising w(sep) (1 + 2 |W1 - W2| / W).
+  void split_refined(const std::vector<int32_t>& S, int32_t g, int64_t W, std::vector<int32_t>& S1,
+                     std::vector<int32_t>& S2, std::vector<int32_t>& sep) {
+    std::vector<std::vector<double>> keys;
+    if (coords) {
+      double ext[3], emax = 0;
+      for (int ax = 0; ax < 3; ++ax) {
+        double lo = 1e300, hi = -1e300;
+        for (int32_t s : S) { double c = coord(s, ax); lo = std::min(lo, c); hi = std::max(hi, c); }
+        ext[ax] = hi - lo;
+        emax = std::max(emax, ext[ax]);
+      }
+      for (int ax = 0; ax < 3; ++ax) {
+        if (ext[ax] < 0.5 * emax) continue;
+        keys.emplace_back(S.size());
+        for (size_t i = 0; i < S.size(); ++i) keys.back()[i] = coord(S[i], ax);
+      }
+    } else {
+      int32_t root = S[0];
+      int32_t d = bfs(S, root, g);
+      for (int it = 0; it < 4; ++it) {
+        int32_t far = root, best = -1;
+        for (int32_t s : S) if (level[s] > best) { best = level[s]; far = s; }
+        int32_t d2 = bfs(S, far, g);
+        if (d2 <= d) { bfs(S, root, g); break; }
+        d = d2; root = far;
+      }
+      keys.emplace_back(S.size());
+      for (size_t i = 0; i < S.size(); ++i)
+        keys.back()[i] = level[S[i]] < 0 ? 1e30 : static_cast<double>(level[S[i]]);
+    }
+    double best_score = 1e300;
+    std::vector<int32_t> idx(S.size()), T1, T2, B1, B2;
+    std::vector<int64_t> pre(S.size() + 1);
+    for (const std::vector<double>& key : keys) {
+      std::iota(idx.begin(), idx.end(), 0);
+      std::sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        return key[a] != key[b] ? key[a] < key[b] : S[a] < S[b];
+      });
+      pre[0] = 0;
+      for (size_t i = 0; i < idx.size(); ++i) pre[i + 1] = pre[i] + q.w[S[idx[i]]];
+      std::vector<size_t> cuts;
+      size_t med = 0;
+      while (med < idx.size() && 2 * pre[med + 1] <= W) ++med;
+      cuts.push_back(std::min(std::max<size_t>(med, 1), idx.size() - 1));
+      size_t a = 0, b = idx.size() - 1;
+      while (a < idx.size() && 100 * pre[a] < 42 * W) ++a;
+      while (b > 0 && 100 * pre[b] > 58 * W) --b;
+      if (a >= 1 && b > a)
+        for (size_t t = 0; t <= 12; ++t) cuts.push_back(a + (b - a) * t / 12);
+      for (size_t cut : cuts) {
+        T1.clear(); T2.clear();
+        for (size_t i = 0; i < idx.size(); ++i) {
+          const int32_t s = S[idx[i]];
+          if (i < cut) { T1.push_back(s); side[s] = 1; } else { T2.push_back(s); side[s] = 2; }
+        }
+        boundaries(T1, T2, g, B1, B2);
+        std::vector<int32_t> cand = weight(B1) <= weight(B2) ? B1 : B2;
+        if (!B1.empty()) {
+          std::vector<int32_t> cover = min_cover(B1, B2, g);
+          if (weight(cover) < weight(cand)) cand.swap(cover);
+        }
+        const double w1 = static_cast<double>(pre[cut]), w2 = static_cast<double>(W - pre[cut]);
+        const double score = static_cast<double>(weight(cand)) * (1.0 + 2.0 * std::fabs(w1 - w2) / W);
+        if (score < best_score) { best_score = score; S1 = T1; S2 = T2; sep.swap(cand); }
+      }
+    }
+    for (int32_t s : S1) side[s] = 1;
+    for (int32_t s : S2) side[s] = 2;
+  }
+
   // Split S; appends the ids of the resulting top nodes to tops.
   void run(std::vector<int32_t> S, std::vector<int32_t>& tops) {
     if (S.empty()) return;
+    if (refined) { run_refined(std::move(S), tops); return; }
     int64_t W = weight(S);
     if (W <= leaf_weight || S.size() < 4) { emit_leaf(S, tops); return; }
     int32_t g = ++gen;
@@ -259,6 +416,30 @@ struct ND {
     tops.push_back(static_cast<int32_t>(nodes.size()));
     nodes.push_back(sep);
   }
+
+  void run_refined(std::vector<int32_t> S, std::vector<int32_t>& tops) {
+    int64_t W = weight(S);
+    if (W <= leaf_weight || S.size() < 4) { emit_leaf(S, tops); return; }
+    int32_t g = ++gen;
+    for (int32_t s : S) tag[s] = g;
+    std::vector<int32_t> S1, S2, sep;
+    split_refined(S, g, W, S1, S2, sep);
+    if (10 * weight(sep) > 6 * W) { emit_leaf(S, tops); return; }
+    int32_t gs = ++gen;
+    for (int32_t s : sep) tag[s] = gs;
+    std::vector<int32_t> R1, R2;
+    for (int32_t s : S1) if (tag[s] != gs) R1.push_back(s);
+    for (int32_t s : S2) if (tag[s] != gs) R2.push_back(s);
+    std::vector<int32_t> kids;
+    run_refined(std::move(R1), kids);
+    run_refined(std::move(R2), kids);
+    if (sep.empty()) {
+      tops.insert(tops.end(), kids.begin(), kids.end());
+      return;
+    }
+    tops.push_back(static_cast<int32_t>(nodes.size()));
+    nodes.push_back(sep);
+  }
 };
 
 }  // namespace
@@ -301,7 +482,7 @@ void plan_memory(Plan& P, int32_t slack_base) {
 
 kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                       const std::vector<double>& av, const std::vector<double>& bv,
-                      const double* coords, bool graph_order, int32_t slack_base, Plan& P,
+                      const double* coords, bool graph_order, bool refined, int32_t slack_base, Plan& P,
                       std::string& err) {
   P = Plan();
   P.n = n;
@@ -314,6 +495,7 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
   }
   Quotient q = build_quotient(n, rp, ci);
   ND nd(q, graph_order ? nullptr : coords, /*leaf rows*/ 64);
+  nd.refined = refined;
   std::vector<int32_t> all(q.ns);
   std::iota(all.begin(), all.end(), 0);
   // each connected piece of the graph is split on its own (disconnected pieces share no separator)

@@ -413,7 +413,7 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return KEP_ERR_CUDA; }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   std::string err;
-  kep_status st = build_plan(n, cnt, ci, av, bv, coords, (flags & KEP_ORDER_GRAPH) != 0, 8, c->plan, err);
+  kep_status st = build_plan(n, cnt, ci, av, bv, coords, (flags & KEP_ORDER_GRAPH) != 0, (flags & KEP_ORDER_REFINED) != 0, 8, c->plan, err);
   if (st != KEP_OK) { delete c; return st; }
   const Plan& P = c->plan;
 #define UP(dst, vec) do { st = dev_upload(c, &dst, vec); if (st != KEP_OK) { kep_destroy(c); return st; } } while (0)
@@ -491,7 +491,7 @@ kep_status kep_symbolic_info(int64_t n, const int64_t* rowptr, const int32_t* co
   if (ps != KEP_OK) return ps;
   Plan P;
   std::string err;
-  const kep_status st = build_plan(n, FP.cnt, FP.ci, FP.av, FP.bv, coords, (flags & KEP_ORDER_GRAPH) != 0, 8, P, err);
+  const kep_status st = build_plan(n, FP.cnt, FP.ci, FP.av, FP.bv, coords, (flags & KEP_ORDER_GRAPH) != 0, (flags & KEP_ORDER_REFINED) != 0, 8, P, err);
   if (st != KEP_OK) return st;
   info->n = P.n;
   info->nnz = P.nnz;

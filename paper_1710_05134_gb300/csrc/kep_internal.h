@@ -134,10 +134,11 @@ struct Plan {
 };
 
 // Build the plan from a full symmetric CSR pattern (both triangles, sorted, no duplicates).
-// coords: optional n*3. graph_order forces the coordinate-free ordering.
+// coords: optional n*3. graph_order forces the coordinate-free ordering; refined selects the
+// cut search with minimum-vertex-cover separators.
 kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                       const std::vector<double>& av, const std::vector<double>& bv,
-                      const double* coords, bool graph_order, int32_t slack_base, Plan& plan,
+                      const double* coords, bool graph_order, bool refined, int32_t slack_base, Plan& plan,
                       std::string& err);
 
 // (Re)compute the slack-dependent memory plan.

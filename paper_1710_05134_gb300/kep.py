@@ -18,7 +18,7 @@ KEP_OK, KEP_ERR_INVALID, KEP_ERR_NOT_SPD, KEP_ERR_SINGULAR = 0, 1, 2, 3
 KEP_ERR_NOT_CONVERGED, KEP_ERR_CLUSTER, KEP_ERR_POOL, KEP_ERR_TIMEOUT = 4, 5, 6, 7
 KEP_ERR_CUDA, KEP_ERR_NONFINITE, KEP_ERR_NOMEM = 8, 9, 10
 KEP_HOST, KEP_DEVICE = 0, 1
-KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH = 0, 1, 2
+KEP_PATTERN_FULL, KEP_PATTERN_LOWER, KEP_ORDER_GRAPH, KEP_ORDER_REFINED = 0, 1, 2, 4
 
 # symbols declared in include/kep.h
 EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_get_info", "kep_symbolic_info", "kep_set_stream", "kep_factor",
@@ -134,7 +134,8 @@ def lib() -> ctypes.CDLL:
     return _LIB
 
 
-def symbolic_info(n, rowptr, colind, coords=None, *, lower: bool = False, graph_order: bool = False) -> Info:
+def symbolic_info(n, rowptr, colind, coords=None, *, lower: bool = False, graph_order: bool = False,
+                  refined_order: bool = False) -> Info:
     """The symbolic facts (#nzf, flop count, fronts) of a pattern, computed on the host only."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
@@ -142,7 +143,8 @@ def symbolic_info(n, rowptr, colind, coords=None, *, lower: bool = False, graph_
     if coords is not None:
         coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1)
         cp = coords.ctypes.data_as(ctypes.c_void_p)
-    flags = (KEP_PATTERN_LOWER if lower else KEP_PATTERN_FULL) | (KEP_ORDER_GRAPH if graph_order else 0)
+    flags = ((KEP_PATTERN_LOWER if lower else KEP_PATTERN_FULL) | (KEP_ORDER_GRAPH if graph_order else 0)
+             | (KEP_ORDER_REFINED if refined_order else 0))
     inf = Info()
     _check(lib().kep_symbolic_info(int(n), rowptr.ctypes.data, colind.ctypes.data, flags, cp, ctypes.byref(inf)),
            "kep_symbolic_info")
@@ -192,7 +194,7 @@ class Problem:
     derivatives are then complex128, and inertia counts are those of the complex pencil."""
 
     def __init__(self, n, rowptr, colind, a, b, coords=None, *, lower: bool = False,
-                 graph_order: bool = False):
+                 graph_order: bool = False, refined_order: bool = False):
         L = lib()
         self.n = int(n)
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
@@ -207,7 +209,8 @@ class Problem:
             if coords.size != 3 * self.n:
                 raise ValueError("coords must hold 3 values per row")
             cp = coords.ctypes.data_as(ctypes.c_void_p)
-        flags = (KEP_PATTERN_LOWER if lower else KEP_PATTERN_FULL) | (KEP_ORDER_GRAPH if graph_order else 0)
+        flags = ((KEP_PATTERN_LOWER if lower else KEP_PATTERN_FULL) | (KEP_ORDER_GRAPH if graph_order else 0)
+                 | (KEP_ORDER_REFINED if refined_order else 0))
         h = ctypes.c_void_p()
         fn, name = (L.kep_analyze_hermitian, "kep_analyze_hermitian") if self.hermitian else (L.kep_analyze, "kep_analyze")
         _check(fn(self.n, rowptr.ctypes.data, colind.ctypes.data, a.ctypes.data, b.ctypes.data, flags, cp,

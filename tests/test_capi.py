@@ -105,3 +105,25 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["steps"] == 1 and line["warmup"] == 3
+
+
+def test_refined_ordering_reduces_fill_without_gpu():
+    """KEP_ORDER_REFINED (cut search + minimum-vertex-cover separators) gives less fill and fewer
+    flops than the default ordering, on the same pattern; the default ordering is unchanged."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import paper_1710_05134_gb300 as k
+    from gen import make_pair, workload
+    p = make_pair(8, 8, 6, seed=3, vacancies=300)
+    d = k.symbolic_info(p.n, p.rowptr, p.colind, p.coords)
+    r = k.symbolic_info(p.n, p.rowptr, p.colind, p.coords, refined_order=True)
+    assert (r.n, r.nnz) == (d.n, d.nnz)
+    assert r.flops_factor < 0.9 * d.flops_factor and r.nnz_factor < d.nnz_factor
+    # without coordinates (breadth-first keys) the option still runs and is no worse
+    g = k.symbolic_info(p.n, p.rowptr, p.colind, graph_order=True)
+    gr = k.symbolic_info(p.n, p.rowptr, p.colind, graph_order=True, refined_order=True)
+    assert gr.flops_factor <= g.flops_factor
+    # the default ordering of the n = 49,768 workload (what the measurements in profiles/ used)
+    m = workload("mid")
+    dm = k.symbolic_info(m.n, m.rowptr, m.colind, m.coords)
+    assert (dm.nfronts, dm.nnz_factor, dm.max_front) == (711, 99508196, 7684)
