@@ -57,12 +57,14 @@ class Bracket:
 def multisection_step(count, k: int, br: Bracket, nshift: int, rank: int = 0, world: int = 1,
                       dist=None, count_many=None) -> Bracket:
     """One step: [lower, upper) cut into nshift + 1 equal parts at sigma_q = lower + q (upper -
-    lower) / (nshift + 1), q = 1..nshift; keep the part whose ends bracket k.  count_many (a list
+    lower) / (nshift + 1), q = 1..nshift (the midpoint (lower + upper) / 2 for nshift = 1); keep the
+    part whose ends bracket k.  count_many (a list
     of shifts -> their counts, e.g. ConcurrentCounter.count_many) replaces one-at-a-time count."""
     if nshift < 1:
         raise ValueError("nshift >= 1")
     lo, hi = br.lower, br.upper
-    sig = [lo + (hi - lo) * q / (nshift + 1) for q in range(1, nshift + 1)]
+    # nshift = 1: the midpoint, as Algorithm 1' bisects
+    sig = [0.5 * (lo + hi)] if nshift == 1 else [lo + (hi - lo) * q / (nshift + 1) for q in range(1, nshift + 1)]
     mine = shard(range(nshift), rank, world)
     local = count_many([sig[q] for q in mine]) if count_many else [int(count(sig[q])) for q in mine]
     nus = gather_counts([int(v) for v in local], nshift, rank, world, dist)
@@ -88,6 +90,26 @@ def multisection(count, k: int, br: Bracket, m_max: int = 20, nshift: int = 8, r
             return br
         br = multisection_step(count, k, br, nshift, rank, world, dist, count_many)
     raise RuntimeError("multisection did not narrow the bracket (a cluster of eigenvalues?)")
+
+
+def bisect_to_width(count, k: int, br: Bracket, rel_tol: float = 1e-10, nshift: int = 1, rank: int = 0,
+                    world: int = 1, dist=None, max_steps: int = 400, count_many=None):
+    """Algorithm 1 run to a width instead of to m_max: narrow [lower, upper) (nu(lower) < k <=
+    nu(upper)) until (upper - lower) / max(|lower|, |upper|) < rel_tol, the stop of the straight-
+    bisection comparison in Section 4.3.2; lambda_k is taken as the midpoint.  nshift > 1 cuts each
+    step into nshift + 1 parts.  Returns (lambda_hat, bracket, steps)."""
+    if not br.nu_lower < k <= br.nu_upper:
+        raise ValueError("the bracket must hold k: nu_lower < k <= nu_upper")
+    steps = 0
+    while (br.upper - br.lower) / max(abs(br.lower), abs(br.upper)) >= rel_tol:
+        if steps >= max_steps:
+            raise RuntimeError("bisection did not reach the width")
+        nxt = multisection_step(count, k, br, nshift, rank, world, dist, count_many)
+        if (nxt.lower, nxt.upper) == (br.lower, br.upper):
+            break                                  # the shifts no longer separate (rounding)
+        br = nxt
+        steps += 1
+    return 0.5 * (br.lower + br.upper), br, steps
 
 
 class ConcurrentCounter:

@@ -155,3 +155,22 @@ def test_concurrent_counter_keeps_shift_order():
                                                                    single.nu_upper)
     # every context served, none by two threads at once
     assert set(calls) == {0, 1} and max(peak.values()) == 1
+
+
+def test_bisection_to_width_matches_oracle():
+    """Straight bisection to a relative width (the comparison run of Section 4.3.2) gives the
+    oracle's lambda_k and iteration count, and lambda_k of the closed-form diagonal pencil within
+    the width; multisection reaches the same width in fewer steps."""
+    lam = _pencil()
+    ops = _Ops(lam)
+    lo, hi = -10.0, 10.0
+    ref, it_ref = ts.bisect_straight(ops, K, lo, hi, rel_tol=1e-10)
+    got, br, steps = ms.bisect_to_width(ops.nu, K, ms.Bracket(lo, hi, 0, N), rel_tol=1e-10)
+    assert got == ref and steps == it_ref
+    assert abs(got - lam[K - 1]) <= 1e-10 * max(abs(br.lower), abs(br.upper))
+    assert br.nu_lower < K <= br.nu_upper
+    got8, br8, steps8 = ms.bisect_to_width(ops.nu, K, ms.Bracket(lo, hi, 0, N), rel_tol=1e-10, nshift=8)
+    assert abs(got8 - lam[K - 1]) <= 1e-10 * max(abs(br8.lower), abs(br8.upper))
+    assert steps8 < steps / 2
+    with pytest.raises(ValueError):
+        ms.bisect_to_width(ops.nu, K, ms.Bracket(lo, hi, K, N))
