@@ -127,3 +127,13 @@ def test_refined_ordering_reduces_fill_without_gpu():
     m = workload("mid")
     dm = k.symbolic_info(m.n, m.rowptr, m.colind, m.coords)
     assert (dm.nfronts, dm.nnz_factor, dm.max_front) == (711, 99508196, 7684)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the oracle arm; the other ranks exit 0 without output."""
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "small",
+                        "--gpus", "2"], capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
+    assert r.returncode == 0 and r.stdout.strip() == ""
