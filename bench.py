@@ -167,8 +167,8 @@ def run_reference(args):
     return 0
 
 
-VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "gershgorin_multisection8", "stage3_f32_ir",
-            "hermitian_mid")
+VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_min_front", "gershgorin_multisection8",
+            "stage3_f32_ir", "hermitian_mid")
 
 
 def measure_variants(P, p, torch, kth, which="all"):
@@ -198,6 +198,13 @@ def measure_variants(P, p, torch, kth, which="all"):
         out["fp32_factor_ir"] = measure_fp32_factor(P, p, torch)
     if "two_shifts_in_flight" in want:
         out["two_shifts_in_flight"] = measure_two_in_flight(P, p, torch)
+    if "autotune_min_front" in want:
+        from paper_1710_05134_gb300 import tune
+        try:
+            out["autotune_min_front"] = tune.tune_min_front(P, [0.31, 0.33], sync=sync)
+        except Exception as exc:
+            out["autotune_min_front"] = {"error": str(exc)}
+        P.set_schur_mode(True)                         # back to the default for what follows
     # Algorithm 4 variants
     for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),
                      ("stage3_f32_ir", {"solve_precision": "f32_ir"})):
@@ -328,8 +335,7 @@ def main():
     ap.add_argument("--kth", action="store_true",
                     help="also run Algorithm 4 once (k = n/2) and report the time to lambda_k")
     ap.add_argument("--variants", nargs="?", const="all", default=None,
-                    help="also measure the next rows (all, or a comma list of: grad, fp32_factor_ir, "
-                         "two_shifts_in_flight, gershgorin_multisection8, stage3_f32_ir, hermitian_mid)")
+                    help="also measure the next rows (all, or a comma list of: " + ", ".join(VARIANTS) + ")")
     ap.add_argument("--event-timing", type=int, default=1,
                     help="bracket every launch with CUDA events for the per-kernel roofline (1) or not (0)")
     args = ap.parse_args()
