@@ -26,7 +26,6 @@
 #include <cstring>
 #include <functional>
 #include <numeric>
-#include <thread>
 
 #include "kep_internal.h"
 
@@ -152,7 +151,6 @@ struct ND {
   const double* coords;          // per row (n x 3) or null
   int64_t leaf_weight;
   bool refined = false;          // cut search and minimum-vertex-cover separators
-  int depth = 0;                 // dissection depth of this object's root piece
   std::vector<std::vector<int32_t>> nodes;   // supernodes of each ND node, post-order
   std::vector<int32_t> tag, side, level, queue;
   int32_t gen = 0;
@@ -433,27 +431,8 @@ struct ND {
     for (int32_t s : S1) if (tag[s] != gs) R1.push_back(s);
     for (int32_t s : S2) if (tag[s] != gs) R2.push_back(s);
     std::vector<int32_t> kids;
-    if (depth < 3 && W > 20000) {
-      // the two halves on two threads, each with its own scratch arrays; their node lists are
-      // appended in the serial order (first half, second half, separator), so the result does
-      // not depend on the threading
-      ND a(q, coords, leaf_weight), b(q, coords, leaf_weight);
-      a.refined = b.refined = true;
-      a.depth = b.depth = depth + 1;
-      std::vector<int32_t> ka, kb;
-      std::thread th([&] { a.run_refined(std::move(R1), ka); });
-      b.run_refined(std::move(R2), kb);
-      th.join();
-      for (int32_t& t : ka) t += static_cast<int32_t>(nodes.size());
-      for (auto& v : a.nodes) nodes.push_back(std::move(v));
-      for (int32_t& t : kb) t += static_cast<int32_t>(nodes.size());
-      for (auto& v : b.nodes) nodes.push_back(std::move(v));
-      kids = ka;
-      kids.insert(kids.end(), kb.begin(), kb.end());
-    } else {
-      run_refined(std::move(R1), kids);
-      run_refined(std::move(R2), kids);
-    }
+    run_refined(std::move(R1), kids);
+    run_refined(std::move(R2), kids);
     if (sep.empty()) {
       tops.insert(tops.end(), kids.begin(), kids.end());
       return;
