@@ -25,12 +25,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "inertia-validated factorizations/s (n=524,288 tight-binding pencil)"
+WORKLOAD_N = {"scale": "524,288", "million": "1,048,576", "mid": "49,768", "small": "2,048"}
+
+
+def metric_for(workload: str) -> str:
+    return f"inertia-validated factorizations/s (n={WORKLOAD_N[workload]} tight-binding pencil)"
 UNIT = "factorizations/s"
 # FP64 FMA issue rate of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock).
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9
 WORKLOAD_DESC = {
     "scale": "periodic diamond 32x32x18 cells, 16,384 random vacancies, 131,072 atoms x 4 sp3 orbitals, "
              "n=524,288, jitter 0.05 A, 2.9 A cutoff",
+    "million": "periodic diamond 32x32x32 cells, 262,144 atoms x 4 sp3 orbitals, n=1,048,576, jitter 0.05 A, "
+               "2.9 A cutoff",
     "mid": "periodic diamond 12x12x12 cells, 1,382 vacancies, n=49,768",
     "small": "periodic diamond 4x4x4 cells, n=2,048",
 }
@@ -157,7 +164,7 @@ def run_reference(args):
     sample = (f"oracle sparse LDL^T (c3) on the same generator at {s['nx']}x{s['ny']}x{s['nz']} cells "
               f"(n={p.n}), {args.steps} factorizations in {dt:.2f} s, scaled to the full workload by the "
               f"GPU plan's flop ratio {ratio:.3e}")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps / 1.0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload)},
@@ -329,7 +336,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kep", choices=["kep", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "mid", "small"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "million", "mid", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kth", action="store_true",
@@ -491,7 +498,7 @@ def main():
         variants = measure_variants(P, p, torch, kth, args.variants)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload), "n": n,
