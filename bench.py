@@ -338,6 +338,8 @@ def main():
     ap.add_argument("--impl", default="kep", choices=["kep", "reference"])
     ap.add_argument("--workload", default="scale", choices=["scale", "million", "mid", "small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refined-order", action="store_true",
+                    help="analyse with the refined nested dissection (minimum-vertex-cover separators)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kth", action="store_true",
                     help="also run Algorithm 4 once (k = n/2) and report the time to lambda_k")
@@ -362,7 +364,7 @@ def main():
 
     p = make_workload(args.workload)
     t0 = time.perf_counter()
-    P = kep.Problem.from_pencil(p)
+    P = kep.Problem.from_pencil(p, refined_order=args.refined_order)
     t_analyze = time.perf_counter() - t0
     info = P.info
     stream = torch.cuda.Stream()
@@ -509,6 +511,7 @@ def main():
                            "l2": "inputs larger than L2 (front storage %.1f GB)" % (info.front_bytes / 1e9),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "analyze_s": t_analyze, "wall_s": wall,
+                           "ordering": "refined nested dissection" if args.refined_order else "nested dissection",
                            "event_timing": bool(args.event_timing),
                            "nu": nus[args.warmup:args.warmup + args.steps]},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": timing["total_launches"],
