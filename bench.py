@@ -122,10 +122,10 @@ def _measured_peaks():
                 "bf16_sustained": (1.7e15, "fallback 1.7 PFLOP/s bf16 sustained")}
 
 
-def flops_of(p) -> float:
+def flops_of(p, refined: bool = False) -> float:
     """Symbolic factorization flops of the GPU plan for pencil p (host analysis only, no device)."""
     import paper_1710_05134_gb300 as kep
-    return kep.symbolic_info(p.n, p.rowptr, p.colind, p.coords).flops_factor
+    return kep.symbolic_info(p.n, p.rowptr, p.colind, p.coords, refined_order=refined).flops_factor
 
 
 def cpu_oracle_sample(reps: int = 1):
@@ -478,7 +478,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ps, times = cpu_oracle_sample(reps=1)
-        ratio = flops_of(ps) / info.flops_factor
+        ratio = flops_of(ps, args.refined_order) / info.flops_factor
         cpu_val = (1.0 / min(times)) * ratio
         cpu = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": (f"oracle sparse LDL^T (c3, single thread) on the same generator at "
