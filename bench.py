@@ -1,10 +1,13 @@
 #!/usr/bin/env python
-"""Benchmark: inertia-validated factorizations per second on the synthetic tight-binding workload.
+"""Benchmark: inertia-validated factorizations per second and time to lambda_k on the synthetic
+tight-binding workload (default: n = 1,048,576, the periodic diamond pencil of 32x32x32 cells).
 
 A step is one pass of the whole hot path on the GPU: numeric LDL^T of A - sigma*B (assembly,
 extend-add, Bunch-Kaufman pivoting, Schur updates, inertia reduction), one solve with the factor,
-and one A/B sparse product.  Every step uses a new shift.  The default workload is the
-n = 524,288 periodic diamond pencil with 11 % vacancies (32x32x18 cells, 16,384 sites removed).
+and one A/B sparse product.  Every step uses a new shift.  After the timed steps the counts are
+validated (non-decreasing in sigma, and equal to those of a second, independently ordered
+analysis at two of the timed shifts: Sylvester's law makes the count independent of the
+ordering and of every pivot choice), and Algorithm 4 runs once for the time to lambda_k.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead (bounded sample).
 """
@@ -16,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -24,12 +28,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "inertia-validated factorizations/s (n=524,288 tight-binding pencil)"
 WORKLOAD_N = {"scale": "524,288", "million": "1,048,576", "mid": "49,768", "small": "2,048"}
 
 
 def metric_for(workload: str) -> str:
     return f"inertia-validated factorizations/s (n={WORKLOAD_N[workload]} tight-binding pencil)"
+
+
 UNIT = "factorizations/s"
 # FP64 FMA issue rate of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock).
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9
@@ -43,6 +48,9 @@ WORKLOAD_DESC = {
 }
 # cpu_baseline sample: the same generator (jitter, vacancy fraction) on a smaller periodic box
 CPU_SAMPLE = dict(nx=5, ny=5, nz=4, vacancies=89)
+# the oracle's work is scaled to the full workload by the ratio of the default-ordering GPU plan's
+# flop counts (the oracle runs its own ordering whichever ordering the GPU arm uses)
+CPU_SCALE_NOTE = "scaled by the ratio of the default nested-dissection plan's flop counts (sample / full)"
 
 
 def _env_int(name, default):
@@ -109,17 +117,24 @@ class ClockSampler:
 
 
 def _measured_peaks():
-    """bf16 peaks (FLOP/s) from MEASURED_PEAKS.json when present, else the fallback figures."""
+    """Peaks from MEASURED_PEAKS.json when present (bf16 FLOP/s burst and sustained, HBM B/s), else
+    the fallback figures; each with its source."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"bf16": (1.9e15, "of fallback: 1.9 PFLOP/s bf16 burst"),
+           "bf16_sustained": (1.7e15, "of fallback: 1.7 PFLOP/s bf16 sustained"),
+           "hbm": (6.8e12, "of fallback: 6.8 TB/s")}
     try:
         with open(path) as f:
             d = json.load(f)
-        return {"bf16": (d["bf16_tflops"] * 1e12, "measured (MEASURED_PEAKS.json bf16_tflops, burst)"),
-                "bf16_sustained": (d["bf16_tflops_sustained"] * 1e12,
-                                   "measured (MEASURED_PEAKS.json bf16_tflops_sustained)")}
-    except (OSError, KeyError, ValueError):
-        return {"bf16": (1.9e15, "fallback 1.9 PFLOP/s bf16 burst"),
-                "bf16_sustained": (1.7e15, "fallback 1.7 PFLOP/s bf16 sustained")}
+    except (OSError, ValueError):
+        return out
+    for key, field, scale in (("bf16", "bf16_tflops", 1e12), ("bf16_sustained", "bf16_tflops_sustained", 1e12),
+                              ("hbm", "hbm_gbs", 1e9)):
+        try:
+            out[key] = (float(d[field]) * scale, f"of measured: MEASURED_PEAKS.json {field}")
+        except (KeyError, TypeError, ValueError):
+            pass
+    return out
 
 
 def flops_of(p, refined: bool = False) -> float:
@@ -128,50 +143,91 @@ def flops_of(p, refined: bool = False) -> float:
     return kep.symbolic_info(p.n, p.rowptr, p.colind, p.coords, refined_order=refined).flops_factor
 
 
-def cpu_oracle_sample(reps: int = 1):
-    """Time the oracle's sparse LDL^T (c3, single thread, as it stands) on the sample pencil."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_run(seconds: float, first_shift: int = 0):
+    """The oracle's sparse LDL^T (c3, plain C, as it stands) on the sample pencil, one factorization
+    per thread at a time on every host core (independent shifts; the C call releases the GIL), for
+    about `seconds` of wall time.  Returns (sample pencil, factorizations done, wall seconds, cores)."""
     from gen import make_pair
     from oracle import core
     s = CPU_SAMPLE
     p = make_pair(s["nx"], s["ny"], s["nz"], seed=0, vacancies=s["vacancies"])
     core.sparse_inertia(p.rowptr, p.colind, p.a, p.b, 1.0, -0.3)   # compile/load outside timing
-    times = []
-    for i in range(reps):
-        t0 = time.perf_counter()
-        core.sparse_inertia(p.rowptr, p.colind, p.a, p.b, 1.0, -(0.30 + 0.013 * i))
-        times.append(time.perf_counter() - t0)
-    return p, times
+    cores = host_cores()
+    counter = [first_shift]
+    done = [0]
+    lock = threading.Lock()
+    deadline = [0.0]
+
+    def worker():
+        while True:
+            with lock:
+                if time.perf_counter() >= deadline[0]:
+                    return
+                i = counter[0]
+                counter[0] += 1
+            core.sparse_inertia(p.rowptr, p.colind, p.a, p.b, 1.0, -(0.30 + 0.013 * (i % 64)))
+            with lock:
+                done[0] += 1
+
+    threads = [threading.Thread(target=worker) for _ in range(cores)]
+    t0 = time.perf_counter()
+    deadline[0] = t0 + seconds
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    return p, done[0], time.perf_counter() - t0, cores
+
+
+def cpu_sample_desc(p, done, wall, cores, ratio, n_full):
+    s = CPU_SAMPLE
+    return (f"oracle sparse LDL^T (c3, plain C, own nested dissection) on the same generator at "
+            f"{s['nx']}x{s['ny']}x{s['nz']} cells with {s['vacancies']} vacancies (n={p.n}): {done} factorizations "
+            f"at independent shifts on {cores} threads in {wall:.1f} s, {CPU_SCALE_NOTE}, "
+            f"{ratio:.3e}, to n={n_full}")
 
 
 def run_reference(args):
-    """The CPU oracle timed on the host cores: each step factors the bounded sample once."""
+    """The CPU oracle timed on the host cores: each step is a bounded run of the oracle on the
+    sample pencil on every core, scaled to the workload."""
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
-    from gen import make_pair
-    from oracle import core
-    s = CPU_SAMPLE
-    p = make_pair(s["nx"], s["ny"], s["nz"], seed=0, vacancies=s["vacancies"])
     full = make_workload(args.workload)
-    ratio = flops_of(p) / flops_of(full)
-    for i in range(args.warmup):
-        core.sparse_inertia(p.rowptr, p.colind, p.a, p.b, 1.0, -(0.30 + 0.013 * i))
-    t0 = time.perf_counter()
+    p0 = _cpu_sample_pencil()
+    ratio = flops_of(p0) / flops_of(full)
+    per_step = 4.0
+    if args.warmup > 0:
+        cpu_oracle_run(1.0)                            # warm-up
+    done_all, wall_all, cores = 0, 0.0, 1
     for i in range(args.steps):
-        core.sparse_inertia(p.rowptr, p.colind, p.a, p.b, 1.0, -(0.30 + 0.013 * i))
-    dt = time.perf_counter() - t0
-    value = args.steps / dt * ratio
-    sample = (f"oracle sparse LDL^T (c3) on the same generator at {s['nx']}x{s['ny']}x{s['nz']} cells "
-              f"(n={p.n}), {args.steps} factorizations in {dt:.2f} s, scaled to the full workload by the "
-              f"GPU plan's flop ratio {ratio:.3e}")
-    line = {"impl": "reference", "metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps / 1.0,
+        p, done, wall, cores = cpu_oracle_run(per_step, first_shift=i)
+        done_all += done
+        wall_all += wall
+    value = done_all / wall_all * ratio
+    sample = cpu_sample_desc(p0, done_all, wall_all, cores, ratio, full.n)
+    line = {"impl": "reference", "metric": metric_for(args.workload), "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value if value > 0 else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "desc": WORKLOAD_DESC.get(args.workload)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _cpu_sample_pencil():
+    from gen import make_pair
+    s = CPU_SAMPLE
+    return make_pair(s["nx"], s["ny"], s["nz"], seed=0, vacancies=s["vacancies"])
 
 
 VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_min_front", "gershgorin_multisection8",
@@ -333,20 +389,23 @@ def measure_hermitian(torch):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kep", choices=["kep", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "million", "mid", "small"])
+    ap.add_argument("--workload", default="million", choices=["scale", "million", "mid", "small"])
+    ap.add_argument("--ordering", default="refined", choices=["refined", "default"],
+                    help="nested dissection of the timed analysis: refined (minimum-vertex-cover separators, "
+                         "less fill) or default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--refined-order", action="store_true",
-                    help="analyse with the refined nested dissection (minimum-vertex-cover separators)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="wall time of the cpu_baseline run")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end leg (at most --steps)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--kth", action="store_true",
-                    help="also run Algorithm 4 once (k = n/2) and report the time to lambda_k")
+    ap.add_argument("--no-kth", action="store_true", help="skip Algorithm 4 (time to lambda_k)")
+    ap.add_argument("--no-validate", action="store_true", help="skip the second-ordering count check")
     ap.add_argument("--variants", nargs="?", const="all", default=None,
                     help="also measure the next rows (all, or a comma list of: " + ", ".join(VARIANTS) + ")")
     ap.add_argument("--event-timing", type=int, default=1,
-                    help="bracket every launch with CUDA events for the per-kernel roofline (1) or not (0)")
+                    help="bracket the roofline kernels' launches with CUDA events (1) or not (0)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -362,9 +421,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
+    refined = args.ordering == "refined"
     p = make_workload(args.workload)
     t0 = time.perf_counter()
-    P = kep.Problem.from_pencil(p, refined_order=args.refined_order)
+    P = kep.Problem.from_pencil(p, refined_order=refined)
     t_analyze = time.perf_counter() - t0
     info = P.info
     stream = torch.cuda.Stream()
@@ -373,9 +433,10 @@ def main():
     gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
     b = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
     x = torch.empty_like(b)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
     # each rank factors its own shifts (round-robin over one sequence): independent units, no
-    # collective on the data path
-    shifts = multishift.shard(shifts_for(p.k, world * (args.warmup + 2 * args.steps + 8)), rank, world)
+    # collective on the data path; the sequence increases, so each rank's counts must not decrease
+    shifts = multishift.shard(shifts_for(p.k, world * (args.warmup + args.steps + e2e_steps + 2)), rank, world)
 
     nus = []
 
@@ -385,6 +446,7 @@ def main():
         P.solve(b, out=x)
         P.spmv(x)
 
+    warm = None
     for i in range(args.warmup):
         last = i == args.warmup - 1
         if last:                       # per-class breakdown from the last warm-up step
@@ -395,6 +457,8 @@ def main():
             warm = P.timing(reset=True)
             P.set_timing(False)
     torch.cuda.synchronize()
+    if warm is None:
+        warm = P.timing(reset=True)
     warm_classes = {k: v for k, v in warm.items() if k not in ("total_launches", "flops")}
     dom = max(warm_classes, key=lambda k: warm_classes[k][1])
 
@@ -426,6 +490,8 @@ def main():
         ms = float(t.item())
         dist.barrier()
     value = world * args.steps / (ms / 1e3)
+    timed_shifts = shifts[args.warmup:args.warmup + args.steps]
+    timed_nus = nus[args.warmup:args.warmup + args.steps]
 
     # end to end through the public API with host buffers: copies inside the timed region
     e2e = None
@@ -434,7 +500,7 @@ def main():
         xh = np.empty(n)
         torch.cuda.synchronize()
         e0 = time.perf_counter()
-        for i in range(args.steps):
+        for i in range(e2e_steps):
             P.factor(shifts[args.warmup + args.steps + i])
             P.solve(bh, out=xh)
             P.spmv(xh)
@@ -443,9 +509,10 @@ def main():
             t = torch.tensor([et], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             et = float(t.item())
-        e2e = {"value": world * args.steps / et, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * 8 * n,
-               "d2h_bytes_per_step": 3 * 8 * n + 32}
+        e2e = {"value": world * e2e_steps / et, "unit": UNIT, "steps": e2e_steps,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 3 * 8 * n + 32,
+               "path": "Problem.factor + Problem.solve (pageable host rhs in, x out) + Problem.spmv "
+                       "(host x in, A x and B x out) through the C ABI"}
 
     # roofline of the dominant kernel class (dominant in the last warm-up step; its launches in
     # the timed region are event-timed)
@@ -461,13 +528,19 @@ def main():
                                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
                                "launches": classes["update"][0], "kernel_ms": classes["update"][1]}
     if classes["flush_tc"][1] > 0 and fl["flush_tc"] > 0:
-        a = fl["flush_tc"] / (classes["flush_tc"][1] / 1e3)
+        sec = classes["flush_tc"][1] / 1e3
         pk, src = peaks["bf16_sustained"]
-        rooflines["flush_tc"] = {"bound": "tensor", "kernel": "lf_flush_tc_kernel (tcgen05 bf16, exact splitting)",
-                                 "achieved": a / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s", "frac": a / pk,
-                                 "peak_source": src, "launches": classes["flush_tc"][0],
-                                 "kernel_ms": classes["flush_tc"][1],
-                                 "fp64_equivalent_tflops": fl["flush_fp64_equivalent"] / (classes["flush_tc"][1] / 1e3) / 1e12}
+        method = fl["flush_fp64_equivalent"] / sec          # the FP64 update work carried out
+        issued = fl["flush_tc"] / sec                       # bf16 products issued (36 per FP64 FMA)
+        rooflines["flush_tc"] = {
+            "bound": "tensor", "kernel": "lf_flush_tc_kernel (tcgen05 bf16, exact splitting of FP64)",
+            "achieved": method / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s", "frac": method / pk,
+            "achieved_is": "the Schur-update flops of the method (2 per FP64 multiply-add) per second of the "
+                           "kernel's launches",
+            "peak_source": src + " (the kernel's own dtype)",
+            "issued_bf16_tflops": issued / 1e12, "frac_issued_bf16": issued / pk,
+            "fp64_fma_peak_ratio": method / FP64_PEAK_DERIVED,
+            "launches": classes["flush_tc"][0], "kernel_ms": classes["flush_tc"][1]}
     roofline = rooflines.get(dom)
     if roofline is not None:
         roofline = dict(roofline)
@@ -475,29 +548,48 @@ def main():
         roofline["share_of_step"] = roofline["kernel_ms"] / ms if ms > 0 else None
         roofline["class"] = dom
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ps, times = cpu_oracle_sample(reps=1)
-        ratio = flops_of(ps, args.refined_order) / info.flops_factor
-        cpu_val = (1.0 / min(times)) * ratio
-        cpu = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"oracle sparse LDL^T (c3, single thread) on the same generator at "
-                          f"{CPU_SAMPLE['nx']}x{CPU_SAMPLE['ny']}x{CPU_SAMPLE['nz']} cells (n={ps.n}): "
-                          f"{min(times):.2f} s per factorization, scaled to n={n} by the GPU plan's flop "
-                          f"ratio {ratio:.3e}")}
-
     kth = None
-    if args.kth and rank == 0:
+    if not args.no_kth and rank == 0:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lam, xk, rep = P.kth_eigenpair(p.k)
-        t_kth = time.perf_counter() - t0
-        P._last_x = xk
-        kth = {"time_to_lambda_k_s": t_kth, "k": p.k, "lambda_k": lam, "report": rep}
+        try:
+            lam, xk, rep = P.kth_eigenpair(p.k)
+            t_kth = time.perf_counter() - t0
+            P._last_x = xk
+            kth = {"time_to_lambda_k_s": t_kth, "k": p.k, "lambda_k": lam, "report": rep}
+        except Exception as exc:
+            kth = {"error": str(exc), "seconds": time.perf_counter() - t0}
 
     variants = None
     if args.variants and rank == 0:
         variants = measure_variants(P, p, torch, kth, args.variants)
+
+    # validation of the timed counts: nu is non-decreasing in sigma, and a second analysis with the
+    # other nested dissection (other fronts, pivots and update batches) gives the same count at the
+    # first and last timed shift (Sylvester's law)
+    validation = {"monotone": all(a <= b2 for a, b2 in zip(timed_nus, timed_nus[1:]))}
+    P.close()
+    if not args.no_validate:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        other = "default" if refined else "refined"
+        check = sorted({0, len(timed_shifts) - 1})
+        with kep.Problem.from_pencil(p, refined_order=not refined) as Q:
+            got = [Q.factor(timed_shifts[i]).neg for i in check]
+        want = [timed_nus[i] for i in check]
+        validation.update({"second_ordering": other, "shifts": [timed_shifts[i] for i in check],
+                           "nu_timed": want, "nu_second": got, "equal": got == want,
+                           "seconds": time.perf_counter() - t0})
+    validation["ok"] = validation["monotone"] and validation.get("equal", True)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ps = _cpu_sample_pencil()
+        ratio = flops_of(ps) / (info.flops_factor if not refined else flops_of(p))
+        ps, done, cwall, cores = cpu_oracle_run(args.cpu_seconds)
+        cpu_val = done / cwall * ratio
+        cpu = {"value": cpu_val, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": cpu_sample_desc(ps, done, cwall, cores, ratio, n)}
 
     if rank == 0:
         line = {"metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -511,11 +603,13 @@ def main():
                            "l2": "inputs larger than L2 (front storage %.1f GB)" % (info.front_bytes / 1e9),
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "analyze_s": t_analyze, "wall_s": wall,
-                           "ordering": "refined nested dissection" if args.refined_order else "nested dissection",
+                           "ordering": ("refined nested dissection (minimum-vertex-cover separators)" if refined
+                                        else "nested dissection"),
                            "event_timing": bool(args.event_timing),
-                           "nu": nus[args.warmup:args.warmup + args.steps]},
+                           "shifts": timed_shifts, "nu": timed_nus},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": timing["total_launches"],
                 "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu,
+                "nu_validation": validation,
                 "factorization_fp64_equivalent_tflops": info.flops_factor * args.steps / (ms / 1e3) / 1e12,
                 "kernels_ms_warmup_step": {k: v[1] for k, v in warm_classes.items()},
                 "kernels_ms_timed": {k: v[1] for k, v in classes.items() if v[1] > 0}}

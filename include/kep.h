@@ -92,10 +92,17 @@ typedef struct {
                                  KEP_SOLVE_F32_IR (KEP_SCHUR_FP32 factor, every solve refined in
                                  FP64 to a normwise backward error <= 1e-13; the inertia
                                  factorizations of stages 1-2 stay FP64-accurate) */
-  int32_t reserved;           /* 0 */
+  int32_t b_factor;           /* where B's factor (the B-solves of Algorithms 2 and 3) lives:
+                                 KEP_BFACTOR_AUTO (default) its own factor slot when a second
+                                 factor fits in free device memory, else shared;
+                                 KEP_BFACTOR_SHARED the slot of the A - sigma B factorizations,
+                                 B factored again whenever a B-solve finds it replaced (one extra
+                                 factorization per Algorithm 2 step; the largest problems);
+                                 KEP_BFACTOR_OWN its own slot always */
 } kep_params;
 
 enum { KEP_INIT_LANCZOS = 0, KEP_INIT_GERSHGORIN = 1 };
+enum { KEP_BFACTOR_AUTO = 0, KEP_BFACTOR_SHARED = 1, KEP_BFACTOR_OWN = 2 };
 enum { KEP_SOLVE_F64 = 0, KEP_SOLVE_F32_IR = 1 };
 
 /* Report of kep_kth_eigenpair. */
@@ -273,6 +280,27 @@ kep_status kep_spmv(kep_ctx* ctx, const double* x, double* ax, double* bx, int p
  */
 kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, double* lambda,
                              double* x, kep_report* report);
+
+/*
+ * kep_multisection_points - the shifts of one step of Algorithm 1' on [lo, hi) (host only, no
+ * device): nshift = 1 gives the midpoint (lo + hi) / 2 (the paper's bisection); nshift > 1 the
+ * points lo + (hi - lo) q / (nshift + 1), q = 1 .. nshift (multisection, the evaluations of one step
+ * being independent factorizations).  sigmas: nshift doubles, increasing.  Errors: KEP_ERR_INVALID
+ * for nshift < 1, lo >= hi or a null pointer.
+ */
+kep_status kep_multisection_points(double lo, double hi, int32_t nshift, double* sigmas);
+
+/*
+ * kep_multisection_update - the bracket update of one step of Algorithm 1' (host only): given the
+ * bracket [*lo, *hi) with *nu_lo < k <= *nu_hi (nu = the inertia count nu_sigma(A, B), Section 2.1)
+ * and the counts nus of the first `count` shifts of kep_multisection_points, in increasing order,
+ * keep the part [sigma_{q-1}, sigma_q) whose counts bracket k (k 1-based).  The counts may stop at
+ * the first one >= k.  Errors: KEP_ERR_INVALID when k is not bracketed, a shift lies outside the
+ * bracket or out of order, or the counts decrease with sigma (a non-monotone count means a wrong
+ * factorization); the bracket is then left unchanged.
+ */
+kep_status kep_multisection_update(int64_t k, int32_t count, const double* sigmas, const int64_t* nus,
+                                   double* lo, double* hi, int64_t* nu_lo, int64_t* nu_hi);
 
 /*
  * kep_set_values - new values of A and B on the pattern given to kep_analyze (same layout:

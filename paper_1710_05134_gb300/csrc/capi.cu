@@ -82,6 +82,13 @@ kep_status setup_memory(kep_ctx* c) {
   KEP_TRY(dev_alloc(c, &c->W.P21, std::max<int64_t>(P.max_large_rows, 1) * kPanel, true));
   KEP_TRY(dev_alloc(c, &c->d_vasm, P.vec_total, true));
   KEP_TRY(dev_alloc(c, &c->d_vfac, P.vec_total, true));
+  std::vector<int32_t> fbase;
+  const int64_t nflags = df_flag_bases(P, fbase);
+  KEP_TRY(dev_alloc(c, &c->d_df_flags, nflags, true));
+  if (cudaMemset(c->d_df_flags, 0, sizeof(int32_t) * std::max<int64_t>(nflags, 1)) != cudaSuccess) return KEP_ERR_CUDA;
+  const int32_t* fb = nullptr;
+  KEP_TRY(dev_upload_mem(c, &fb, fbase));
+  c->d_df_fbase = const_cast<int32_t*>(fb);
   return KEP_OK;
 }
 
@@ -93,7 +100,15 @@ void release_memory(kep_ctx* c) {
   c->emul_bytes = 0;
   c->d_emul_off = nullptr;
   c->emul_min_planned = -1;
-  for (int i = 0; i < 2; ++i) { c->slot_ready[i] = false; c->slot[i].valid = false; }
+  for (int i = 0; i < 2; ++i) {
+    c->slot_ready[i] = false;
+    c->slot[i].valid = false;
+    c->d_df_items[i] = nullptr;
+    c->df_items_cap[i] = 0;
+    c->df_version[i] = 0;
+  }
+  c->d_df_flags = nullptr;
+  c->d_df_fbase = nullptr;
 }
 
 // Delayed pivots overflowed a front's slack: grow the slack of every non-leaf front and rebuild
@@ -214,9 +229,13 @@ kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inert
   S.ca = ca; S.cb = cb;
   c->slot_status[slot] = bits;
   c->slot_nelim[slot].resize(c->plan.nfronts);
+  c->slot_din[slot].resize(c->plan.nfronts);
   if (cudaMemcpy(c->slot_nelim[slot].data(), S.nelim, sizeof(int32_t) * c->plan.nfronts,
+                 cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(c->slot_din[slot].data(), S.d_in, sizeof(int32_t) * c->plan.nfronts,
                  cudaMemcpyDeviceToHost) != cudaSuccess)
     return KEP_ERR_CUDA;
+  ++c->factor_version[slot];
   if (out) *out = in;
   if (bits & ST_POOL) return KEP_ERR_POOL;
   if (bits & ST_NONFINITE) return KEP_ERR_NONFINITE;
@@ -244,10 +263,40 @@ kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x) {
   L.xnew = c->d_xnew;
   L.partial = c->d_solve_partial;
   L.h_nelim = c->slot_nelim[slot].data();
+  if (c->df_version[slot] != c->factor_version[slot]) {
+    // work items of the dataflow solve for this factorization (its delays and pivot counts)
+    build_df_items(c->plan, c->slot_nelim[slot].data(), c->slot_din[slot].data(), c->df_items[slot],
+                   c->df_fwd_off[slot], c->df_bwd_off[slot], c->df_bwd_start[slot]);
+    const int64_t need = std::max<int64_t>(1, static_cast<int64_t>(c->df_items[slot].size()));
+    if (need > c->df_items_cap[slot]) {
+      int2* p = nullptr;
+      KEP_TRY(dev_alloc(c, &p, need + need / 4, true));
+      c->d_df_items[slot] = p;
+      c->df_items_cap[slot] = need + need / 4;
+    }
+    if (!c->df_items[slot].empty() &&
+        cudaMemcpyAsync(c->d_df_items[slot], c->df_items[slot].data(), sizeof(int2) * c->df_items[slot].size(),
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    c->df_version[slot] = c->factor_version[slot];
+  }
+  L.df_fwd_items = c->d_df_items[slot];
+  L.df_bwd_items = c->d_df_items[slot] + c->df_bwd_start[slot];
+  L.h_df_fwd_off = c->df_fwd_off[slot].data();
+  L.h_df_bwd_off = c->df_bwd_off[slot].data();
+  L.df_counters = c->d_df_ctr;
+  L.df_flags = c->d_df_flags;
+  L.df_fbase = c->d_df_fbase;
+  L.epoch = ++c->df_epoch;
   L.stream = c->stream;
   L.num_sms = c->num_sms;
   L.timer = &c->timer;
-  return run_solve(L, b, x);
+  KEP_TRY(run_solve(L, b, x));
+  // the dataflow kernels' bounded waits report through the first counter
+  if (cudaMemcpyAsync(c->h_df_err, c->d_df_ctr, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  return *c->h_df_err ? KEP_ERR_TIMEOUT : KEP_OK;
 }
 
 kep_status ctx_spmv_dev(kep_ctx* c, const double* x, double* ax, double* bx) {
@@ -270,7 +319,7 @@ void kep_default_params(kep_params* p) {
   p->init = KEP_INIT_LANCZOS;
   p->nshift = 1;
   p->solve_precision = KEP_SOLVE_F64;
-  p->reserved = 0;
+  p->b_factor = KEP_BFACTOR_AUTO;
 }
 
 const char* kep_status_str(kep_status s) {
@@ -455,12 +504,14 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   if (cudaMemset(c->d_flops, 0, sizeof(unsigned long long) * (KC_COUNT + 1)) != cudaSuccess) { kep_destroy(c); return KEP_ERR_CUDA; }
   AL(c->d_bnew, P.n); AL(c->d_xnew, P.n);
   AL(c->d_solve_partial, static_cast<size_t>(c->num_sms) * 4 * (kSolveBlk + 1));
+  AL(c->d_df_ctr, 1 + 2 * static_cast<size_t>(P.nlevels));
   AL(c->d_io0, P.n); AL(c->d_io1, P.n); AL(c->d_io2, P.n); AL(c->d_io3, P.n); AL(c->d_io4, P.n);
 #undef AL
   st = setup_memory(c);
   if (st != KEP_OK) { kep_destroy(c); return st; }
   if (cudaMallocHost(reinterpret_cast<void**>(&c->h_done), sizeof(int32_t) * ent) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(long long) * 8) != cudaSuccess) {
+      cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(long long) * 8) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&c->h_df_err), sizeof(int32_t)) != cudaSuccess) {
     kep_destroy(c);
     return KEP_ERR_NOMEM;
   }
@@ -827,6 +878,7 @@ void kep_destroy(kep_ctx* c) {
   for (void* p : c->mem_allocs) cudaFree(p);
   if (c->h_done) cudaFreeHost(c->h_done);
   if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->h_df_err) cudaFreeHost(c->h_df_err);
   c->driver_release();
   c->timer.release();
   delete c;

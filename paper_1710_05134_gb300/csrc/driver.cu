@@ -236,9 +236,30 @@ struct Run {
     return KEP_ERR_SINGULAR;
   }
 
+  // Slot of B's factor: slot 1 while a second factor fits on the device next to slot 0;
+  // otherwise B shares slot 0 with the factorizations of A - sigma B and is factored again
+  // whenever a B-solve finds slot 0 holding another matrix (at most once per Algorithm 2 step).
+  int bslot = 1;
+
+  kep_status choose_bslot(int32_t policy) {
+    if (policy == KEP_BFACTOR_SHARED) { bslot = 0; return KEP_OK; }
+    if (policy == KEP_BFACTOR_OWN || c->slot_ready[1]) { bslot = 1; return KEP_OK; }
+    size_t free_b = 0, total_b = 0;
+    CTRY(cudaMemGetInfo(&free_b, &total_b));
+    const double need = 8.0 * static_cast<double>(c->plan.front_total) +
+                        4.0 * 2.0 * static_cast<double>(c->plan.vec_total) + (2ll << 30);
+    bslot = static_cast<double>(free_b) > need ? 1 : 0;
+    return KEP_OK;
+  }
+
+  bool b_factored() const {
+    const FactorSlot& S = c->slot[bslot];
+    return c->slot_ready[bslot] && S.valid && S.ca == 0.0 && S.cb == 1.0;
+  }
+
   kep_status factor_B() {
     kep_inertia in{};
-    kep_status st = ctx_factor(c, 1, 0.0, 1.0, &in);
+    kep_status st = ctx_factor(c, bslot, 0.0, 1.0, &in);
     rep.n_factor++;
     if (st == KEP_ERR_SINGULAR) return KEP_ERR_NOT_SPD;
     if (st != KEP_OK) return st;
@@ -247,8 +268,8 @@ struct Run {
   }
 
   kep_status solve_B(const double* b, double* x) {
-    if (!c->slot[1].valid) DTRY(factor_B());   // a re-plan of the storage drops both factors
-    return ctx_solve_dev(c, 1, b, x);
+    if (!b_factored()) DTRY(factor_B());   // shared slot, or a re-plan of the storage dropped it
+    return ctx_solve_dev(c, bslot, b, x);
   }
 
   // B-normalize column j of V (given in V(:, j)), fill BV(:, j); returns the B-norm
@@ -296,6 +317,30 @@ struct Run {
 
 }  // namespace
 
+extern "C" kep_status kep_multisection_points(double lo, double hi, int32_t nshift, double* sigmas) {
+  if (!sigmas || nshift < 1 || !(lo < hi)) return KEP_ERR_INVALID;
+  if (nshift == 1) { sigmas[0] = 0.5 * (lo + hi); return KEP_OK; }
+  for (int32_t q = 1; q <= nshift; ++q) sigmas[q - 1] = lo + (hi - lo) * static_cast<double>(q) / (nshift + 1);
+  return KEP_OK;
+}
+
+extern "C" kep_status kep_multisection_update(int64_t k, int32_t count, const double* sigmas, const int64_t* nus,
+                                              double* lo, double* hi, int64_t* nu_lo, int64_t* nu_hi) {
+  if (!sigmas || !nus || !lo || !hi || !nu_lo || !nu_hi || count < 1) return KEP_ERR_INVALID;
+  if (!(*nu_lo < k && k <= *nu_hi)) return KEP_ERR_INVALID;
+  double plo = *lo, phi = *hi;
+  int64_t pnl = *nu_lo, pnh = *nu_hi;
+  for (int32_t q = 0; q < count; ++q) {
+    // counts must not decrease with sigma, and the shifts must lie inside the bracket, in order
+    const double s = sigmas[q];
+    if (!(s >= plo && s <= phi) || nus[q] < pnl || nus[q] > pnh) return KEP_ERR_INVALID;
+    if (k <= nus[q]) { phi = s; pnh = nus[q]; break; }
+    plo = s; pnl = nus[q];
+  }
+  *lo = plo; *hi = phi; *nu_lo = pnl; *nu_hi = pnh;
+  return KEP_OK;
+}
+
 extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params* params, double* lambda,
                                         double* x_out, kep_report* report) {
   if (!c || !lambda) return KEP_ERR_INVALID;
@@ -305,6 +350,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   kep_params prm;
   if (params) prm = *params; else kep_default_params(&prm);
   if (prm.m_max < 1 || prm.max_lanczos < 2 || prm.max_si < 1) return KEP_ERR_INVALID;
+  if (prm.b_factor < KEP_BFACTOR_AUTO || prm.b_factor > KEP_BFACTOR_OWN) return KEP_ERR_INVALID;
   const int64_t cap = std::min<int64_t>(n + 1, std::max(prm.max_lanczos, prm.max_si) + 2);
   Driver* d = static_cast<Driver*>(c->driver);
   if (!d || d->cap_cols < cap) {
@@ -366,6 +412,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     nh = n_eig;
   } else {
   // ---------------- stage 1: Algorithm 2 ----------------
+  DTRY(R.choose_bslot(prm.b_factor));
   DTRY(R.factor_B());
   CTRY(cudaMemcpyAsync(d->V, h_start.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
   DTRY(R.b_normalize(0, nrm));                        // v_1 := v_1 / ||v_1||_B
@@ -407,19 +454,18 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   // ---------------- stage 2: Algorithm 1' (bisection, or multisection with nshift points) ----------------
   t0 = clock_::now();
   const int32_t ns = std::max(1, prm.nshift);
+  std::vector<double> sig(ns);
+  std::vector<int64_t> nus(ns);
   while (nh - nl > prm.m_max) {
-    // points lo + (hi - lo) q / (ns + 1), q = 1..ns; keep the part [sigma_{q-1}, sigma_q) with
-    // nu(sigma_{q-1}) < k <= nu(sigma_q)
-    double plo = lo, phi = hi;
-    int64_t pnl = nl, pnh = nh;
-    for (int32_t q = 1; q <= ns; ++q) {
-      double s = ns == 1 ? 0.5 * (lo + hi) : lo + (hi - lo) * static_cast<double>(q) / (ns + 1);
-      int64_t nu = 0;
-      DTRY(R.nu_at(s, nu));
-      if (k <= nu) { phi = s; pnh = nu; break; }
-      plo = s; pnl = nu;
+    // the shifts in increasing order; once one of them reaches k the later ones are not needed
+    DTRY(kep_multisection_points(lo, hi, ns, sig.data()));
+    int32_t used = 0;
+    for (int32_t q = 0; q < ns; ++q) {
+      DTRY(R.nu_at(sig[q], nus[q]));
+      used = q + 1;
+      if (k <= nus[q]) break;
     }
-    lo = plo; hi = phi; nl = pnl; nh = pnh;
+    DTRY(kep_multisection_update(k, used, sig.data(), nus.data(), &lo, &hi, &nl, &nh));
     rep.n_bisect++;
     if (rep.n_bisect > 200) return KEP_ERR_CLUSTER;    // a multiple eigenvalue can stall the count
   }
@@ -431,6 +477,12 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   const int64_t l = k - nl, mm = nh - nl;
   double sigma = 0.5 * (lo + hi);
   const bool f32ir = prm.solve_precision == KEP_SOLVE_F32_IR;
+  // v_1 = B^{-1} v~_1, so that ||v_1||_B = ||v~_1||_{B^{-1}} (formed before the shifted factor,
+  // which may take B's slot)
+  if (prm.init == KEP_INIT_GERSHGORIN) DTRY(R.choose_bslot(prm.b_factor));
+  CTRY(cudaMemcpyAsync(d->u, h_start.data() + n, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  DTRY(R.solve_B(d->u, d->V));
+  DTRY(R.b_normalize(0, nrm));
   {
     int64_t nu_mid = 0;
     const int mode = c->schur_mode;
@@ -449,10 +501,6 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     rep.solve_berr = std::max(rep.solve_berr, be);
     return st;
   };
-  // v_1 = B^{-1} v~_1, so that ||v_1||_B = ||v~_1||_{B^{-1}}
-  CTRY(cudaMemcpyAsync(d->u, h_start.data() + n, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
-  DTRY(R.solve_B(d->u, d->V));
-  DTRY(R.b_normalize(0, nrm));
   alpha.clear(); beta.clear();
   std::vector<double> G;                              // 2-norm Gram matrix of [v_1 .. v_{j+1}]
   int64_t gcap = cap;

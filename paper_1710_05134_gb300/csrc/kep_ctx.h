@@ -67,6 +67,20 @@ struct kep_ctx {
   double* d_krylov = nullptr;       // refinement workspace (in allocs; allocated at first use)
   double* d_solve_partial = nullptr;
   std::vector<int32_t> slot_nelim[2];   // pivots eliminated per front, per slot (host copy)
+  std::vector<int32_t> slot_din[2];     // delayed columns received per front, per slot (host copy)
+  uint64_t factor_version[2] = {0, 0};  // bumped by every successful factorization of the slot
+  // dataflow solve: work items per slot (built from the slot's factorization), counters, flags
+  uint64_t df_version[2] = {0, 0};
+  std::vector<int2> df_items[2];
+  std::vector<int32_t> df_fwd_off[2], df_bwd_off[2];
+  int64_t df_bwd_start[2] = {0, 0};
+  int2* d_df_items[2] = {nullptr, nullptr};   // in mem_allocs
+  int64_t df_items_cap[2] = {0, 0};
+  int32_t* d_df_ctr = nullptr;          // 1 + 2 nlevels (in allocs)
+  int32_t* d_df_flags = nullptr;        // in mem_allocs
+  int32_t* d_df_fbase = nullptr;        // in mem_allocs
+  int32_t* h_df_err = nullptr;          // pinned
+  int32_t df_epoch = 0;
   kep::Timer timer;
   int schur_mode = KEP_SCHUR_EMULATED;
   int64_t emul_min_front = 512;

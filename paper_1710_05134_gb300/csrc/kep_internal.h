@@ -18,9 +18,9 @@ constexpr int kSmallMax = 128;      // fronts with m_alloc <= this are factored 
 constexpr int kPanel = 32;          // block width of the large-front pivoting panel
 constexpr int kWindow = 256;        // pivot window: the trailing matrix right of it is updated once
                                     //   per window with all of the window's pivots
-constexpr int kSolveBigM = 2048;    // fronts at least this large (and with kSolveBigP pivots) are
-constexpr int kSolveBigP = 128;     //   solved by the multi-block path
-constexpr int kSolveBlk = 64;       // pivot block of the multi-block solve
+constexpr int kSolveBigM = 512;     // fronts at least this large (and with kSolveBigP pivots) are
+constexpr int kSolveBigP = 32;      //   solved by the dataflow path
+constexpr int kSolveBlk = 64;       // row block of the dataflow solve
 constexpr double kBKAlpha = 0.6403882032022076;   // (1 + sqrt 17) / 8
 constexpr double kThresholdU = 0.01;               // threshold pivoting parameter u
 
@@ -257,6 +257,16 @@ struct SolveLaunch {
   double* xnew;
   double* partial;            // num_sms * 4 * (kSolveBlk + 1) doubles (shared by a level's fronts)
   const int32_t* h_nelim;     // pivots eliminated per front (host copy of the factor's counts)
+  // dataflow path (the leading level_nbig_solve[l] fronts of each level): work items of the
+  // factorization (device) at per-level offsets (host, nlevels + 1 each)
+  const int2* df_fwd_items;
+  const int2* df_bwd_items;
+  const int32_t* h_df_fwd_off;
+  const int32_t* h_df_bwd_off;
+  int32_t* df_counters;       // [0] wait error, [1, 1 + nlevels) forward, then backward counters
+  int32_t* df_flags;          // per possible pivot block of every front (at df_fbase[front])
+  const int32_t* df_fbase;
+  int32_t epoch;              // this solve's number (flags compare against 2 epoch + 1 / + 2)
   cudaStream_t stream;
   int num_sms;
   Timer* timer;
@@ -269,6 +279,9 @@ void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, 
                         cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops);
 int32_t emul_max_batch();
 kep_status run_solve(SolveLaunch& L, const double* b, double* x);
+void build_df_items(const Plan& P, const int32_t* nelim, const int32_t* din, std::vector<int2>& items,
+                    std::vector<int32_t>& fwd_off, std::vector<int32_t>& bwd_off, int64_t& bwd_start);
+int64_t df_flag_bases(const Plan& P, std::vector<int32_t>& fbase);
 kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
                     const double* x, double* ya, double* yb, cudaStream_t st, int num_sms,
                     Timer* timer);

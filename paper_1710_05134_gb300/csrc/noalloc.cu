@@ -13,6 +13,7 @@
 // streams) race; callers must serialise them.  The counters are zeroed by the kernel at the start
 // of every call; the matrix copy is fully overwritten before it is read.
 #include <cstdint>
+#include <mutex>
 
 #include "kep_internal.h"
 
@@ -147,9 +148,12 @@ __global__ void __launch_bounds__(kNoallocThreads) dense_bk_inertia_kernel(
   }
 }
 
+std::mutex g_setup_mutex;   // host threads making their first call on a device at the same time
+
 // Per-device lookup of the arrays' device addresses; the first call on a device does it.
 kep_status noalloc_setup(int dev, double** m, long long** c) {
   if (dev < 0 || dev >= kMaxDevices) return KEP_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (!g_matrix_addr[dev]) {
     void* pm = nullptr;
     void* pc = nullptr;

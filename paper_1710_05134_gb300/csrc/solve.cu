@@ -8,6 +8,14 @@
 // its contribution rows is passed to the parent.  Backward pass, root to leaves: each front
 // reads the solution on its contribution rows (written by its ancestors), applies D^{-1} and
 // L^{-T}, and writes its own variables.  No atomics: the result does not depend on scheduling.
+//
+// Fronts of order >= 512 (with at least 32 pivots) are solved by a dataflow kernel instead of one
+// CTA per front: their rows are cut into blocks of 64 (pivot blocks never split a 2x2 pair), every
+// block is a work item taken from a counter in dependency order, and an item waits only for the
+// pivot blocks it needs (forward: the earlier ones; backward: the later ones), which their CTAs
+// publish through per-block flags.  Many CTAs then stream one front's L at once, and the chain of
+// 64-row diagonal solves is the only serial part.  An item only waits for items taken before it,
+// so the waits cannot deadlock whatever the CTA scheduling; every wait is also bounded in time.
 #include <algorithm>
 
 #include "kep_device.cuh"
@@ -196,21 +204,310 @@ __global__ void __launch_bounds__(kSolveThreads) sv_bwd_kernel(FrontTables T, Fa
 }
 
 // ------------------------------------------------------------------------------------------
-// multi-block path for the largest fronts: the pivot range is cut into blocks of kSolveBlk
-// (boundaries moved by one where they would split a 2x2 pair); every block is one launch whose
-// CTAs all reproduce the small diagonal-block solve and then update their own rows.  All such
-// fronts of a level share the launches: grid.y = front (fronts[blockIdx.y]), grid.x = the CTAs of
-// one front.
+// dataflow path for the large fronts
 // ------------------------------------------------------------------------------------------
+constexpr int kDfThreads = 256;
+
+// first pivot of block b (blocks of kSolveBlk, a boundary moved by one where it would split a 2x2
+// pair)
 KEP_D int32_t blk_start(const int8_t* piv, int32_t b, int32_t nel) {
   if (b <= 0) return 0;
   int32_t s = b * kSolveBlk;
   if (s >= nel) return nel;
   return piv[s] == 0 ? s + 1 : s;
 }
+constexpr long long kDfWaitNs = 2000000000ll;   // a flag wait gives up after 2 s
+
+KEP_D long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+KEP_D int32_t ld_acquire(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+KEP_D void st_release(int32_t* p, int32_t v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until *flag == want; false when the time limit passed (err set) or another CTA
+// already gave up.
+KEP_D bool df_wait(const int32_t* flag, int32_t want, int32_t* err) {
+  if (ld_acquire(flag) == want) return true;
+  const long long t0 = global_ns();
+  unsigned ns = 32;
+  while (true) {
+    if (ld_acquire(flag) == want) return true;
+    if (ld_acquire(err) != 0) return false;
+    if (global_ns() - t0 > kDfWaitNs) { atomicExch(err, 1); return false; }
+    __nanosleep(ns);
+    if (ns < 256) ns *= 2;
+  }
+}
+
+struct DfArgs {
+  const int32_t* fronts;   // the level's dataflow fronts
+  const int2* items;       // (front position, round) in the order items are taken
+  int32_t nitems;
+  int32_t* counter;        // next item (zeroed before the solve)
+  int32_t* flags;          // per pivot block: the epoch value once its result is published
+  const int32_t* fbase;    // per front: its first flag
+  int32_t epoch;
+  int32_t* err;            // set when a wait gave up
+};
+
+// rows [r0, r1) of work item round r of front t: pivot block r (r < npb), else the r - npb-th
+// block of 64 contribution rows
+KEP_D void df_rows(const int8_t* piv, int32_t r, int32_t npb, int32_t nel, int32_t m, int32_t& r0, int32_t& r1) {
+  if (r < npb) { r0 = blk_start(piv, r, nel); r1 = blk_start(piv, r + 1, nel); }
+  else { r0 = nel + (r - npb) * kSolveBlk; r1 = min(m, r0 + kSolveBlk); }
+}
+
+// forward: y(block) = L11(block)^{-1} (f(block) - sum_{earlier blocks j} L(block, j) y(j)) for a
+// pivot block, f(rows) -= sum_j L(rows, j) y(j) for contribution rows; y is left in vfac
+__global__ void __launch_bounds__(kDfThreads) sv_df_fwd_kernel(FrontTables T, FactorSlot S, DfArgs A,
+                                                               double* vfac) {
+  __shared__ double ys[kSolveBlk + 1];
+  __shared__ double red[4][kSolveBlk + 1];
+  __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
+  __shared__ int8_t pb[kSolveBlk + 1];
+  __shared__ int32_t s_item, s_ok;
+  const int32_t tid = threadIdx.x, g = tid / kSolveBlk, rr = tid % kSolveBlk;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(A.counter, 1);
+    __syncthreads();
+    const int32_t it = s_item;
+    __syncthreads();
+    if (it >= A.nitems) return;
+    const int2 I = A.items[it];
+    const int32_t t = A.fronts[I.x];
+    const int32_t d_in = S.d_in[t];
+    const int32_t m = T.m_sym[t] + d_in;
+    const int32_t nel = S.nelim[t];
+    const int32_t npb = (nel + kSolveBlk - 1) / kSolveBlk;
+    const int8_t* piv = S.piv + T.piv_off[t];
+    const double* L = S.F + T.front_off[t];
+    const int64_t ld = T.m_alloc[t];
+    double* vf = vfac + T.vec_off[t];
+    int32_t* fl = A.flags + A.fbase[t];
+    int32_t r0, r1;
+    df_rows(piv, I.y, npb, nel, m, r0, r1);
+    const int32_t nr = r1 - r0;
+    const bool pivot = I.y < npb;
+    const int32_t ndep = pivot ? I.y : npb;
+    const int32_t i0 = r0 + rr;
+    const bool v0 = rr < nr, v1 = rr == 0 && nr > kSolveBlk;
+    double acc0 = 0.0, acc1 = 0.0;
+    bool ok = true;
+    for (int32_t j = 0; j < ndep && ok; ++j) {
+      const int32_t c0 = blk_start(piv, j, nel), c1 = blk_start(piv, j + 1, nel);
+      if (tid == 0) s_ok = df_wait(fl + j, A.epoch, A.err) ? 1 : 0;
+      __syncthreads();
+      ok = s_ok != 0;
+      if (ok && tid < c1 - c0) ys[tid] = __ldcg(vf + c0 + tid);
+      __syncthreads();
+      if (ok) {
+#pragma unroll 4
+        for (int32_t c = c0 + g; c < c1; c += 4) {
+          const double yc = ys[c - c0];
+          const double* col = L + static_cast<int64_t>(c) * ld + r0;
+          if (v0) acc0 = fma(__ldg(col + rr), yc, acc0);
+          if (v1) acc1 = fma(__ldg(col + kSolveBlk), yc, acc1);
+        }
+      }
+      __syncthreads();
+    }
+    if (!ok) return;
+    red[g][rr] = acc0;
+    if (rr == 0) red[g][kSolveBlk] = acc1;
+    __syncthreads();
+    if (!pivot) {
+      if (tid < nr) vf[r0 + tid] -= red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
+      __syncthreads();
+      continue;
+    }
+    for (int32_t e = tid; e < nr * nr; e += blockDim.x) {
+      const int32_t c = e / nr, a = e % nr;
+      if (a > c) Lb[c][a] = L[static_cast<int64_t>(r0 + c) * ld + r0 + a];
+    }
+    if (tid < nr) {
+      ys[tid] = vf[r0 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
+      pb[tid] = piv[r0 + tid];
+    }
+    __syncthreads();
+    if (tid < 32) {
+      for (int32_t c = 0; c < nr;) {
+        if (pb[c] == 2) {
+          const double y0 = ys[c], y1 = ys[c + 1];
+          for (int32_t a = c + 2 + tid; a < nr; a += 32) ys[a] -= Lb[c][a] * y0 + Lb[c + 1][a] * y1;
+          c += 2;
+        } else {
+          const double y0 = ys[c];
+          for (int32_t a = c + 1 + tid; a < nr; a += 32) ys[a] -= Lb[c][a] * y0;
+          c += 1;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (tid < nr) vf[r0 + tid] = ys[tid];
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(fl + I.y, A.epoch);
+    }
+  }
+}
+
+// backward preparation: the solution on the contribution rows (written by the ancestors)
+__global__ void sv_df_bwd_prep_kernel(FrontTables T, FactorSlot S, const int32_t* fronts, const double* xnew,
+                                      double* vfac) {
+  const int32_t t = fronts[blockIdx.y];
+  const int32_t m = T.m_sym[t] + S.d_in[t];
+  const int32_t nel = S.nelim[t];
+  double* vf = vfac + T.vec_off[t];
+  const int32_t* rv = S.rowvar + T.vec_off[t];
+  for (int32_t i = nel + blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    vf[i] = xnew[rv[i]];
+}
+
+// backward, pivot block b (taken from the last block down): x(block) = L11(block)^{-T}
+// (D^{-1} y(block) - sum_{rows a below the block} L(a, block) x(a)); contribution rows first (their
+// x is known), then the later pivot blocks as they are published
+__global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, FactorSlot S, DfArgs A,
+                                                               double* vfac, double* xnew) {
+  constexpr int kCols = (kSolveBlk + 1 + 7) / 8;
+  __shared__ double xs[kSolveBlk + 1];
+  __shared__ double part[kSolveBlk + 1];
+  __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
+  __shared__ int8_t pb[kSolveBlk + 1];
+  __shared__ int32_t s_item, s_ok;
+  const int32_t tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(A.counter, 1);
+    __syncthreads();
+    const int32_t it = s_item;
+    __syncthreads();
+    if (it >= A.nitems) return;
+    const int2 I = A.items[it];
+    const int32_t t = A.fronts[I.x];
+    const int32_t d_in = S.d_in[t];
+    const int32_t m = T.m_sym[t] + d_in;
+    const int32_t nel = S.nelim[t];
+    const int32_t npb = (nel + kSolveBlk - 1) / kSolveBlk;
+    const int32_t b = npb - 1 - I.y;
+    const int8_t* piv = S.piv + T.piv_off[t];
+    const double* L = S.F + T.front_off[t];
+    const int64_t ld = T.m_alloc[t];
+    double* vf = vfac + T.vec_off[t];
+    int32_t* fl = A.flags + A.fbase[t];
+    const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
+    const int32_t kb = k1 - k0;
+    double acc[kCols];
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) acc[j] = 0.0;
+    // contribution rows
+    for (int32_t a = nel + lane; a < m; a += 32) {
+      const double xa = __ldcg(vf + a);
+#pragma unroll
+      for (int j = 0; j < kCols; ++j) {
+        const int32_t c = warp + 8 * j;
+        if (c < kb) acc[j] = fma(__ldg(L + static_cast<int64_t>(k0 + c) * ld + a), xa, acc[j]);
+      }
+    }
+    // later pivot blocks, last first
+    bool ok = true;
+    for (int32_t bp = npb - 1; bp > b && ok; --bp) {
+      const int32_t s0 = blk_start(piv, bp, nel), s1 = blk_start(piv, bp + 1, nel);
+      if (tid == 0) s_ok = df_wait(fl + (npb - 1 - bp), A.epoch, A.err) ? 1 : 0;
+      __syncthreads();
+      ok = s_ok != 0;
+      if (ok && tid < s1 - s0) xs[tid] = __ldcg(vf + s0 + tid);
+      __syncthreads();
+      if (ok) {
+        for (int32_t a = s0 + lane; a < s1; a += 32) {
+          const double xa = xs[a - s0];
+#pragma unroll
+          for (int j = 0; j < kCols; ++j) {
+            const int32_t c = warp + 8 * j;
+            if (c < kb) acc[j] = fma(__ldg(L + static_cast<int64_t>(k0 + c) * ld + a), xa, acc[j]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!ok) return;
+#pragma unroll
+    for (int j = 0; j < kCols; ++j) {
+      const int32_t c = warp + 8 * j;
+      const double v = warp_sum(acc[j]);
+      if (lane == 0 && c < kb) part[c] = v;
+    }
+    for (int32_t e = tid; e < kb * kb; e += blockDim.x) {
+      const int32_t c = e / kb, a = e % kb;
+      if (a > c) Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
+    }
+    if (tid < kb) pb[tid] = piv[k0 + tid];
+    __syncthreads();
+    // z = D^{-1} y on the block's rows (a 2x2 pair never straddles blocks)
+    if (tid < kb) {
+      const int32_t c = k0 + tid;
+      const int64_t po = T.piv_off[t];
+      const double yc = vf[c];
+      double z;
+      if (pb[tid] == 1) {
+        z = yc / S.Dd[po + c];
+      } else if (pb[tid] == 2) {
+        const double a = S.Dd[po + c], cc = S.Dd[po + c + 1], bb = S.De[po + c];
+        z = (cc * yc - bb * vf[c + 1]) / (a * cc - bb * bb);
+      } else {
+        const double a = S.Dd[po + c - 1], cc = S.Dd[po + c], bb = S.De[po + c - 1];
+        z = (a * yc - bb * vf[c - 1]) / (a * cc - bb * bb);
+      }
+      xs[tid] = z;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      for (int32_t c = kb - 1; c >= 0;) {
+        if (pb[c] == 0) {                     // second of a pair at (c-1, c)
+          double s0 = 0.0, s1 = 0.0;
+          for (int32_t a = c + 1 + lane; a < kb; a += 32) {
+            s0 += Lb[c - 1][a] * xs[a];
+            s1 += Lb[c][a] * xs[a];
+          }
+          s0 = warp_sum(s0); s1 = warp_sum(s1);
+          if (lane == 0) {
+            xs[c] -= part[c] + s1;
+            xs[c - 1] -= part[c - 1] + s0;
+          }
+          c -= 2;
+        } else {
+          double s0 = 0.0;
+          for (int32_t a = c + 1 + lane; a < kb; a += 32) s0 += Lb[c][a] * xs[a];
+          s0 = warp_sum(s0);
+          if (lane == 0) xs[c] -= part[c] + s0;
+          c -= 1;
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (tid < kb) {
+      vf[k0 + tid] = xs[tid];
+      xnew[S.rowvar[T.vec_off[t] + k0 + tid]] = xs[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(fl + I.y, A.epoch);
+    }
+  }
+}
 
 // assembly of the front's right-hand side (children in order) and the pivot permutation
-__global__ void __launch_bounds__(1024) sv_big_prep_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
+__global__ void __launch_bounds__(1024) sv_df_prep_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
                                                            const double* bnew, double* vasm, double* vfac) {
   const int32_t t = fronts[blockIdx.x];
   const int32_t d_in = S.d_in[t];
@@ -237,195 +534,6 @@ __global__ void __launch_bounds__(1024) sv_big_prep_kernel(FrontTables T, Factor
   for (int32_t i = threadIdx.x; i < m; i += blockDim.x) vf[i] = va[ap[i]];
 }
 
-// forward block b: y(block) = L11^{-1} f(block) (every CTA), CTA 0 stores it in ysol; rows below
-// the block: f(a) -= L(a, block) y(block)
-__global__ void __launch_bounds__(256) sv_big_fwd_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
-                                                         int32_t b, double* vfac, double* ysol) {
-  __shared__ double y[kSolveBlk + 1];
-  __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
-  __shared__ int8_t pb[kSolveBlk + 1];
-  const int32_t t = fronts[blockIdx.y];
-  const int32_t d_in = S.d_in[t];
-  const int32_t m = T.m_sym[t] + d_in;
-  const int32_t nel = S.nelim[t];
-  const int8_t* piv = S.piv + T.piv_off[t];
-  const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
-  if (k0 >= k1) return;
-  const double* L = S.F + T.front_off[t];
-  const int64_t ld = T.m_alloc[t];
-  double* vf = vfac + T.vec_off[t];
-  double* ys = ysol + T.vec_off[t];
-  const int32_t kb = k1 - k0;
-  for (int32_t e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int32_t c = e / kb, a = e % kb;
-    Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
-  }
-  if (threadIdx.x < kb) { y[threadIdx.x] = vf[k0 + threadIdx.x]; pb[threadIdx.x] = piv[k0 + threadIdx.x]; }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int32_t c = 0; c < kb;) {
-      if (pb[c] == 2) {
-        const double y0 = y[c], y1 = y[c + 1];
-        for (int32_t a = c + 2 + lane; a < kb; a += 32) y[a] -= Lb[c][a] * y0 + Lb[c + 1][a] * y1;
-        c += 2;
-      } else {
-        const double y0 = y[c];
-        for (int32_t a = c + 1 + lane; a < kb; a += 32) y[a] -= Lb[c][a] * y0;
-        c += 1;
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x < kb) ys[k0 + threadIdx.x] = y[threadIdx.x];
-  for (int32_t a = k1 + blockIdx.x * blockDim.x + threadIdx.x; a < m; a += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int32_t c = 0; c < kb; ++c) s = fma(L[static_cast<int64_t>(k0 + c) * ld + a], y[c], s);
-    vf[a] -= s;
-  }
-}
-
-// backward preparation: solution on the contribution rows, z = D^{-1} y on the pivots
-__global__ void sv_big_bwd_prep_kernel(FrontTables T, FactorSlot S, const int32_t* fronts, const double* xnew,
-                                       const double* ysol, double* vfac) {
-  const int32_t t = fronts[blockIdx.y];
-  const int32_t d_in = S.d_in[t];
-  const int32_t m = T.m_sym[t] + d_in;
-  const int32_t nel = S.nelim[t];
-  double* vf = vfac + T.vec_off[t];
-  const double* ys = ysol + T.vec_off[t];
-  const int32_t* rv = S.rowvar + T.vec_off[t];
-  const int8_t* piv = S.piv + T.piv_off[t];
-  const double* Dd = S.Dd + T.piv_off[t];
-  const double* De = S.De + T.piv_off[t];
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    if (i >= nel) { vf[i] = xnew[rv[i]]; continue; }
-    if (piv[i] == 1) {
-      vf[i] = ys[i] / Dd[i];
-    } else if (piv[i] == 2) {
-      const double a = Dd[i], cc = Dd[i + 1], bb = De[i];
-      const double det = a * cc - bb * bb;
-      vf[i] = (cc * ys[i] - bb * ys[i + 1]) / det;
-    } else {
-      const double a = Dd[i - 1], cc = Dd[i], bb = De[i - 1];
-      const double det = a * cc - bb * bb;
-      vf[i] = (a * ys[i] - bb * ys[i - 1]) / det;
-    }
-  }
-}
-
-// backward block b, part 1: per-CTA partial sums s_c = sum_{a >= k1} L(a, k0 + c) x(a), stored
-// column-major (partial[c * gridDim.x + cta]); warp w owns columns w, w + 8, ..., its lanes stride
-// the CTA's rows
-__global__ void __launch_bounds__(256) sv_big_bwd_partial_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
-                                                                 int32_t step, const double* vfac, double* partial) {
-  constexpr int kCols = (kSolveBlk + 1 + 7) / 8;
-  const int32_t t = fronts[blockIdx.y];
-  const int32_t d_in = S.d_in[t];
-  const int32_t m = T.m_sym[t] + d_in;
-  const int32_t nel = S.nelim[t];
-  const int32_t b = (nel + kSolveBlk - 1) / kSolveBlk - 1 - step;   // blocks from the last one down
-  if (b < 0) return;
-  partial += static_cast<int64_t>(blockIdx.y) * (kSolveBlk + 1) * gridDim.x;
-  const int8_t* piv = S.piv + T.piv_off[t];
-  const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
-  const int32_t kb = k1 - k0;
-  const double* L = S.F + T.front_off[t];
-  const int64_t ld = T.m_alloc[t];
-  const double* vf = vfac + T.vec_off[t];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  double acc[kCols];
-#pragma unroll
-  for (int j = 0; j < kCols; ++j) acc[j] = 0.0;
-  for (int32_t a = k1 + blockIdx.x * 32 + lane; a < m; a += gridDim.x * 32) {
-    const double xa = vf[a];
-#pragma unroll
-    for (int j = 0; j < kCols; ++j) {
-      const int32_t c = warp + 8 * j;
-      if (c < kb) acc[j] = fma(L[static_cast<int64_t>(k0 + c) * ld + a], xa, acc[j]);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kCols; ++j) {
-    const int32_t c = warp + 8 * j;
-    const double v = warp_sum(acc[j]);
-    if (lane == 0 && c < kb) partial[static_cast<int64_t>(c) * gridDim.x + blockIdx.x] = v;
-  }
-}
-
-// backward block b, part 2 (one CTA): add the partials, solve the block's unit upper triangle
-__global__ void __launch_bounds__(128) sv_big_bwd_block_kernel(FrontTables T, FactorSlot S, const int32_t* fronts,
-                                                               int32_t step, int32_t nparts, const double* partial,
-                                                               double* vfac) {
-  __shared__ double part[kSolveBlk + 1];
-  __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
-  __shared__ double xb[kSolveBlk + 1];
-  __shared__ int8_t pb[kSolveBlk + 1];
-  const int32_t t = fronts[blockIdx.x];
-  const int32_t nel = S.nelim[t];
-  const int32_t b = (nel + kSolveBlk - 1) / kSolveBlk - 1 - step;
-  if (b < 0) return;
-  partial += static_cast<int64_t>(blockIdx.x) * (kSolveBlk + 1) * nparts;
-  const int8_t* piv = S.piv + T.piv_off[t];
-  const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
-  const int32_t kb = k1 - k0;
-  const double* L = S.F + T.front_off[t];
-  const int64_t ld = T.m_alloc[t];
-  double* vf = vfac + T.vec_off[t];
-  for (int32_t e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-    const int32_t c = e / kb, a = e % kb;
-    Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
-  }
-  {  // column sums of the partials: warp w takes columns w, w + 4, ..., its lanes the CTAs
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int32_t c = warp; c < kb; c += blockDim.x / 32) {
-      double s = 0.0;
-      for (int32_t q = lane; q < nparts; q += 32) s += partial[static_cast<int64_t>(c) * nparts + q];
-      s = warp_sum(s);
-      if (lane == 0) part[c] = s;
-    }
-  }
-  if (threadIdx.x < kb) {
-    xb[threadIdx.x] = vf[k0 + threadIdx.x];
-    pb[threadIdx.x] = piv[k0 + threadIdx.x];
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int32_t c = kb - 1; c >= 0;) {
-      if (pb[c] == 0) {
-        double s0 = 0.0, s1 = 0.0;
-        for (int32_t a = c + 1 + lane; a < kb; a += 32) {
-          s0 += Lb[c - 1][a] * xb[a];
-          s1 += Lb[c][a] * xb[a];
-        }
-        s0 = warp_sum(s0); s1 = warp_sum(s1);
-        if (lane == 0) { xb[c] -= part[c] + s1; xb[c - 1] -= part[c - 1] + s0; }
-        c -= 2;
-      } else {
-        double s0 = 0.0;
-        for (int32_t a = c + 1 + lane; a < kb; a += 32) s0 += Lb[c][a] * xb[a];
-        s0 = warp_sum(s0);
-        if (lane == 0) xb[c] -= part[c] + s0;
-        c -= 1;
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < kb) vf[k0 + threadIdx.x] = xb[threadIdx.x];
-}
-
-__global__ void sv_big_scatter_kernel(FrontTables T, FactorSlot S, const int32_t* fronts, const double* vfac,
-                                      double* xnew) {
-  const int32_t t = fronts[blockIdx.y];
-  const int32_t nel = S.nelim[t];
-  const double* vf = vfac + T.vec_off[t];
-  const int32_t* rv = S.rowvar + T.vec_off[t];
-  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nel; c += gridDim.x * blockDim.x) xnew[rv[c]] = vf[c];
-}
-
 __global__ void gather_perm_kernel(int64_t n, const int32_t* perm, const double* src, double* dst) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -447,29 +555,31 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   const Plan& P = *L.plan;
   cudaStream_t st = L.stream;
   const int g = L.num_sms * 4;
+  if (cudaMemsetAsync(L.df_counters, 0, sizeof(int32_t) * (1 + 2 * static_cast<size_t>(P.nlevels)), st) != cudaSuccess)
+    return KEP_ERR_CUDA;
   KEP_LAUNCH(L.timer, KC_PERM, st, gather_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, b, L.bnew));
-  // the level's multi-block fronts: their block count and CTAs per front (a uniform grid)
-  auto big_shape = [&](int32_t lb, int32_t nbig, int32_t& maxblk, int& gx) {
-    int64_t rows = 0;
-    maxblk = 0;
-    for (int32_t i = 0; i < nbig; ++i) {
-      const int32_t t = P.level_fronts[lb + i];
-      rows = std::max<int64_t>(rows, P.m_alloc[t]);
-      maxblk = std::max(maxblk, (L.h_nelim[t] + kSolveBlk - 1) / kSolveBlk);
-    }
-    gx = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256 + 1, g / std::max(1, nbig))));
+  auto df_args = [&](int32_t l, bool fwd) {
+    DfArgs A;
+    A.fronts = L.d_level_fronts + P.level_ptr[l];
+    const int32_t* off = fwd ? L.h_df_fwd_off : L.h_df_bwd_off;
+    A.items = (fwd ? L.df_fwd_items : L.df_bwd_items) + off[l];
+    A.nitems = off[l + 1] - off[l];
+    A.counter = L.df_counters + 1 + (fwd ? 0 : P.nlevels) + l;
+    A.flags = L.df_flags;
+    A.fbase = L.df_fbase;
+    A.epoch = fwd ? 2 * L.epoch + 1 : 2 * L.epoch + 2;
+    A.err = L.df_counters;
+    return A;
   };
   for (int32_t l = 0; l < P.nlevels; ++l) {
     const int32_t lb = P.level_ptr[l], w = P.level_ptr[l + 1] - lb, nbig = P.level_nbig_solve[l];
     if (nbig > 0) {
-      int32_t maxblk;
-      int gx;
-      big_shape(lb, nbig, maxblk, gx);
       const int32_t* fr = L.d_level_fronts + lb;
-      KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st, sv_big_prep_kernel<<<nbig, 1024, 0, st>>>(L.T, L.S, fr, L.bnew, L.vasm, L.vfac));
-      for (int32_t bb = 0; bb < maxblk; ++bb)
+      KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st, sv_df_prep_kernel<<<nbig, 1024, 0, st>>>(L.T, L.S, fr, L.bnew, L.vasm, L.vfac));
+      const DfArgs A = df_args(l, true);
+      if (A.nitems > 0)
         KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st,
-                   sv_big_fwd_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, bb, L.vfac, L.vasm));
+                   sv_df_fwd_kernel<<<std::min(A.nitems, g), kDfThreads, 0, st>>>(L.T, L.S, A, L.vfac));
     }
     if (w > nbig)
       KEP_LAUNCH(L.timer, KC_SOLVE_FWD, st,
@@ -479,20 +589,13 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   for (int32_t l = P.nlevels - 1; l >= 0; --l) {
     const int32_t lb = P.level_ptr[l], w = P.level_ptr[l + 1] - lb, nbig = P.level_nbig_solve[l];
     if (nbig > 0) {
-      int32_t maxblk;
-      int gx;
-      big_shape(lb, nbig, maxblk, gx);
       const int32_t* fr = L.d_level_fronts + lb;
       KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
-                 sv_big_bwd_prep_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, L.xnew, L.vasm, L.vfac));
-      for (int32_t step = 0; step < maxblk; ++step) {
+                 sv_df_bwd_prep_kernel<<<dim3(8, nbig), 256, 0, st>>>(L.T, L.S, fr, L.xnew, L.vfac));
+      const DfArgs A = df_args(l, false);
+      if (A.nitems > 0)
         KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
-                   sv_big_bwd_partial_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, step, L.vfac, L.partial));
-        KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
-                   sv_big_bwd_block_kernel<<<nbig, 128, 0, st>>>(L.T, L.S, fr, step, gx, L.partial, L.vfac));
-      }
-      KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
-                 sv_big_scatter_kernel<<<dim3(gx, nbig), 256, 0, st>>>(L.T, L.S, fr, L.vfac, L.xnew));
+                   sv_df_bwd_kernel<<<std::min(A.nitems, g), kDfThreads, 0, st>>>(L.T, L.S, A, L.vfac, L.xnew));
     }
     if (w > nbig)
       KEP_LAUNCH(L.timer, KC_SOLVE_BWD, st,
@@ -501,6 +604,50 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   }
   KEP_LAUNCH(L.timer, KC_PERM, st, scatter_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, L.xnew, x));
   return cudaGetLastError() == cudaSuccess ? KEP_OK : KEP_ERR_CUDA;
+}
+
+// Work items of the dataflow solve for one factorization: per level, the leading
+// level_nbig_solve[l] fronts; forward rounds r = 0, 1, ... take pivot block r (then contribution
+// block r - npb) of every front that has one, backward rounds the pivot blocks from the last.
+void build_df_items(const Plan& P, const int32_t* nelim, const int32_t* din, std::vector<int2>& items,
+                    std::vector<int32_t>& fwd_off, std::vector<int32_t>& bwd_off, int64_t& bwd_start) {
+  items.clear();
+  fwd_off.assign(P.nlevels + 1, 0);
+  bwd_off.assign(P.nlevels + 1, 0);
+  std::vector<int32_t> npb, nall;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t base = static_cast<int64_t>(items.size());
+    if (pass == 1) bwd_start = base;
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+      (pass == 0 ? fwd_off : bwd_off)[l] = static_cast<int32_t>(items.size() - base);
+      const int32_t lb = P.level_ptr[l], nbig = P.level_nbig_solve[l];
+      npb.assign(nbig, 0);
+      nall.assign(nbig, 0);
+      int32_t rounds = 0;
+      for (int32_t q = 0; q < nbig; ++q) {
+        const int32_t t = P.level_fronts[lb + q];
+        const int32_t nel = nelim[t], m = P.m_sym[t] + din[t];
+        npb[q] = (nel + kSolveBlk - 1) / kSolveBlk;
+        nall[q] = pass == 0 ? npb[q] + (m - nel + kSolveBlk - 1) / kSolveBlk : npb[q];
+        rounds = std::max(rounds, nall[q]);
+      }
+      for (int32_t r = 0; r < rounds; ++r)
+        for (int32_t q = 0; q < nbig; ++q)
+          if (r < nall[q]) items.push_back(make_int2(q, r));
+    }
+    (pass == 0 ? fwd_off : bwd_off)[P.nlevels] = static_cast<int32_t>(items.size() - base);
+  }
+}
+
+// Flag offsets of the dataflow solve: per front, one flag per possible pivot block.
+int64_t df_flag_bases(const Plan& P, std::vector<int32_t>& fbase) {
+  fbase.assign(P.nfronts, 0);
+  int64_t tot = 0;
+  for (int32_t t = 0; t < P.nfronts; ++t) {
+    fbase[t] = static_cast<int32_t>(tot);
+    tot += (P.p_alloc[t] + kSolveBlk - 1) / kSolveBlk + 1;
+  }
+  return tot;
 }
 
 }  // namespace kep

@@ -25,10 +25,12 @@ EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_g
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
             "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi", "kep_solve_refined",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
+            "kep_multisection_points", "kep_multisection_update",
             "kep_set_schur_mode"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
 KEP_INIT_LANCZOS, KEP_INIT_GERSHGORIN = 0, 1
 KEP_SOLVE_F64, KEP_SOLVE_F32_IR = 0, 1
+KEP_BFACTOR_AUTO, KEP_BFACTOR_SHARED, KEP_BFACTOR_OWN = 0, 1, 2
 KEP_SCHUR_FP32 = 2
 KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
                   "perm", "spmv", "vec", "slice", "flush_tc"]
@@ -60,7 +62,7 @@ class Params(ctypes.Structure):
                 ("max_lanczos", ctypes.c_int64), ("max_si", ctypes.c_int64),
                 ("start_vectors", ctypes.c_void_p), ("seed", ctypes.c_uint64),
                 ("init", ctypes.c_int32), ("nshift", ctypes.c_int32),
-                ("solve_precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("solve_precision", ctypes.c_int32), ("b_factor", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -94,7 +96,7 @@ def lib() -> ctypes.CDLL:
     """Load (building if needed) libkep.so; raises if it cannot be built or loaded."""
     global _LIB
     if _LIB is None:
-        path = _build.LIB if os.path.exists(_build.LIB) else _build.build()
+        path = _build.build()        # rebuilds when a source is newer than the library
         L = ctypes.CDLL(path)
         P, I64, D, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         L.kep_default_params.argtypes = [ctypes.POINTER(Params)]
@@ -118,6 +120,10 @@ def lib() -> ctypes.CDLL:
         L.kep_solve_refined.argtypes = [P, P, P, I, D, ctypes.c_int32, P, P]
         L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
         L.kep_dense_inertia_noalloc.argtypes = [I64, P, P, I64, D, P, P]
+        L.kep_multisection_points.argtypes = [D, D, ctypes.c_int32, P]
+        L.kep_multisection_points.restype = I
+        L.kep_multisection_update.argtypes = [I64, ctypes.c_int32, P, P, P, P, P, P]
+        L.kep_multisection_update.restype = I
         L.kep_dense_inertia_noalloc.restype = I
         L.kep_set_schur_mode.argtypes = [P, I, I64]
         L.kep_set_schur_mode.restype = I
@@ -132,6 +138,26 @@ def lib() -> ctypes.CDLL:
             getattr(L, name).restype = I
         _LIB = L
     return _LIB
+
+
+def multisection_points(lo: float, hi: float, nshift: int) -> list[float]:
+    """The shifts of one Algorithm 1' step on [lo, hi) (kep_multisection_points; host only)."""
+    out = (ctypes.c_double * max(1, int(nshift)))()
+    _check(lib().kep_multisection_points(float(lo), float(hi), int(nshift), out), "kep_multisection_points")
+    return [float(v) for v in out[:int(nshift)]]
+
+
+def multisection_update(k: int, sigmas, nus, lo: float, hi: float, nu_lo: int, nu_hi: int):
+    """The bracket update of one Algorithm 1' step (kep_multisection_update; host only):
+    returns (lo, hi, nu_lo, nu_hi)."""
+    cnt = len(sigmas)
+    s = (ctypes.c_double * max(1, cnt))(*[float(v) for v in sigmas])
+    v = (ctypes.c_int64 * max(1, cnt))(*[int(x) for x in nus])
+    lo_, hi_ = ctypes.c_double(lo), ctypes.c_double(hi)
+    nl_, nh_ = ctypes.c_int64(nu_lo), ctypes.c_int64(nu_hi)
+    _check(lib().kep_multisection_update(int(k), cnt, s, v, ctypes.byref(lo_), ctypes.byref(hi_), ctypes.byref(nl_),
+                                         ctypes.byref(nh_)), "kep_multisection_update")
+    return lo_.value, hi_.value, nl_.value, nh_.value
 
 
 def symbolic_info(n, rowptr, colind, coords=None, *, lower: bool = False, graph_order: bool = False,
@@ -375,10 +401,10 @@ class Problem:
     def kth_eigenpair(self, k: int, *, m_max: int = 20, tau_res: float = 1e-10, tau_diff: float = 1e-10,
                       max_lanczos: int = 200, max_si: int = 300, start_vectors=None, seed: int = 0x5eed,
                       want_vector: bool = True, init: str = "lanczos", nshift: int = 1,
-                      solve_precision: str = "f64"):
+                      solve_precision: str = "f64", b_factor: str = "auto"):
         """Algorithm 4: (lambda_k, x_k (B-normalized), report dict).  init: "lanczos" (Algorithm 2)
         or "gershgorin" (an interval holding the whole spectrum); nshift: shifts per Algorithm 1'
-        step (1 = bisection)."""
+        step (1 = bisection); b_factor: "auto", "shared" or "own" (where B's factor lives)."""
         prm = Params()
         lib().kep_default_params(ctypes.byref(prm))
         prm.m_max, prm.tau_res, prm.tau_diff = int(m_max), float(tau_res), float(tau_diff)
@@ -386,6 +412,7 @@ class Problem:
         prm.init = {"lanczos": KEP_INIT_LANCZOS, "gershgorin": KEP_INIT_GERSHGORIN}[init]
         prm.nshift = int(nshift)
         prm.solve_precision = {"f64": KEP_SOLVE_F64, "f32_ir": KEP_SOLVE_F32_IR}[solve_precision]
+        prm.b_factor = {"auto": KEP_BFACTOR_AUTO, "shared": KEP_BFACTOR_SHARED, "own": KEP_BFACTOR_OWN}[b_factor]
         sv = None
         if start_vectors is not None:
             sv = np.ascontiguousarray(start_vectors, dtype=np.float64).reshape(-1)

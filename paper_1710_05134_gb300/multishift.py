@@ -6,6 +6,10 @@ across ranks round-robin; the only exchange is an all-gather of one int64 count 
 which every rank holds the same counts and takes the same sub-interval, so the ranks stay in step
 without any other communication.
 
+The shifts of a step and the bracket update are the library's (kep_multisection_points and
+kep_multisection_update, the same code Algorithm 4 runs); this module only shards the shifts and
+gathers the counts.
+
 ``count`` is any callable sigma -> nu (on a GPU: ``lambda s: problem.factor(s).neg``).  ``dist``
 is ``torch.distributed`` (initialised) or None for a single process."""
 from __future__ import annotations
@@ -62,22 +66,16 @@ def multisection_step(count, k: int, br: Bracket, nshift: int, rank: int = 0, wo
     of shifts -> their counts, e.g. ConcurrentCounter.count_many) replaces one-at-a-time count."""
     if nshift < 1:
         raise ValueError("nshift >= 1")
-    lo, hi = br.lower, br.upper
-    # nshift = 1: the midpoint, as Algorithm 1' bisects
-    sig = [0.5 * (lo + hi)] if nshift == 1 else [lo + (hi - lo) * q / (nshift + 1) for q in range(1, nshift + 1)]
+    from . import kep
+    sig = kep.multisection_points(br.lower, br.upper, nshift)      # the library's Algorithm 1' step
     mine = shard(range(nshift), rank, world)
     local = count_many([sig[q] for q in mine]) if count_many else [int(count(sig[q])) for q in mine]
     nus = gather_counts([int(v) for v in local], nshift, rank, world, dist)
-    for a, b in zip(nus, nus[1:]):
-        if b < a:
-            raise RuntimeError("inertia counts are not monotone in sigma")
-    plo, pnl, phi, pnu = lo, br.nu_lower, hi, br.nu_upper
-    for s, nu in zip(sig, nus):
-        if k <= nu:
-            phi, pnu = s, nu
-            break
-        plo, pnl = s, nu
-    return Bracket(plo, phi, pnl, pnu, br.history + list(zip(sig, nus)))
+    try:
+        lo, hi, nl, nh = kep.multisection_update(k, sig, nus, br.lower, br.upper, br.nu_lower, br.nu_upper)
+    except kep.KepError as exc:
+        raise RuntimeError("inertia counts are not monotone in sigma (or do not bracket k)") from exc
+    return Bracket(lo, hi, nl, nh, br.history + list(zip(sig, nus)))
 
 
 def multisection(count, k: int, br: Bracket, m_max: int = 20, nshift: int = 8, rank: int = 0,

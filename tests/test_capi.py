@@ -2,6 +2,8 @@
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -137,3 +139,27 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "small",
                         "--gpus", "2"], capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_multisection_step_through_the_abi():
+    """kep_multisection_points / kep_multisection_update (host only): the points of one
+    Algorithm 1' step and the bracket update, checked against the definition (Section 2.1: keep the
+    part whose counts bracket k) on a known count function; decreasing counts are refused."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import paper_1710_05134_gb300 as k
+    assert k.multisection_points(1.0, 3.0, 1) == [2.0]
+    pts = k.multisection_points(0.0, 9.0, 8)
+    assert pts == [float(q) for q in range(1, 9)]
+    eig = np.array([0.5, 1.5, 2.5, 2.6, 4.5, 7.2, 8.9])          # nu(s) = #eig < s
+    nu = [int((eig < s).sum()) for s in pts]
+    for kk in range(1, 8):
+        lo, hi, nl, nh = k.multisection_update(kk, pts, nu, 0.0, 9.0, 0, 7)
+        assert nl < kk <= nh and nl == int((eig < lo).sum()) and nh == int((eig < hi).sum())
+        assert hi - lo == 1.0 and lo <= eig[kk - 1] < hi
+    # counts may stop at the first one reaching k
+    assert k.multisection_update(3, pts[:3], nu[:3], 0.0, 9.0, 0, 7) == (2.0, 3.0, 2, 4)
+    with pytest.raises(k.KepError):
+        k.multisection_update(3, pts, [0, 2, 1, 4, 5, 5, 5, 6], 0.0, 9.0, 0, 7)   # not monotone
+    with pytest.raises(k.KepError):
+        k.multisection_update(9, pts, nu, 0.0, 9.0, 0, 7)                        # k not bracketed

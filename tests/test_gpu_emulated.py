@@ -106,3 +106,40 @@ def test_emulated_matches_fp64_factor(kep):
     xe = P.solve(b)
     assert (r64.neg, r64.zero, r64.pos) == (re.neg, re.zero, re.pos)
     assert np.abs(xe - x64).max() <= 1e-10 * np.abs(x64).max()
+
+
+def test_emulated_near_eigenvalue_shifts(kep, small):
+    """Shifts 2e-8 ||A|| from an eigenvalue (the Schur complements cancel down to the size of the
+    nearest eigenvalue's gap): the tensor-core update must still give the exact count, on the
+    oracle's dense spectrum (n = 2,048, fronts from order 256 on the tensor cores) and on the
+    closed-form diamond spectrum (n = 16,384)."""
+    p, A, B, lam = small
+    nrm = np.abs(A).sum(1).max()
+    P = kep.Problem.from_pencil(p)
+    P.set_schur_mode(True, min_front=256)
+    idx = np.random.default_rng(8).choice(np.arange(1, p.n - 1), 16, replace=False)
+    tried = 0
+    for i in idx:
+        for sgn in (1.0, -1.0):
+            s = lam[i] + sgn * 2e-8 * nrm
+            if np.abs(lam - s).min() < 1e-8 * nrm:
+                continue
+            r = P.factor(s)
+            ref = core.count_below(lam, s)
+            assert (r.neg, r.zero, r.pos) == (ref, 0, p.n - ref), (i, sgn)
+            tried += 1
+    assert tried >= 16
+    q = perfect_diamond_pencil(8, 8, 8)
+    cf = core.diamond_bloch_eigs(8, 8, 8, 1.0, 0.02)
+    nq = float(abs(q.A()).sum(1).max())
+    lv = np.unique(np.round(cf / (1e-10 * nq))) * 1e-10 * nq
+    gaps = np.diff(lv)
+    ok = np.where((gaps[:-1] > 1e-7 * nq) & (gaps[1:] > 1e-7 * nq))[0] + 1
+    Q = kep.Problem.from_pencil(q)
+    Q.set_schur_mode(True, min_front=256)
+    assert Q.info.max_front >= 256
+    for i in np.random.default_rng(9).choice(ok, 6, replace=False):
+        for sgn in (1.0, -1.0):
+            s = lv[i] + sgn * 2e-8 * nq
+            assert np.abs(cf - s).min() > 1e-8 * nq
+            assert Q.factor(s).neg == core.count_below(cf, s), (i, sgn)

@@ -204,7 +204,8 @@ def test_timing_counters(kep, small):
 
 
 def test_solve_multiblock_fronts_vs_sparse_lu(kep):
-    """Fronts of order >= 2048 take the multi-block solve; compare with the oracle's sparse LU."""
+    """Fronts of order >= 512 take the dataflow solve (many CTAs per front, 64-row blocks, flags);
+    compare with the oracle's sparse LU."""
     p = make_pair(8, 8, 8, seed=3)            # n = 16384, largest front > 2048
     P = kep.Problem.from_pencil(p)
     assert P.info.max_front >= 2048
@@ -219,3 +220,30 @@ def test_solve_multiblock_fronts_vs_sparse_lu(kep):
     assert np.abs(x - xr).max() <= 1e-9 * np.abs(xr).max()
     M = (p.A() - s * p.B()).tocsr()
     assert np.linalg.norm(M @ x - b) <= 1e-13 * abs(M).sum(1).max() * np.linalg.norm(x)
+
+
+def test_solve_two_by_two_pivots_and_delays_dataflow(kep):
+    """A zero diagonal in A - sigma B forces 2x2 pivots and delayed columns inside fronts large
+    enough for the dataflow solve (block boundaries moved around 2x2 pairs); the solve must match
+    the oracle's dense solve, for several right-hand sides in a row."""
+    import scipy.sparse as sp
+    p = make_pair(4, 4, 4, seed=6)            # n = 2048
+    sigma = 0.3
+    a = p.a.copy()
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    d = rows == p.colind
+    a[d] = sigma * p.b[d]
+    A = sp.csr_matrix((a, p.colind, p.rowptr), shape=(p.n, p.n)).toarray()
+    B = p.B().toarray()
+    M = A - sigma * B
+    P = kep.Problem(p.n, p.rowptr, p.colind, a, p.b, p.coords)
+    assert P.info.max_front >= 512
+    r = P.factor(sigma)
+    assert (r.neg, r.zero, r.pos) == core.dense_inertia(M)
+    rng = np.random.default_rng(11)
+    for _ in range(3):
+        b = rng.normal(size=p.n)
+        x = P.solve(b)
+        xr = np.linalg.solve(M, b)
+        assert np.abs(x - xr).max() <= 1e-8 * np.abs(xr).max()
+        assert np.linalg.norm(M @ x - b) <= 1e-12 * np.linalg.norm(M, np.inf) * np.linalg.norm(x)

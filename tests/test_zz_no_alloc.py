@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from gen import make_pair
+from oracle import core
 from tests.gpu_util import require_gpu
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +42,28 @@ def test_noalloc_matches_factor_two_calls():
         assert code == kep.KEP_OK
         r = P.factor(sigma)
         assert got == (r.neg, r.zero, r.pos)
+        assert got == core.dense_inertia(A - sigma * B)   # the oracle's dense Bunch-Kaufman
     P.close()
+
+
+def test_noalloc_largest_order_and_bad_arguments():
+    """n = 512, the largest order, fills the whole fixed array; n = 0 and lda < n are refused."""
+    kep = require_gpu()
+    p = make_pair(2, 2, 4, seed=4)                     # n = 512
+    assert p.n == 512
+    A, B = p.A().toarray(), p.B().toarray()
+    P = kep.Problem.from_pencil(p)
+    for sigma in (0.33, -1.5):
+        code, got = _noalloc(kep, A, B, sigma)
+        assert code == kep.KEP_OK
+        r = P.factor(sigma)
+        assert got == (r.neg, r.zero, r.pos) == core.dense_inertia(A - sigma * B)
+    P.close()
+    import torch
+    d = torch.zeros(16, dtype=torch.float64, device="cuda")
+    out = (ctypes.c_int64 * 3)()
+    assert kep.lib().kep_dense_inertia_noalloc(0, d.data_ptr(), d.data_ptr(), 1, 0.0, None, out) == kep.KEP_ERR_INVALID
+    assert kep.lib().kep_dense_inertia_noalloc(4, d.data_ptr(), d.data_ptr(), 3, 0.0, None, out) == kep.KEP_ERR_INVALID
 
 
 def test_noalloc_two_by_two_pivots_and_limits():
@@ -60,7 +82,7 @@ def test_noalloc_two_by_two_pivots_and_limits():
         code, got = _noalloc(kep, A, B, s)
         assert code == kep.KEP_OK
         r = P.factor(s)
-        assert got == (r.neg, r.zero, r.pos)
+        assert got == (r.neg, r.zero, r.pos) == core.dense_inertia(A - s * B)
     P.close()
     out = (ctypes.c_int64 * 3)()
     assert kep.lib().kep_dense_inertia_noalloc(513, 1, 1, 513, 0.0, None, out) == kep.KEP_ERR_INVALID
