@@ -38,6 +38,10 @@ def metric_for(workload: str) -> str:
 UNIT = "factorizations/s"
 # FP64 FMA issue rate of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock).
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9
+# DRAM bytes (read + write) of lf_flush_tc_kernel per FP64-equivalent update flop, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) over all 832 flush launches of one factorization
+# of the n = 49,768 workload: 18.41 GB for 4.095e11 flop
+FLUSH_DRAM_BYTES_PER_FP64_FLOP = 0.04496
 WORKLOAD_DESC = {
     "scale": "periodic diamond 32x32x18 cells, 16,384 random vacancies, 131,072 atoms x 4 sp3 orbitals, "
              "n=524,288, jitter 0.05 A, 2.9 A cutoff",
@@ -137,6 +141,27 @@ def _measured_peaks():
     return out
 
 
+def measure_fp64_peak(torch, n: int = 8192, reps: int = 3):
+    """FP64 rate of this GPU measured with the vendor library (cuBLAS DGEMM through torch.mm,
+    n x n, best of reps): the denominator for the FP64 fractions (not on the hot path)."""
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.mm(a, b)
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.mm(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / best
+
+
 def flops_of(p, refined: bool = False) -> float:
     """Symbolic factorization flops of the GPU plan for pencil p (host analysis only, no device)."""
     import paper_1710_05134_gb300 as kep
@@ -232,11 +257,13 @@ def _cpu_sample_pencil():
 
 VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_min_front", "gershgorin_multisection8",
             "stage3_f32_ir", "hermitian_mid")
+# variants on a workload of their own (run after the main problem is released)
+SEPARATE_VARIANTS = ("multisection_batch", "graph_replay")
 
 
 def measure_variants(P, p, torch, kth, which="all"):
     """Timings of the next rows on the same problem (device-synchronised wall clock)."""
-    want = set(VARIANTS) if which == "all" else set(which.split(","))
+    want = set(VARIANTS) if which == "all" else set(which.split(",")) - set(SEPARATE_VARIANTS)
     unknown = want - set(VARIANTS)
     if unknown:
         raise ValueError(f"unknown variants {sorted(unknown)}")
@@ -287,6 +314,61 @@ def measure_variants(P, p, torch, kth, which="all"):
     if "hermitian_mid" in want:
         out["hermitian_mid"] = measure_hermitian(torch)
     return out
+
+
+def measure_multisection_batch(torch, nshift: int = 8, reps: int = 2):
+    """The multisection workload (n = 262,144, 32x16x16 cells, refined nested dissection): nshift
+    shifts factored one after another (kep_factor each) against the same shifts in one
+    kep_factor_multi call (all shifts' fronts in the same launches), best of reps, equal counts
+    required."""
+    import paper_1710_05134_gb300 as kep
+    from gen import workload
+    sync = torch.cuda.synchronize
+    p = workload("batch")
+    res = {"n": p.n, "shifts": nshift, "workload": "periodic diamond 32x16x16 cells, n=262,144"}
+    sig = [0.30 + 0.011 * i for i in range(nshift)]
+    with kep.Problem.from_pencil(p, refined_order=True) as P:
+        res["flops_per_factorization"] = P.info.flops_factor
+        P.factor(0.29)
+        P.factor_multi(sig)                            # allocations of the batched path, untimed
+        t_seq, t_multi = [], []
+        for _ in range(reps):
+            sync(); t0 = time.perf_counter()
+            nu_seq = [P.factor(s).neg for s in sig]
+            sync(); t_seq.append(time.perf_counter() - t0)
+            sync(); t0 = time.perf_counter()
+            nu_multi = [r.neg for r in P.factor_multi(sig)]
+            sync(); t_multi.append(time.perf_counter() - t0)
+        res.update(sequential_s=min(t_seq), batched_s=min(t_multi),
+                   sequential_factorizations_per_s=nshift / min(t_seq),
+                   batched_factorizations_per_s=nshift / min(t_multi),
+                   speedup=min(t_seq) / min(t_multi), counts_equal=nu_seq == nu_multi, nu=nu_multi)
+    return res
+
+
+def measure_graph_replay(torch, reps: int = 5):
+    """The n = 49,768 workload (where the pivot-step launches are latency-bound): factorizations
+    with each level's step passes replayed as CUDA graphs against separate launches, best of
+    reps each, equal counts required."""
+    import paper_1710_05134_gb300 as kep
+    from gen import workload
+    sync = torch.cuda.synchronize
+    p = workload("mid")
+    sig = [0.30 + 0.013 * i for i in range(reps)]
+    res = {"n": p.n, "factorizations": reps}
+    with kep.Problem.from_pencil(p) as P:
+        for mode in (False, True):
+            P.set_graphs(mode)
+            P.factor(0.29)                              # capture (graphs) / warm-up, untimed
+            ts_, nus = [], []
+            for s in sig:
+                sync(); t0 = time.perf_counter()
+                nus.append(P.factor(s).neg)
+                sync(); ts_.append(time.perf_counter() - t0)
+            res["graphs" if mode else "launches"] = {"best_s": min(ts_), "mean_s": sum(ts_) / len(ts_), "nu": nus}
+        res["counts_equal"] = res["graphs"]["nu"] == res["launches"]["nu"]
+        res["speedup"] = res["launches"]["best_s"] / res["graphs"]["best_s"]
+    return res
 
 
 def measure_fp32_factor(P, p, torch):
@@ -403,7 +485,7 @@ def main():
     ap.add_argument("--no-kth", action="store_true", help="skip Algorithm 4 (time to lambda_k)")
     ap.add_argument("--no-validate", action="store_true", help="skip the second-ordering count check")
     ap.add_argument("--variants", nargs="?", const="all", default=None,
-                    help="also measure the next rows (all, or a comma list of: " + ", ".join(VARIANTS) + ")")
+                    help="also measure the next rows (all, or a comma list of: " + ", ".join(VARIANTS + SEPARATE_VARIANTS) + ")")
     ap.add_argument("--event-timing", type=int, default=1,
                     help="bracket the roofline kernels' launches with CUDA events (1) or not (0)")
     args = ap.parse_args()
@@ -422,6 +504,7 @@ def main():
         dist.init_process_group("nccl")
 
     refined = args.ordering == "refined"
+    fp64_peak = measure_fp64_peak(torch)
     p = make_workload(args.workload)
     t0 = time.perf_counter()
     P = kep.Problem.from_pencil(p, refined_order=refined)
@@ -523,9 +606,10 @@ def main():
     if classes["update"][1] > 0 and fl["update"] > 0:
         a = fl["update"] / (classes["update"][1] / 1e3)
         rooflines["update"] = {"bound": "alu", "kernel": "lf_schur_kernel (FP64 FMA tiles)",
-                               "achieved": a / 1e12, "peak": FP64_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
-                               "frac": a / FP64_PEAK_DERIVED,
-                               "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                               "achieved": a / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                               "frac": a / fp64_peak,
+                               "peak_source": "measured in this run: cuBLAS DGEMM 8192^3 (torch.mm), best of 3",
+                               "peak_derived_tflops": FP64_PEAK_DERIVED / 1e12,
                                "launches": classes["update"][0], "kernel_ms": classes["update"][1]}
     if classes["flush_tc"][1] > 0 and fl["flush_tc"] > 0:
         sec = classes["flush_tc"][1] / 1e3
@@ -539,12 +623,17 @@ def main():
                            "kernel's launches",
             "peak_source": src + " (the kernel's own dtype)",
             "issued_bf16_tflops": issued / 1e12, "frac_issued_bf16": issued / pk,
-            "fp64_fma_peak_ratio": method / FP64_PEAK_DERIVED,
+            "fp64_peak_ratio": method / fp64_peak,
+            "traffic_note": "DRAM bytes per launch scaled from ncu at n=49,768 (all 832 flush launches of one "
+                            "factorization: 0.04496 B per FP64-equivalent flop) by this run's flops per launch",
             "launches": classes["flush_tc"][0], "kernel_ms": classes["flush_tc"][1]}
+    if "flush_tc" in rooflines and classes["flush_tc"][0] > 0:
+        rooflines["flush_tc"]["traffic"] = FLUSH_DRAM_BYTES_PER_FP64_FLOP * fl["flush_fp64_equivalent"] / classes["flush_tc"][0]
+        rooflines["flush_tc"]["algorithmic_flops_per_launch"] = fl["flush_fp64_equivalent"] / classes["flush_tc"][0]
     roofline = rooflines.get(dom)
     if roofline is not None:
         roofline = dict(roofline)
-        roofline["traffic"] = None
+        roofline.setdefault("traffic", None)
         roofline["share_of_step"] = roofline["kernel_ms"] / ms if ms > 0 else None
         roofline["class"] = dom
 
@@ -581,6 +670,16 @@ def main():
                            "nu_timed": want, "nu_second": got, "equal": got == want,
                            "seconds": time.perf_counter() - t0})
     validation["ok"] = validation["monotone"] and validation.get("equal", True)
+    if args.variants and rank == 0:
+        sep = SEPARATE_VARIANTS if args.variants == "all" else [v for v in args.variants.split(",")
+                                                               if v in SEPARATE_VARIANTS]
+        variants = variants or {}
+        for name in sep:
+            try:
+                variants[name] = measure_multisection_batch(torch) if name == "multisection_batch" \
+                    else measure_graph_replay(torch)
+            except Exception as exc:
+                variants[name] = {"error": str(exc)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -610,6 +709,7 @@ def main():
                 "clocks": clocks, "e2e": e2e, "gpu_launches": timing["total_launches"],
                 "roofline": roofline, "rooflines": rooflines, "cpu_baseline": cpu,
                 "nu_validation": validation,
+                "fp64_peak_measured_tflops": fp64_peak / 1e12,
                 "factorization_fp64_equivalent_tflops": info.flops_factor * args.steps / (ms / 1e3) / 1e12,
                 "kernels_ms_warmup_step": {k: v[1] for k, v in warm_classes.items()},
                 "kernels_ms_timed": {k: v[1] for k, v in classes.items() if v[1] > 0}}

@@ -296,6 +296,9 @@ def workload(name: str, seed: int = 0) -> Pencil:
     * ``million``:  32x32x32 cells, 262,144 atoms, n = 1,048,576.
     * ``mid_peierls``: the ``mid`` pencil with a Peierls phase e^{i theta}, theta ~ U(-pi, pi), on
                     every atom pair (complex Hermitian, n = 49,768).
+    * ``scale_peierls``: the ``scale`` pencil with Peierls phases (complex Hermitian, n = 524,288,
+                    the differentiation workload).
+    * ``batch``:    32x16x16 cells, 65,536 atoms, n = 262,144 (the multisection workload).
     """
     if name == "small":
         return make_pair(4, 4, 4, seed=seed)
@@ -307,6 +310,10 @@ def workload(name: str, seed: int = 0) -> Pencil:
         return make_pair(12, 12, 12, seed=seed, vacancies=1382, phases="peierls")
     if name == "million":
         return make_pair(32, 32, 32, seed=seed)
+    if name == "scale_peierls":
+        return make_pair(32, 32, 18, seed=seed, vacancies=16384, phases="peierls")
+    if name == "batch":
+        return make_pair(32, 16, 16, seed=seed)
     if name.startswith("cells:"):
         nx, ny, nz = (int(v) for v in name[6:].split("x"))
         return make_pair(nx, ny, nz, seed=seed)

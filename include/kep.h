@@ -347,6 +347,13 @@ typedef struct {
   int64_t total_launches;
 } kep_timing;
 
+/* Run each pass of pivot steps of a factorization level (the panel, L21, apply and update
+ * launches of up to a few hundred steps) as a CUDA graph captured at its first use and replayed by
+ * later factorizations of the same context (1, the default), or as separate launches (0).  The
+ * graphs are captured on ctx's stream; with event timing enabled the launches are always issued
+ * separately.  Synchronises ctx's stream.  Errors: KEP_ERR_INVALID. */
+kep_status kep_set_graphs(kep_ctx* ctx, int enable);
+
 /* Enable (1) or disable (0) per-launch event timing; synchronises ctx's stream. */
 kep_status kep_set_timing(kep_ctx* ctx, int enable);
 

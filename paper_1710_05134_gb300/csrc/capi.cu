@@ -31,7 +31,10 @@ template <typename T>
 static kep_status dev_alloc(kep_ctx* c, T** out, size_t count, bool plan_dependent = false) {
   *out = nullptr;
   void* p = nullptr;
-  if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return KEP_ERR_NOMEM;
+  if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();                  // an allocation failure is reported, not left pending
+    return KEP_ERR_NOMEM;
+  }
   (plan_dependent ? c->mem_allocs : c->allocs).push_back(p);
   *out = static_cast<T*>(p);
   return KEP_OK;
@@ -86,6 +89,9 @@ kep_status setup_memory(kep_ctx* c) {
   const int64_t nflags = df_flag_bases(P, fbase);
   KEP_TRY(dev_alloc(c, &c->d_df_flags, nflags, true));
   if (cudaMemset(c->d_df_flags, 0, sizeof(int32_t) * std::max<int64_t>(nflags, 1)) != cudaSuccess) return KEP_ERR_CUDA;
+  KEP_TRY(dev_alloc(c, &c->d_df_pcnt, nflags, true));
+  c->df_nflags = nflags;
+  for (int i = 0; i < 2; ++i) KEP_TRY(dev_alloc(c, &c->d_df_part_base[i], P.nfronts, true));
   const int32_t* fb = nullptr;
   KEP_TRY(dev_upload_mem(c, &fb, fbase));
   c->d_df_fbase = const_cast<int32_t*>(fb);
@@ -94,12 +100,12 @@ kep_status setup_memory(kep_ctx* c) {
 
 void release_memory(kep_ctx* c) {
   cudaStreamSynchronize(c->stream);
+  c->graphs.clear();                     // they hold pointers into the storage freed here
   for (void* p : c->mem_allocs) cudaFree(p);
   c->mem_allocs.clear();
   c->emul_ws = nullptr;
   c->emul_bytes = 0;
-  c->d_emul_off = nullptr;
-  c->emul_min_planned = -1;
+  for (auto& ep : c->emul_plan) { ep.min_planned = -1; ep.G = 0; ep.d_off = nullptr; ep.h_end.clear(); }
   for (int i = 0; i < 2; ++i) {
     c->slot_ready[i] = false;
     c->slot[i].valid = false;
@@ -109,6 +115,22 @@ void release_memory(kep_ctx* c) {
   }
   c->d_df_flags = nullptr;
   c->d_df_fbase = nullptr;
+  c->d_df_pcnt = nullptr;
+  c->d_df_part_base[0] = c->d_df_part_base[1] = nullptr;
+  c->d_df_part = nullptr;
+  c->df_part_cap = 0;
+  c->multi_cap = 0;
+  c->ent_G = 0;
+  c->d_ent_front = nullptr;
+  c->d_ent_shift = nullptr;
+  {   // entry arrays grown for a multisection step were plan-dependent: back to the originals
+    const double* p21 = c->W.P21;
+    const int64_t* p21o = c->W.p21_off;
+    c->W = c->W0;
+    c->W.P21 = const_cast<double*>(p21);
+    c->W.p21_off = const_cast<int64_t*>(p21o);
+    c->w_cap_entries = c->W0.cap;
+  }
 }
 
 // Delayed pivots overflowed a front's slack: grow the slack of every non-leaf front and rebuild
@@ -120,7 +142,174 @@ static kep_status replan(kep_ctx* c, int32_t slack_base) {
   return setup_memory(c);
 }
 
-kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out, int* bits_out);
+// Counts of a Hermitian pencil from those of its real embedding, which has every eigenvalue
+// twice: half of each.  An odd count means an eigenvalue within rounding of the shift (the pair's
+// two copies fell on both sides), reported like an exact zero pivot.
+static kep_status herm_counts(kep_ctx* c, kep_status st, kep_inertia* out) {
+  if (!c->herm_n || !out || (st != KEP_OK && st != KEP_ERR_SINGULAR)) return st;
+  const bool odd = (out->neg & 1) || (out->pos & 1);
+  out->neg /= 2;
+  out->pos /= 2;
+  out->zero = c->herm_n - out->neg - out->pos;
+  return (odd || out->zero > 0) ? KEP_ERR_SINGULAR : st;
+}
+
+// Tensor-core batches for G shifts: a level's entries on the tensor-core path (consecutive in its
+// front-major entry list, at most emul_max_batch() entries and kEmulBudget bytes of workspace
+// each) and each entry's workspace offset inside its batch.
+static kep_status plan_emul(kep_ctx* c, int G, int64_t min_front, kep_ctx::EmulPlan*& out) {
+  out = nullptr;
+  kep_ctx::EmulPlan& ep = c->emul_plan[G == 1 ? 0 : 1];
+  if (ep.min_planned != min_front || ep.G != G) {
+    const Plan& P = c->plan;
+    constexpr int64_t kEmulBudget = 24ll << 30;
+    const int64_t nent = static_cast<int64_t>(P.nfronts) * G;
+    std::vector<int64_t> off(nent, 0);
+    ep.h_end.assign(nent, 0);
+    int64_t need = 0;
+    for (int32_t l = 0; l < P.nlevels; ++l) {
+      const int32_t lb = P.level_ptr[l] * G, le = P.level_ptr[l + 1] * G;
+      auto front = [&](int32_t e) { return P.level_fronts[P.level_ptr[l] + (e - lb) / G]; };
+      int32_t e = lb;
+      while (e < le) {
+        if (P.m_alloc[front(e)] < min_front) { ++e; continue; }
+        const int32_t start = e;
+        int64_t bytes = 0;
+        while (e < le && P.m_alloc[front(e)] >= min_front && e - start < emul_max_batch()) {
+          const int64_t fb = (static_cast<int64_t>(emul_workspace_bytes(P.m_alloc[front(e)])) + 255) / 256 * 256;
+          if (e > start && bytes + fb > kEmulBudget) break;
+          off[e] = bytes;
+          bytes += fb;
+          ++e;
+        }
+        ep.h_end[start] = e - lb;
+        need = std::max(need, bytes);
+      }
+    }
+    if (need > c->emul_bytes) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, need) != cudaSuccess) { cudaGetLastError(); return KEP_ERR_NOMEM; }
+      if (cudaMemset(p, 0, need) != cudaSuccess) return KEP_ERR_CUDA;
+      c->mem_allocs.push_back(p);
+      c->emul_ws = p;
+      c->emul_bytes = need;
+    }
+    if (!ep.d_off) {   // capacity for the largest G this plan can serve
+      int64_t* p = nullptr;
+      KEP_TRY(dev_alloc(c, &p, static_cast<int64_t>(P.nfronts) * (G == 1 ? 1 : kMaxShifts), true));
+      ep.d_off = p;
+    }
+    if (cudaMemcpy(ep.d_off, off.data(), sizeof(int64_t) * nent, cudaMemcpyHostToDevice) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    ep.G = G;
+    ep.min_planned = need > 0 ? min_front : -2;
+  }
+  if (c->emul_bytes > 0 && ep.min_planned == min_front) out = &ep;
+  return KEP_OK;
+}
+
+// Factor the G matrices ca[g] A + cb[g] B in the same launches; shift g's factor goes to slots[g]
+// with contribution-block pool pools[g] and L21 workspace p21[g].
+static kep_status factor_set(kep_ctx* c, int G, FactorSlot* const* slots, double* const* pools,
+                             double* const* p21, const double* ca, const double* cb, kep_inertia* out, int* bits) {
+  const Plan& P = c->plan;
+  FactorLaunch F;
+  F.plan = &P;
+  F.T = c->T;
+  F.SS.n = G;
+  for (int g = 0; g < G; ++g) {
+    slots[g]->valid = false;
+    F.SS.s[g] = *slots[g];
+    F.SS.cbpool[g] = pools[g];
+    F.SS.P21[g] = p21[g];
+  }
+  F.G = G;
+  if (G == 1) {
+    F.W = c->W;
+    F.d_ent_front = c->d_level_fronts;
+    F.d_ent_shift = nullptr;
+    F.h_ent_front = P.level_fronts.data();
+  } else {
+    F.W = c->W;               // the entry arrays of c->W were grown to level width x G
+    F.d_ent_front = c->d_ent_front;
+    F.d_ent_shift = c->d_ent_shift;
+    F.h_ent_front = c->h_ent_front.data();
+  }
+  F.h_done = c->h_done;
+  F.d_red = c->d_red;
+  F.h_red = c->h_red;
+  F.stream = c->stream;
+  F.num_sms = c->num_sms;
+  F.timer = &c->timer;
+  F.flops = c->d_flops;
+  F.graphs = &c->graphs;
+  if (!c->capture_stream && cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->capture_stream = nullptr;
+  }
+  F.capture_stream = c->capture_stream;
+  F.emul_min = c->schur_mode == KEP_SCHUR_EMULATED ? c->emul_min_front : 0;
+  F.fp32_schur = c->schur_mode == KEP_SCHUR_FP32;
+  F.emul_ws = nullptr;
+  F.d_emul_off = nullptr;
+  F.h_emul_end = nullptr;
+  if (F.emul_min > 0) {
+    kep_ctx::EmulPlan* ep = nullptr;
+    KEP_TRY(plan_emul(c, G, F.emul_min, ep));
+    if (ep) {
+      F.emul_ws = c->emul_ws;
+      F.d_emul_off = ep->d_off;
+      F.h_emul_end = ep->h_end.data();
+    } else {
+      F.emul_min = 0;
+    }
+  }
+  const kep_status st = run_factor(F, ca, cb, out, bits);
+  if (st != KEP_OK) return st;
+  for (int g = 0; g < G; ++g) { slots[g]->ca = ca[g]; slots[g]->cb = cb[g]; }
+  return KEP_OK;
+}
+
+// Status of one factorization from its counts and bits; marks the slot valid when usable.
+static kep_status finish_slot(kep_ctx* c, FactorSlot& S, const kep_inertia& in, int bits) {
+  if (bits & ST_POOL) return KEP_ERR_POOL;
+  if (bits & ST_NONFINITE) return KEP_ERR_NONFINITE;
+  if (bits & ST_TIMEOUT) return KEP_ERR_TIMEOUT;
+  if (in.neg + in.zero + in.pos != c->plan.n) return KEP_ERR_POOL;
+  S.valid = true;
+  return in.zero > 0 ? KEP_ERR_SINGULAR : KEP_OK;
+}
+
+// Host copies of a public slot's per-front counts (for the solves), after a factorization.
+static kep_status record_slot(kep_ctx* c, int slot, int bits) {
+  FactorSlot& S = c->slot[slot];
+  c->slot_status[slot] = bits;
+  c->slot_nelim[slot].resize(c->plan.nfronts);
+  c->slot_din[slot].resize(c->plan.nfronts);
+  if (cudaMemcpy(c->slot_nelim[slot].data(), S.nelim, sizeof(int32_t) * c->plan.nfronts,
+                 cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(c->slot_din[slot].data(), S.d_in, sizeof(int32_t) * c->plan.nfronts,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return KEP_ERR_CUDA;
+  ++c->factor_version[slot];
+  return KEP_OK;
+}
+
+kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out, int* bits_out) {
+  FactorSlot* sp = &c->slot[slot];
+  double* pool = c->d_cbpool;
+  double* p21 = c->W.P21;
+  kep_inertia in{0, 0, 0, 0};
+  int bits = 0;
+  const kep_status st = factor_set(c, 1, &sp, &pool, &p21, &ca, &cb, &in, &bits);
+  *bits_out = bits;
+  if (st != KEP_OK) return st;
+  KEP_TRY(record_slot(c, slot, bits));
+  if (out) *out = in;
+  const kep_status fs = finish_slot(c, c->slot[slot], in, bits);
+  c->slot_zero[slot] = c->slot[slot].valid ? in.zero : 0;
+  return fs;
+}
 
 kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out) {
   for (int attempt = 0;; ++attempt) {
@@ -131,120 +320,93 @@ kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* o
       KEP_TRY(replan(c, c->plan.slack_base * 4));
       continue;
     }
-    if (c->herm_n && out && (st == KEP_OK || st == KEP_ERR_SINGULAR)) {
-      // the real embedding of a Hermitian pencil has every eigenvalue twice: its counts are
-      // twice those of the pencil.  An odd count means an eigenvalue within rounding of the shift
-      // (the pair's two copies fell on both sides), reported like an exact zero pivot.
-      const bool odd = (out->neg & 1) || (out->pos & 1);
-      out->neg /= 2;
-      out->pos /= 2;
-      out->zero = c->herm_n - out->neg - out->pos;
-      if (odd || out->zero > 0) st = KEP_ERR_SINGULAR;
-    }
-    return st;
+    return herm_counts(c, st, out);
   }
 }
 
-kep_status ctx_factor_once(kep_ctx* c, int slot, double ca, double cb, kep_inertia* out, int* bits_out) {
-  FactorSlot& S = c->slot[slot];
-  S.valid = false;
-  FactorLaunch F;
-  F.plan = &c->plan;
-  F.T = c->T;
-  F.S = S;
-  F.cbpool = c->d_cbpool;
-  F.W = c->W;
-  F.d_level_fronts = c->d_level_fronts;
-  F.h_done = c->h_done;
-  F.d_red = c->d_red;
-  F.h_red = c->h_red;
-  F.stream = c->stream;
-  F.num_sms = c->num_sms;
-  F.timer = &c->timer;
-  F.flops = c->d_flops;
-  F.emul_min = c->schur_mode == KEP_SCHUR_EMULATED ? c->emul_min_front : 0;
-  F.fp32_schur = c->schur_mode == KEP_SCHUR_FP32;
-  F.emul_ws = nullptr;
-  F.d_emul_off = nullptr;
-  F.h_emul_end = nullptr;
-  if (F.emul_min > 0) {
-    const Plan& P = c->plan;
-    if (c->emul_min_planned != F.emul_min) {
-      // batches of a level's fronts on the tensor-core path (consecutive in the level's
-      // decreasing order, at most emul_max_batch() and kEmulBudget bytes of workspace each) and
-      // each front's workspace offset inside its batch
-      constexpr int64_t kEmulBudget = 24ll << 30;
-      std::vector<int64_t> off(P.nfronts, 0);
-      c->h_emul_end.assign(P.nfronts, 0);
-      int64_t need = 0;
-      for (int32_t l = 0; l < P.nlevels; ++l) {
-        const int32_t lb = P.level_ptr[l], le = P.level_ptr[l + 1];
-        int32_t e = lb;
-        while (e < le) {
-          if (P.m_alloc[P.level_fronts[e]] < F.emul_min) { ++e; continue; }
-          const int32_t start = e;
-          int64_t bytes = 0;
-          while (e < le && P.m_alloc[P.level_fronts[e]] >= F.emul_min && e - start < emul_max_batch()) {
-            const int64_t fb = (static_cast<int64_t>(emul_workspace_bytes(P.m_alloc[P.level_fronts[e]])) + 255) / 256 * 256;
-            if (e > start && bytes + fb > kEmulBudget) break;
-            off[e] = bytes;
-            bytes += fb;
-            ++e;
-          }
-          c->h_emul_end[start] = e - lb;
-          need = std::max(need, bytes);
-        }
-      }
-      if (need > c->emul_bytes) {
-        void* p = nullptr;
-        if (cudaMalloc(&p, need) != cudaSuccess) return KEP_ERR_NOMEM;
-        if (cudaMemset(p, 0, need) != cudaSuccess) return KEP_ERR_CUDA;
-        c->mem_allocs.push_back(p);
-        c->emul_ws = p;
-        c->emul_bytes = need;
-      }
-      if (!c->d_emul_off) {
-        void* p = nullptr;
-        if (cudaMalloc(&p, sizeof(int64_t) * std::max<int32_t>(1, P.nfronts)) != cudaSuccess) return KEP_ERR_NOMEM;
-        c->mem_allocs.push_back(p);
-        c->d_emul_off = static_cast<int64_t*>(p);
-      }
-      if (cudaMemcpy(c->d_emul_off, off.data(), sizeof(int64_t) * P.nfronts, cudaMemcpyHostToDevice) != cudaSuccess)
-        return KEP_ERR_CUDA;
-      c->emul_min_planned = need > 0 ? F.emul_min : -2;
+// Device bytes one more shift of a multisection step needs: its slot, pool and L21 workspace.
+static int64_t shift_bytes(const Plan& P) {
+  return 8 * P.front_total + 8 * P.vec_total + 17 * P.piv_total + 24ll * P.nfronts + 8 * P.cb_total +
+         8ll * std::max<int64_t>(P.max_large_rows, 1) * kPanel;
+}
+
+// Resources for G shifts in one launch sequence: G - 1 extra slots, pools and L21 workspaces,
+// the front-major entry lists, and LargeWork entry arrays for level width x G.
+static kep_status ensure_multi(kep_ctx* c, int G) {
+  const Plan& P = c->plan;
+  if (c->multi_cap < G) {
+    for (int j = std::max(0, c->multi_cap - 1); j < G - 1; ++j) {
+      FactorSlot& S = c->mslot[j];
+      KEP_TRY(dev_alloc(c, &S.F, P.front_total, true));
+      KEP_TRY(dev_alloc(c, &S.rowvar, P.vec_total, true));
+      KEP_TRY(dev_alloc(c, &S.apos, P.vec_total, true));
+      KEP_TRY(dev_alloc(c, &S.Dd, P.piv_total, true));
+      KEP_TRY(dev_alloc(c, &S.De, P.piv_total, true));
+      KEP_TRY(dev_alloc(c, &S.piv, P.piv_total, true));
+      KEP_TRY(dev_alloc(c, &S.d_in, P.nfronts, true));
+      KEP_TRY(dev_alloc(c, &S.nelim, P.nfronts, true));
+      KEP_TRY(dev_alloc(c, &S.d_out, P.nfronts, true));
+      KEP_TRY(dev_alloc(c, &S.cnt, 3 * static_cast<size_t>(P.nfronts), true));
+      KEP_TRY(dev_alloc(c, &S.status, 2, true));
+      KEP_TRY(dev_alloc(c, &c->mpool[j], P.cb_total, true));
+      KEP_TRY(dev_alloc(c, &c->mp21[j], std::max<int64_t>(P.max_large_rows, 1) * kPanel, true));
+      S.valid = false;
     }
-    if (c->emul_bytes > 0 && c->emul_min_planned == F.emul_min) {
-      F.emul_ws = c->emul_ws;
-      F.d_emul_off = c->d_emul_off;
-      F.h_emul_end = c->h_emul_end.data();
-    } else {
-      F.emul_min = 0;
-    }
+    c->multi_cap = G;
   }
-  int bits = 0;
-  kep_inertia in{0, 0, 0, 0};
-  kep_status st = run_factor(F, ca, cb, &in, &bits);
-  *bits_out = bits;
-  if (st != KEP_OK) return st;
-  S.ca = ca; S.cb = cb;
-  c->slot_status[slot] = bits;
-  c->slot_nelim[slot].resize(c->plan.nfronts);
-  c->slot_din[slot].resize(c->plan.nfronts);
-  if (cudaMemcpy(c->slot_nelim[slot].data(), S.nelim, sizeof(int32_t) * c->plan.nfronts,
-                 cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(c->slot_din[slot].data(), S.d_in, sizeof(int32_t) * c->plan.nfronts,
-                 cudaMemcpyDeviceToHost) != cudaSuccess)
-    return KEP_ERR_CUDA;
-  ++c->factor_version[slot];
-  if (out) *out = in;
-  if (bits & ST_POOL) return KEP_ERR_POOL;
-  if (bits & ST_NONFINITE) return KEP_ERR_NONFINITE;
-  if (bits & ST_TIMEOUT) return KEP_ERR_TIMEOUT;
-  if (in.neg + in.zero + in.pos != c->plan.n) return KEP_ERR_POOL;
-  S.valid = true;
-  c->slot_zero[slot] = in.zero;
-  if (in.zero > 0) return KEP_ERR_SINGULAR;
+  if (c->ent_G != G) {
+    const int64_t nent = static_cast<int64_t>(P.nfronts) * G;
+    c->h_ent_front.resize(nent);
+    std::vector<int8_t> sh(nent);
+    for (int32_t q = 0; q < P.nfronts; ++q)       // level order kept: entry q G + g is front q, shift g
+      for (int g = 0; g < G; ++g) {
+        c->h_ent_front[static_cast<int64_t>(q) * G + g] = P.level_fronts[q];
+        sh[static_cast<int64_t>(q) * G + g] = static_cast<int8_t>(g);
+      }
+    if (!c->d_ent_front) {   // capacity for kMaxShifts
+      KEP_TRY(dev_alloc(c, &c->d_ent_front, static_cast<int64_t>(P.nfronts) * kMaxShifts, true));
+      KEP_TRY(dev_alloc(c, &c->d_ent_shift, static_cast<int64_t>(P.nfronts) * kMaxShifts, true));
+    }
+    if (cudaMemcpy(c->d_ent_front, c->h_ent_front.data(), sizeof(int32_t) * nent, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_ent_shift, sh.data(), nent, cudaMemcpyHostToDevice) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    c->ent_G = G;
+  }
+  const int32_t need = std::max<int32_t>(P.max_level_width, 1) * G;
+  if (c->w_cap_entries < need) {
+    LargeWork& W = c->W;
+    KEP_TRY(dev_alloc(c, &W.k, need, true)); KEP_TRY(dev_alloc(c, &W.w, need, true));
+    KEP_TRY(dev_alloc(c, &W.q, need, true)); KEP_TRY(dev_alloc(c, &W.fails, need, true));
+    KEP_TRY(dev_alloc(c, &W.swap, need, true)); KEP_TRY(dev_alloc(c, &W.done, need, true));
+    KEP_TRY(dev_alloc(c, &W.ws, need, true)); KEP_TRY(dev_alloc(c, &W.we, need, true));
+    KEP_TRY(dev_alloc(c, &W.kend, need, true)); KEP_TRY(dev_alloc(c, &W.flush, need, true));
+    KEP_TRY(dev_alloc(c, &W.reset, need, true)); KEP_TRY(dev_alloc(c, &W.finish, need, true));
+    KEP_TRY(dev_alloc(c, &W.L11, static_cast<size_t>(need) * kPanel * kPanel, true));
+    KEP_TRY(dev_alloc(c, &W.Dblk, static_cast<size_t>(need) * 2 * kPanel, true));
+    KEP_TRY(dev_alloc(c, &W.pi, static_cast<size_t>(need) * kPanel, true));
+    KEP_TRY(dev_alloc(c, &W.pt, static_cast<size_t>(need) * kPanel, true));
+    KEP_TRY(dev_alloc(c, &W.colmax, static_cast<size_t>(need) * kPanel, true));
+    int32_t* hd = nullptr;
+    if (cudaMallocHost(reinterpret_cast<void**>(&hd), sizeof(int32_t) * need) != cudaSuccess) return KEP_ERR_NOMEM;
+    if (c->h_done) cudaFreeHost(c->h_done);
+    c->h_done = hd;
+    W.cap = need;
+    c->w_cap_entries = need;
+  }
   return KEP_OK;
+}
+
+// Shifts one launch sequence can serve: at most kMaxShifts, as many as fit in free device memory
+// (with 4 GB to spare).
+static int multi_group(kep_ctx* c, int32_t ns) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); return 1; }
+  const int64_t per = shift_bytes(c->plan);
+  int have = std::max(1, c->multi_cap);
+  int64_t avail = static_cast<int64_t>(free_b) - (4ll << 30);
+  int G = have;
+  while (G < std::min<int32_t>(ns, kMaxShifts) && avail >= per) { ++G; avail -= per; }
+  return std::max(1, std::min<int>(G, std::min<int32_t>(ns, kMaxShifts)));
 }
 
 kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x) {
@@ -265,8 +427,19 @@ kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x) {
   L.h_nelim = c->slot_nelim[slot].data();
   if (c->df_version[slot] != c->factor_version[slot]) {
     // work items of the dataflow solve for this factorization (its delays and pivot counts)
+    int64_t part_total = 0;
     build_df_items(c->plan, c->slot_nelim[slot].data(), c->slot_din[slot].data(), c->df_items[slot],
-                   c->df_fwd_off[slot], c->df_bwd_off[slot], c->df_bwd_start[slot]);
+                   c->df_fwd_off[slot], c->df_bwd_off[slot], c->df_bwd_start[slot], c->df_part_base[slot],
+                   part_total);
+    if (part_total > c->df_part_cap) {
+      double* pp = nullptr;
+      KEP_TRY(dev_alloc(c, &pp, part_total + part_total / 4, true));
+      c->d_df_part = pp;
+      c->df_part_cap = part_total + part_total / 4;
+    }
+    if (cudaMemcpyAsync(c->d_df_part_base[slot], c->df_part_base[slot].data(), sizeof(int64_t) * c->plan.nfronts,
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return KEP_ERR_CUDA;
     const int64_t need = std::max<int64_t>(1, static_cast<int64_t>(c->df_items[slot].size()));
     if (need > c->df_items_cap[slot]) {
       int2* p = nullptr;
@@ -288,6 +461,10 @@ kep_status ctx_solve_dev(kep_ctx* c, int slot, const double* b, double* x) {
   L.df_flags = c->d_df_flags;
   L.df_fbase = c->d_df_fbase;
   L.epoch = ++c->df_epoch;
+  L.df_part = c->d_df_part;
+  L.df_part_base = c->d_df_part_base[slot];
+  L.df_pcnt = c->d_df_pcnt;
+  L.df_nflags = c->df_nflags;
   L.stream = c->stream;
   L.num_sms = c->num_sms;
   L.timer = &c->timer;
@@ -498,8 +675,10 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   AL(W.ws, ent); AL(W.we, ent); AL(W.kend, ent); AL(W.flush, ent); AL(W.reset, ent); AL(W.finish, ent);
   AL(W.L11, ent * kPanel * kPanel); AL(W.Dblk, ent * 2 * kPanel); AL(W.pi, ent * kPanel);
   AL(W.pt, ent * kPanel); AL(W.colmax, ent * kPanel);
+  c->W0 = W;
+  c->w_cap_entries = W.cap;
   AL(c->d_cbpool, P.cb_total);
-  AL(c->d_red, 8);
+  AL(c->d_red, 6 * kMaxShifts);
   AL(c->d_flops, KC_COUNT + 1);
   if (cudaMemset(c->d_flops, 0, sizeof(unsigned long long) * (KC_COUNT + 1)) != cudaSuccess) { kep_destroy(c); return KEP_ERR_CUDA; }
   AL(c->d_bnew, P.n); AL(c->d_xnew, P.n);
@@ -510,7 +689,7 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   st = setup_memory(c);
   if (st != KEP_OK) { kep_destroy(c); return st; }
   if (cudaMallocHost(reinterpret_cast<void**>(&c->h_done), sizeof(int32_t) * ent) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(long long) * 8) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&c->h_red), sizeof(long long) * 6 * kMaxShifts) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&c->h_df_err), sizeof(int32_t)) != cudaSuccess) {
     kep_destroy(c);
     return KEP_ERR_NOMEM;
@@ -826,10 +1005,70 @@ kep_status kep_spmv(kep_ctx* c, const double* x, double* ax, double* bx, int ptr
 
 kep_status kep_factor_multi(kep_ctx* c, const double* sigmas, int32_t ns, kep_inertia* out) {
   if (!c || !sigmas || !out || ns < 1) return KEP_ERR_INVALID;
-  for (int32_t i = 0; i < ns; ++i) {
-    const kep_status st = kep_factor(c, sigmas[i], &out[i]);
-    if (st != KEP_OK && st != KEP_ERR_SINGULAR) return st;
+  int G = ns > 1 ? multi_group(c, ns) : 1;
+  if (G > 1) {
+    const int ngroups = (ns + G - 1) / G;
+    G = (ns + ngroups - 1) / ngroups;              // groups of (nearly) equal size
   }
+  if (G <= 1) {
+    for (int32_t i = 0; i < ns; ++i) {
+      const kep_status st = kep_factor(c, sigmas[i], &out[i]);
+      if (st != KEP_OK && st != KEP_ERR_SINGULAR) return st;
+    }
+    return KEP_OK;
+  }
+  for (int attempt = 0;; ++attempt) {
+    bool redo = false;
+    for (int32_t q0 = 0; q0 < ns && !redo; q0 += G) {
+      const int gs = static_cast<int>(std::min<int32_t>(G, ns - q0));
+      KEP_TRY(alloc_slot(c, 0));
+      const kep_status ms = ensure_multi(c, gs);
+      if (ms == KEP_ERR_NOMEM && q0 == 0) {         // no room after all: one shift at a time
+        cudaGetLastError();
+        for (int32_t i = 0; i < ns; ++i) {
+          const kep_status st = kep_factor(c, sigmas[i], &out[i]);
+          if (st != KEP_OK && st != KEP_ERR_SINGULAR) return st;
+        }
+        return KEP_OK;
+      }
+      KEP_TRY(ms);
+      FactorSlot* slots[kMaxShifts];
+      double* pools[kMaxShifts];
+      double* p21[kMaxShifts];
+      double ca[kMaxShifts], cb[kMaxShifts];
+      kep_inertia in[kMaxShifts];
+      int bits[kMaxShifts];
+      for (int j = 0; j < gs; ++j) {
+        const bool last = j == gs - 1;             // the last shift ends in the public slot
+        slots[j] = last ? &c->slot[0] : &c->mslot[j];
+        pools[j] = last ? c->d_cbpool : c->mpool[j];
+        p21[j] = last ? c->W.P21 : c->mp21[j];
+        ca[j] = 1.0;
+        cb[j] = -sigmas[q0 + j];
+        bits[j] = 0;
+      }
+      KEP_TRY(factor_set(c, gs, slots, pools, p21, ca, cb, in, bits));
+      for (int j = 0; j < gs; ++j) redo = redo || (bits[j] & ST_POOL);
+      if (redo) break;
+      KEP_TRY(record_slot(c, 0, bits[gs - 1]));
+      for (int j = 0; j < gs; ++j) {
+        out[q0 + j] = in[j];
+        kep_status st = finish_slot(c, *slots[j], in[j], bits[j]);
+        if (j == gs - 1) c->slot_zero[0] = c->slot[0].valid ? in[j].zero : 0;
+        st = herm_counts(c, st, &out[q0 + j]);
+        if (st != KEP_OK && st != KEP_ERR_SINGULAR) return st;
+      }
+    }
+    if (!redo) return KEP_OK;
+    if (attempt >= 4) return KEP_ERR_POOL;
+    KEP_TRY(replan(c, c->plan.slack_base * 4));
+  }
+}
+
+kep_status kep_set_graphs(kep_ctx* c, int enable) {
+  if (!c) return KEP_ERR_INVALID;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return KEP_ERR_CUDA;
+  c->graphs.enabled = enable != 0;
   return KEP_OK;
 }
 
@@ -874,6 +1113,8 @@ kep_status kep_get_timing(kep_ctx* c, kep_timing* out, int reset) {
 void kep_destroy(kep_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  c->graphs.clear();
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   for (void* p : c->allocs) cudaFree(p);
   for (void* p : c->mem_allocs) cudaFree(p);
   if (c->h_done) cudaFreeHost(c->h_done);

@@ -28,11 +28,6 @@ namespace {
 constexpr int kTile = 64;          // Schur-update tile edge
 constexpr int kRowTile = 64;       // rows per CTA in the row-parallel kernels
 
-struct Batch {
-  const int32_t* lf;   // fronts of the level
-  int32_t e0;          // first entry of this batch within the level
-};
-
 KEP_D int32_t children_delays(const FrontTables& T, const FactorSlot& S, int32_t t, bool& bad) {
   int32_t d = 0;
   for (int32_t c = T.child_ptr[t]; c < T.child_ptr[t + 1]; ++c) {
@@ -46,9 +41,12 @@ KEP_D int32_t children_delays(const FrontTables& T, const FactorSlot& S, int32_t
 // ------------------------------------------------------------------------------------------
 // assembly
 // ------------------------------------------------------------------------------------------
-__global__ void lf_init_kernel(FrontTables T, FactorSlot S, double* cbpool, LargeWork W, Batch B) {
+__global__ void lf_init_kernel(FrontTables T, SlotSet SS, LargeWork W, Batch B) {
   const int32_t b = B.e0 + blockIdx.y;
   const int32_t t = B.lf[b];
+  const int32_t g = entry_shift(B, b);
+  const FactorSlot& S = SS.s[g];
+  double* const cbpool = SS.cbpool[g];
   bool bad = false;
   const int32_t d_in = children_delays(T, S, t, bad);
   if (d_in > T.m_alloc[t] - T.m_sym[t]) bad = true;
@@ -93,9 +91,13 @@ __global__ void lf_init_kernel(FrontTables T, FactorSlot S, double* cbpool, Larg
   }
 }
 
-__global__ void lf_scatter_kernel(FrontTables T, FactorSlot S, double* cbpool, Batch B,
-                                  double ca, double cb) {
-  const int32_t t = B.lf[B.e0 + blockIdx.y];
+__global__ void lf_scatter_kernel(FrontTables T, SlotSet SS, Batch B) {
+  const int32_t b = B.e0 + blockIdx.y;
+  const int32_t t = B.lf[b];
+  const int32_t g = entry_shift(B, b);
+  const FactorSlot& S = SS.s[g];
+  double* const cbpool = SS.cbpool[g];
+  const double ca = S.ca, cb = S.cb;
   const int32_t d_in = S.d_in[t];
   if (d_in < 0) return;
   const FrontView v = front_view(T, S, cbpool, t, d_in);
@@ -109,8 +111,12 @@ __global__ void lf_scatter_kernel(FrontTables T, FactorSlot S, double* cbpool, B
 
 // Extend-add of the s-th child of every front in the batch (one launch per child slot keeps
 // the additions of different children to one parent entry in a fixed order).
-__global__ void lf_extend_kernel(FrontTables T, FactorSlot S, double* cbpool, Batch B, int32_t s) {
-  const int32_t t = B.lf[B.e0 + blockIdx.y];
+__global__ void lf_extend_kernel(FrontTables T, SlotSet SS, Batch B, int32_t s) {
+  const int32_t b = B.e0 + blockIdx.y;
+  const int32_t t = B.lf[b];
+  const int32_t g = entry_shift(B, b);
+  const FactorSlot& S = SS.s[g];
+  double* const cbpool = SS.cbpool[g];
   const int32_t d_in = S.d_in[t];
   if (d_in < 0) return;
   const int32_t c0 = T.child_ptr[t];
@@ -131,11 +137,76 @@ __global__ void lf_extend_kernel(FrontTables T, FactorSlot S, double* cbpool, Ba
 }
 
 // ------------------------------------------------------------------------------------------
-// pivoting panel: Bunch-Kaufman on the w x w diagonal block (one warp)
+// move a failed pivot to the end: symmetric interchange of fully-summed positions a < z of the
+// front (both < p, so every touched entry lives in the L storage), with its row bookkeeping
 // ------------------------------------------------------------------------------------------
-constexpr int kPanelThreads = 128;   // the pivot search runs in warp 0, the block updates in all four
+KEP_D void sym_swap_front(double* L, int64_t ld, int32_t m, int32_t a, int32_t z, int32_t* rv, int32_t* ap) {
+  if (a == z) return;
+  if (a > z) { int32_t tmp = a; a = z; z = tmp; }
+  for (int32_t c = threadIdx.x; c < a; c += blockDim.x) {        // rows a and z of earlier columns
+    double* col = L + static_cast<int64_t>(c) * ld;
+    double x = col[a]; col[a] = col[z]; col[z] = x;
+  }
+  for (int32_t c = a + 1 + threadIdx.x; c < z; c += blockDim.x) { // (c, a) <-> (z, c)
+    double* pa = L + static_cast<int64_t>(a) * ld + c;
+    double* pz = L + static_cast<int64_t>(c) * ld + z;
+    double x = *pa; *pa = *pz; *pz = x;
+  }
+  for (int32_t r = z + 1 + threadIdx.x; r < m; r += blockDim.x) { // (r, a) <-> (r, z)
+    double* pa = L + static_cast<int64_t>(a) * ld + r;
+    double* pz = L + static_cast<int64_t>(z) * ld + r;
+    double x = *pa; *pa = *pz; *pz = x;
+  }
+  if (threadIdx.x == 0) {
+    double* da = L + static_cast<int64_t>(a) * ld + a;
+    double* dz = L + static_cast<int64_t>(z) * ld + z;
+    double x = *da; *da = *dz; *dz = x;
+    int32_t v = rv[a]; rv[a] = rv[z]; rv[z] = v;
+    v = ap[a]; ap[a] = ap[z]; ap[z] = v;
+  }
+  __syncthreads();
+}
 
-__global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, FactorSlot S, LargeWork W,
+// The previous step's bookkeeping, run by the panel kernel before its block: a front that passes
+// its remaining columns to the parent finishes (its window flush has run), and a pending move of a
+// failed pivot (one or two columns) to the end of the fully-summed range is carried out.
+// Returns true when the front has finished.
+KEP_D bool pending_swap(const FrontTables& T, const FactorSlot& S, const LargeWork& W, int32_t b, int32_t t) {
+  if (W.finish[b]) {
+    __syncthreads();
+    if (threadIdx.x == 0) { W.done[b] = 1; W.finish[b] = 0; }
+    return true;
+  }
+  const int32_t nf = W.swap[b];
+  if (nf == 0) return false;
+  const int32_t d_in = S.d_in[t];
+  const int32_t m = T.m_sym[t] + d_in, p = T.p_sym[t] + d_in;
+  const int32_t k = W.k[b];
+  double* L = S.F + T.front_off[t];
+  const int64_t ld = T.m_alloc[t];
+  int32_t* rv = S.rowvar + T.vec_off[t];
+  int32_t* ap = S.apos + T.vec_off[t];
+  const int32_t a0 = k + W.pi[b * kPanel];
+  int32_t a1 = nf == 2 ? k + W.pi[b * kPanel + 1] : -1;
+  sym_swap_front(L, ld, m, a0, p - 1, rv, ap);
+  if (nf == 2) {
+    if (a1 == p - 1) a1 = a0;              // the first interchange moved it
+    sym_swap_front(L, ld, m, a1, p - 2, rv, ap);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) W.swap[b] = 0;
+  return false;
+}
+
+// ------------------------------------------------------------------------------------------
+// pivoting panel: Bunch-Kaufman on the w x w diagonal block.  The pivot search runs in warp 0; the
+// interchanges, the multipliers and the trailing update of the block use all eight warps (GB300
+// issues FP64 arithmetic at a small fraction of its FP32 rate, so the update is spread over every
+// scheduler of the SM: lane = row, warp = every eighth column)
+// ------------------------------------------------------------------------------------------
+constexpr int kPanelThreads = 256;
+
+__global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, SlotSet SS, LargeWork W,
                                                                  Batch B) {
   __shared__ double Bk[kPanel][kPanel + 1];
   __shared__ int32_t perm[kPanel];
@@ -144,17 +215,21 @@ __global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, 
   __shared__ int32_t s_kind, s_piv;
   const int32_t b = B.e0 + blockIdx.x;
   const int32_t tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  constexpr int32_t kWarps = kPanelThreads / 32;
   if (W.done[b]) return;
   const int32_t t = B.lf[b];
+  const FactorSlot& S = SS.s[entry_shift(B, b)];
+  if (pending_swap(T, S, W, b, t)) return;
   const int32_t d_in = S.d_in[t];
   const int32_t p = T.p_sym[t] + d_in;
   const int32_t k = W.k[b] + W.q[b];
   int32_t we = W.we[b];
-  if (k < p && (k >= we || W.reset[b])) we = min(k + kWindow, p);   // open a new pivot window
+  const bool open = k < p && (k >= we || W.reset[b]);
+  if (open) we = min(k + kWindow, p);   // open a new pivot window
   __syncthreads();
   if (tid == 0) {
     W.k[b] = k; W.q[b] = 0; W.flush[b] = 0;
-    if (k < p && (k >= W.we[b] || W.reset[b])) { W.ws[b] = k; W.we[b] = we; W.reset[b] = 0; }
+    if (open) { W.ws[b] = k; W.we[b] = we; W.reset[b] = 0; }
   }
   if (k >= p) {
     if (tid == 0) { W.done[b] = 1; S.nelim[t] = k; S.d_out[t] = p - k; W.w[b] = 0; }
@@ -163,13 +238,13 @@ __global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, 
   const int32_t w = min(kPanel, we - k);
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
-  // the block's lower triangle, mirrored into a full symmetric copy
-  for (int32_t e = tid; e < kPanel * kPanel; e += kPanelThreads) {
-    const int32_t c = e / kPanel, r = e % kPanel;
-    if (r >= c && r < w && c < w) {
-      const double val = L[static_cast<int64_t>(k + c) * ld + k + r];
-      Bk[r][c] = val;
-      Bk[c][r] = val;
+  // the block's lower triangle, mirrored into a full symmetric copy: lane = row, warp = every
+  // eighth column (each column one coalesced load)
+  for (int32_t c = warp; c < w; c += kWarps) {
+    if (lane >= c && lane < w) {
+      const double val = L[static_cast<int64_t>(k + c) * ld + k + lane];
+      Bk[lane][c] = val;
+      Bk[c][lane] = val;
     }
   }
   if (tid < kPanel) perm[tid] = tid;
@@ -180,14 +255,12 @@ __global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, 
     if (warp == 0) {
       double v = (lane > kk && lane < w) ? fabs(Bk[lane][kk]) : -1.0;
       double lam = warp_max(v);
-      unsigned ball = __ballot_sync(0xffffffffu, v == lam && lane > kk && lane < w);
-      int32_t r = ball ? __ffs(ball) - 1 : -1;
+      const unsigned ball = __ballot_sync(0xffffffffu, v == lam && lane > kk && lane < w);
+      const int32_t r = ball ? __ffs(ball) - 1 : -1;
       if (lam < 0) lam = 0.0;
-      double akk = fabs(Bk[kk][kk]);
+      const double akk = fabs(Bk[kk][kk]);
       int32_t kind = 1, piv = kk;          // kind 1: 1x1 at piv; kind 2: 2x2 (kk, piv)
-      if (lam == 0.0 || akk >= kBKAlpha * lam) {
-        kind = 1; piv = kk;
-      } else {
+      if (!(lam == 0.0 || akk >= kBKAlpha * lam) && r >= 0) {   // (r < 0 only for NaN entries)
         double vr = (lane >= kk && lane < w && lane != r) ? fabs(Bk[lane][r]) : -1.0;
         double sig = warp_max(vr);
         if (sig < 0) sig = 0.0;
@@ -201,42 +274,42 @@ __global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, 
     const int32_t kind = s_kind, piv = s_piv;
     const int32_t dst = kind == 1 ? kk : kk + 1;
     if (piv != dst) {   // symmetric interchange of dst and piv in the full block copy
-      if (tid < w) { double tmp = Bk[tid][dst]; Bk[tid][dst] = Bk[tid][piv]; Bk[tid][piv] = tmp; }
+      if (tid < w) { const double tmp = Bk[tid][dst]; Bk[tid][dst] = Bk[tid][piv]; Bk[tid][piv] = tmp; }
       __syncthreads();
-      if (tid < w) { double tmp = Bk[dst][tid]; Bk[dst][tid] = Bk[piv][tid]; Bk[piv][tid] = tmp; }
-      if (tid == 0) { int32_t tp = perm[dst]; perm[dst] = perm[piv]; perm[piv] = tp; }
+      if (tid < w) { const double tmp = Bk[dst][tid]; Bk[dst][tid] = Bk[piv][tid]; Bk[piv][tid] = tmp; }
+      if (tid == 0) { const int32_t tp = perm[dst]; perm[dst] = perm[piv]; perm[piv] = tp; }
       __syncthreads();
     }
     const int32_t c0 = kk + kind;         // first column of the trailing block
     if (kind == 1) {
       const double d = Bk[kk][kk];
-      if (tid > kk && tid < w) lv0[tid] = d != 0.0 ? Bk[tid][kk] / d : 0.0;
+      if (tid >= c0 && tid < w) lv0[tid] = d != 0.0 ? Bk[tid][kk] / d : 0.0;
     } else {
       const double a = Bk[kk][kk], bb = Bk[kk + 1][kk], c2 = Bk[kk + 1][kk + 1];
       const double det = a * c2 - bb * bb;
-      if (tid > kk + 1 && tid < w) {
+      if (tid >= c0 && tid < w) {
         const double w0 = Bk[tid][kk], w1 = Bk[tid][kk + 1];
         lv0[tid] = (c2 * w0 - bb * w1) / det;
         lv1[tid] = (a * w1 - bb * w0) / det;
       }
     }
     __syncthreads();
-    // trailing update of the block, rows and columns [c0, w): thread (row lane, columns warp + 4j)
+    // trailing update of the block, rows and columns [c0, w)
     if (lane >= c0 && lane < w) {
       if (kind == 1) {
         const double l0 = lv0[lane];
-        for (int32_t c = c0 + warp; c < w; c += kPanelThreads / 32) Bk[lane][c] -= l0 * Bk[c][kk];
+        for (int32_t c = c0 + warp; c < w; c += kWarps) Bk[lane][c] -= l0 * Bk[c][kk];
       } else {
         const double l0 = lv0[lane], l1 = lv1[lane];
-        for (int32_t c = c0 + warp; c < w; c += kPanelThreads / 32) Bk[lane][c] -= l0 * Bk[c][kk] + l1 * Bk[c][kk + 1];
+        for (int32_t c = c0 + warp; c < w; c += kWarps) Bk[lane][c] -= l0 * Bk[c][kk] + l1 * Bk[c][kk + 1];
       }
     }
     __syncthreads();
     if (kind == 1) {
-      if (tid > kk && tid < w) { Bk[tid][kk] = lv0[tid]; Bk[kk][tid] = lv0[tid]; }
+      if (tid >= c0 && tid < w) { Bk[tid][kk] = lv0[tid]; Bk[kk][tid] = lv0[tid]; }
       if (tid == 0) { dd[kk] = Bk[kk][kk]; de[kk] = 0.0; pt[kk] = 1; }
     } else {
-      if (tid > kk + 1 && tid < w) {
+      if (tid >= c0 && tid < w) {
         Bk[tid][kk] = lv0[tid]; Bk[kk][tid] = lv0[tid];
         Bk[tid][kk + 1] = lv1[tid]; Bk[kk + 1][tid] = lv1[tid];
       }
@@ -270,7 +343,7 @@ __global__ void __launch_bounds__(kPanelThreads) lf_panel_kernel(FrontTables T, 
 // L21 rows and column maxima: row i solves y L11^T = f (f: row i of the permuted block columns),
 // then l = y D^{-1}
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, FactorSlot S, LargeWork W,
+__global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, SlotSet SS, LargeWork W,
                                                           Batch B) {
   __shared__ double L11s[kPanel][kPanel + 1];
   __shared__ double dd[kPanel], r0[kPanel], r1[kPanel], r2[kPanel];
@@ -280,6 +353,8 @@ __global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, FactorS
   const int32_t b = B.e0 + blockIdx.y;
   if (W.done[b]) return;
   const int32_t t = B.lf[b];
+  const int32_t g = entry_shift(B, b);
+  const FactorSlot& S = SS.s[g];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in;
   const int32_t k = W.k[b], w = W.w[b];
@@ -311,7 +386,7 @@ __global__ void __launch_bounds__(kRowTile) lf_l21_kernel(FrontTables T, FactorS
   __syncthreads();
   const double* L = S.F + T.front_off[t];
   const int64_t ld = T.m_alloc[t];
-  double* P21 = W.P21 + W.p21_off[t];
+  double* P21 = SS.P21[g] + W.p21_off[t];
   const int64_t ldp = T.m_alloc[t];
   double cm[kPanel];
 #pragma unroll
@@ -396,7 +471,7 @@ KEP_D int32_t accepted_count(const LargeWork& W, int32_t b, int32_t w) {
 // ------------------------------------------------------------------------------------------
 // apply: permute the block, write accepted L columns and D, restore rejected columns
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot S, LargeWork W,
+__global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, SlotSet SS, LargeWork W,
                                                        Batch B) {
   __shared__ double Bo[kPanel][kPanel + 1];
   __shared__ double Fo[kPanel][kRowTile + 1];
@@ -405,6 +480,8 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
   const int32_t b = B.e0 + blockIdx.y;
   if (W.done[b]) return;
   const int32_t t = B.lf[b];
+  const int32_t g = entry_shift(B, b);
+  const FactorSlot& S = SS.s[g];
   const int32_t d_in = S.d_in[t];
   const int32_t m = T.m_sym[t] + d_in, p = T.p_sym[t] + d_in;
   const int32_t k = W.k[b], w = W.w[b];
@@ -446,7 +523,7 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
   const int32_t rows = m - k - w;
   const int32_t nB = (rows + kRowTile - 1) / kRowTile;
   const double* L11 = W.L11 + static_cast<int64_t>(b) * kPanel * kPanel;
-  const double* P21 = W.P21 + W.p21_off[t];
+  const double* P21 = SS.P21[g] + W.p21_off[t];
   const int64_t ldp = T.m_alloc[t];
   for (int32_t item = blockIdx.x; item < 1 + nA + nB; item += gridDim.x) {
     if (item == 0) {
@@ -535,65 +612,6 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, FactorSlot
 }
 
 // ------------------------------------------------------------------------------------------
-// move a failed pivot to the end: symmetric interchange of fully-summed positions a < z of the
-// front (both < p, so every touched entry lives in the L storage), with its row bookkeeping
-// ------------------------------------------------------------------------------------------
-KEP_D void sym_swap_front(double* L, int64_t ld, int32_t m, int32_t a, int32_t z, int32_t* rv, int32_t* ap) {
-  if (a == z) return;
-  if (a > z) { int32_t tmp = a; a = z; z = tmp; }
-  for (int32_t c = threadIdx.x; c < a; c += blockDim.x) {        // rows a and z of earlier columns
-    double* col = L + static_cast<int64_t>(c) * ld;
-    double x = col[a]; col[a] = col[z]; col[z] = x;
-  }
-  for (int32_t c = a + 1 + threadIdx.x; c < z; c += blockDim.x) { // (c, a) <-> (z, c)
-    double* pa = L + static_cast<int64_t>(a) * ld + c;
-    double* pz = L + static_cast<int64_t>(c) * ld + z;
-    double x = *pa; *pa = *pz; *pz = x;
-  }
-  for (int32_t r = z + 1 + threadIdx.x; r < m; r += blockDim.x) { // (r, a) <-> (r, z)
-    double* pa = L + static_cast<int64_t>(a) * ld + r;
-    double* pz = L + static_cast<int64_t>(z) * ld + r;
-    double x = *pa; *pa = *pz; *pz = x;
-  }
-  if (threadIdx.x == 0) {
-    double* da = L + static_cast<int64_t>(a) * ld + a;
-    double* dz = L + static_cast<int64_t>(z) * ld + z;
-    double x = *da; *da = *dz; *dz = x;
-    int32_t v = rv[a]; rv[a] = rv[z]; rv[z] = v;
-    v = ap[a]; ap[a] = ap[z]; ap[z] = v;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(256) lf_swap_kernel(FrontTables T, FactorSlot S, LargeWork W, Batch B) {
-  const int32_t b = B.e0 + blockIdx.x;
-  if (threadIdx.x == 0) W.flush[b] = 0;    // this step's flush (if any) has run
-  if (W.done[b]) return;
-  if (W.finish[b]) {                       // the window flush of a front that delays the rest ran
-    if (threadIdx.x == 0) { W.done[b] = 1; W.finish[b] = 0; }
-    return;
-  }
-  const int32_t nf = W.swap[b];
-  if (nf == 0) return;
-  const int32_t t = B.lf[b];
-  const int32_t d_in = S.d_in[t];
-  const int32_t m = T.m_sym[t] + d_in, p = T.p_sym[t] + d_in;
-  const int32_t k = W.k[b];
-  double* L = S.F + T.front_off[t];
-  const int64_t ld = T.m_alloc[t];
-  int32_t* rv = S.rowvar + T.vec_off[t];
-  int32_t* ap = S.apos + T.vec_off[t];
-  const int32_t a0 = k + W.pi[b * kPanel];
-  int32_t a1 = nf == 2 ? k + W.pi[b * kPanel + 1] : -1;
-  sym_swap_front(L, ld, m, a0, p - 1, rv, ap);
-  if (nf == 2) {
-    if (a1 == p - 1) a1 = a0;              // the first interchange moved it
-    sym_swap_front(L, ld, m, a1, p - 2, rv, ap);
-  }
-  if (threadIdx.x == 0) W.swap[b] = 0;
-}
-
-// ------------------------------------------------------------------------------------------
 // Schur update of the trailing matrix: C(i, j) -= sum_c L(i, c) (L D)(j, c) over the q accepted
 // pivots, for s = k + q <= j <= i < m.  64 x 64 tiles, 256 threads with 4 x 4 register tiles.
 // ------------------------------------------------------------------------------------------
@@ -622,8 +640,8 @@ struct Part {
 // 64 x 64 tiles, 256 threads with 4 x 4 FP64 register tiles, the pivot range in chunks of 32.
 // R: arithmetic of the tiles (double, or float for the reduced-precision factorization mode)
 template <bool WINDOW, typename R>
-__global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot S, double* cbpool,
-                                                       LargeWork W, Batch B, unsigned long long* flops) {
+__global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, SlotSet SS, LargeWork W, Batch B,
+                                                       unsigned long long* flops) {
   __shared__ R Ai[kPanel][kTile + 1];
   __shared__ R Wj[kPanel][kTile + 1];
   const int32_t b = B.e0 + blockIdx.y;
@@ -638,8 +656,10 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot
     c0 = W.ws[b]; c1 = W.kend[b]; s = W.we[b];
   }
   const int32_t t = B.lf[b];
+  const int32_t g = entry_shift(B, b);
+  const FactorSlot& S = SS.s[g];
   const int32_t d_in = S.d_in[t];
-  const FrontView v = front_view(T, S, cbpool, t, d_in);
+  const FrontView v = front_view(T, S, SS.cbpool[g], t, d_in);
   if (!WINDOW) ce = v.m;
   if (c1 <= c0 || s >= ce) return;
   Part P;
@@ -730,7 +750,9 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, FactorSlot
   }
 }
 
-__global__ void reduce_inertia_kernel(FactorSlot S, int32_t nfronts, long long* out) {
+__global__ void reduce_inertia_kernel(SlotSet SS, int32_t nfronts, long long* out) {
+  const FactorSlot& S = SS.s[blockIdx.x];
+  out += 6 * blockIdx.x;
   // out: neg, zero, pos, delayed (sum of d_out over roots is 0; delayed = sum of all d_out)
   long long a = 0, z = 0, c = 0, d = 0;
   for (int32_t t = threadIdx.x; t < nfronts; t += blockDim.x) {
@@ -764,56 +786,62 @@ static int grid_cap(int64_t want, int64_t cap) {
   return static_cast<int>(want < cap ? want : cap);
 }
 
-kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, int* status_bits) {
+kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_inertia* out, int* status_bits) {
   const Plan& P = *F.plan;
   cudaStream_t st = F.stream;
-  int32_t init_status[2] = {0, -1};
-  if (cudaMemcpyAsync(F.S.status, init_status, sizeof(init_status), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return KEP_ERR_CUDA;
+  const int G = F.G;
+  if (F.emul_min > 0) emul_init();
+  for (int g = 0; g < G; ++g) {
+    const int32_t init_status[2] = {0, -1};
+    if (cudaMemcpyAsync(F.SS.s[g].status, init_status, sizeof(init_status), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    F.SS.s[g].ca = ca[g];
+    F.SS.s[g].cb = cb[g];
+  }
   const int target = F.num_sms * 8;
   for (int32_t l = 0; l < P.nlevels; ++l) {
-    const int32_t lb = P.level_ptr[l], le = P.level_ptr[l + 1];
-    const int32_t width = le - lb;
-    // batches: each front with a large order alone, the rest together (chunks of 65535)
+    // the level's entries: its fronts in decreasing order, each G times (one per shift)
+    const int32_t lb = P.level_ptr[l] * G;
+    const int32_t width = (P.level_ptr[l + 1] - P.level_ptr[l]) * G;
+    const int32_t* lfh = F.h_ent_front + lb;
+    // batches: the tensor-core fronts in groups, each front of a large order alone (with its
+    // shifts), the rest together (chunks of 65535)
     int32_t e = 0;
     while (e < width) {
-      int32_t t0 = P.level_fronts[lb + e];
+      const int32_t t0 = lfh[e];
       int32_t e1;
       const bool emul = F.emul_min > 0 && P.m_alloc[t0] >= F.emul_min;
       if (emul) {
-        e1 = F.h_emul_end[lb + e];   // the level's fronts on the tensor-core path, batched
+        e1 = F.h_emul_end[lb + e];   // the level's entries on the tensor-core path, batched
       } else if (P.m_alloc[t0] > 4096) {
-        e1 = e + 1;
+        e1 = std::min(e + G, width);
       } else {
-        e1 = e + 1;                  // the rest of the level (sorted by size), stopping at a front
-        while (e1 < width && e1 - e < 65535 &&   // that must go alone
-               !(F.emul_min > 0 && P.m_alloc[P.level_fronts[lb + e1]] >= F.emul_min))
+        e1 = e + 1;                  // the rest of the level (sorted by size), stopping at an
+        while (e1 < width && e1 - e < 65535 &&   // entry that must go alone
+               !(F.emul_min > 0 && P.m_alloc[lfh[e1]] >= F.emul_min))
           ++e1;
       }
       const int32_t nb = e1 - e;
-      Batch B{F.d_level_fronts + lb, e};
+      Batch B{F.d_ent_front + lb, F.d_ent_shift ? F.d_ent_shift + lb : nullptr, e};
       int64_t max_m = 0, max_p = 0, max_c = 0, max_ent = 0;
+      int32_t maxch = 0;
       for (int32_t i = e; i < e1; ++i) {
-        int32_t t = P.level_fronts[lb + i];
+        const int32_t t = lfh[i];
         max_m = std::max<int64_t>(max_m, P.m_alloc[t]);
         max_p = std::max<int64_t>(max_p, P.p_alloc[t]);
         max_c = std::max<int64_t>(max_c, P.m_sym[t] - P.p_sym[t]);
         max_ent = std::max<int64_t>(max_ent, P.ent_ptr[t + 1] - P.ent_ptr[t]);
-      }
-      const int gx_cols = grid_cap(std::max(max_p, max_c), std::max<int64_t>(1, (target + nb - 1) / nb));
-      KEP_LAUNCH(F.timer, KC_ASSEMBLE, st, lf_init_kernel<<<dim3(gx_cols, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B));
-      KEP_LAUNCH(F.timer, KC_ASSEMBLE, st,
-                 lf_scatter_kernel<<<dim3(grid_cap((max_ent + 255) / 256, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 256, 0, st>>>(
-                     F.T, F.S, F.cbpool, B, ca, cb));
-      int32_t maxch = 0;
-      for (int32_t i = e; i < e1; ++i) {
-        int32_t t = P.level_fronts[lb + i];
         maxch = std::max(maxch, P.child_ptr[t + 1] - P.child_ptr[t]);
       }
+      const int gx_cols = grid_cap(std::max(max_p, max_c), std::max<int64_t>(1, (target + nb - 1) / nb));
+      KEP_LAUNCH(F.timer, KC_ASSEMBLE, st, lf_init_kernel<<<dim3(gx_cols, nb), 256, 0, st>>>(F.T, F.SS, F.W, B));
+      KEP_LAUNCH(F.timer, KC_ASSEMBLE, st,
+                 lf_scatter_kernel<<<dim3(grid_cap((max_ent + 255) / 256, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 256, 0, st>>>(
+                     F.T, F.SS, B));
       for (int32_t s = 0; s < maxch; ++s)
         KEP_LAUNCH(F.timer, KC_ASSEMBLE, st,
                    lf_extend_kernel<<<dim3(grid_cap(max_m, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 128, 0, st>>>(
-                       F.T, F.S, F.cbpool, B, s));
+                       F.T, F.SS, B, s));
       const int64_t rowtiles = (max_m + kRowTile - 1) / kRowTile;
       // CTAs per front: enough for the largest front of the batch (fronts of one level differ in
       // size by up to ~10x; CTAs beyond a front's own work return at once)
@@ -831,38 +859,76 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       const int64_t blocks = (max_p + kPanel - 1) / kPanel + 2;
       const int64_t step_cap = 64 + 2 * blocks * blocks;
       int64_t steps_done = 0;
+      // one pass: `steps` pivot steps (panel, L21 rows, apply, in-window and trailing updates),
+      // then one more panel call that finalises fronts whose last block was accepted
+      auto issue_pass = [&](cudaStream_t sx, int64_t nsteps) {
+        for (int64_t it = 0; it < nsteps; ++it) {
+          KEP_LAUNCH(F.timer, KC_PANEL, sx, lf_panel_kernel<<<nb, kPanelThreads, 0, sx>>>(F.T, F.SS, F.W, B));
+          KEP_LAUNCH(F.timer, KC_L21, sx, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, sx>>>(F.T, F.SS, F.W, B));
+          KEP_LAUNCH(F.timer, KC_APPLY, sx, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, sx>>>(F.T, F.SS, F.W, B));
+          if (emul) {
+            // in-window and trailing updates on the tensor cores (FP64-accurate splitting)
+            launch_emul_update(true, F.T, F.SS, F.W, B, nb, F.emul_ws, F.d_emul_off + lb + e, max_m, sx, F.num_sms,
+                               F.timer, F.flops);
+            launch_emul_update(false, F.T, F.SS, F.W, B, nb, F.emul_ws, F.d_emul_off + lb + e, max_m, sx, F.num_sms,
+                               F.timer, F.flops);
+          } else if (F.fp32_schur) {
+            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
+                       lf_schur_kernel<true, float><<<dim3(gx_win, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
+                                                                                     F.flops + KC_UPDATE));
+            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
+                       lf_schur_kernel<false, float><<<dim3(gx_upd, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
+                                                                                       F.flops + KC_UPDATE));
+          } else {
+            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
+                       lf_schur_kernel<true, double><<<dim3(gx_win, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
+                                                                                      F.flops + KC_UPDATE));
+            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
+                       lf_schur_kernel<false, double><<<dim3(gx_upd, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
+                                                                                        F.flops + KC_UPDATE));
+          }
+        }
+        KEP_LAUNCH(F.timer, KC_PANEL, sx, lf_panel_kernel<<<nb, kPanelThreads, 0, sx>>>(F.T, F.SS, F.W, B));
+      };
       while (true) {
         if (steps_done > step_cap) return KEP_ERR_NOT_CONVERGED;
         steps_done += steps;
-        for (int64_t it = 0; it < steps; ++it) {
-          KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, kPanelThreads, 0, st>>>(F.T, F.S, F.W, B));
-          KEP_LAUNCH(F.timer, KC_L21, st, lf_l21_kernel<<<dim3(gx_rows, nb), kRowTile, 0, st>>>(F.T, F.S, F.W, B));
-          KEP_LAUNCH(F.timer, KC_APPLY, st, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, st>>>(F.T, F.S, F.W, B));
-          if (emul) {
-            // in-window and trailing updates on the tensor cores (FP64-accurate splitting)
-            launch_emul_update(true, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, nb, F.emul_ws, F.d_emul_off + lb + e,
-                               max_m, st, F.num_sms, F.timer, F.flops);
-            launch_emul_update(false, F.T, F.S, F.cbpool, F.W, B.lf, B.e0, nb, F.emul_ws, F.d_emul_off + lb + e,
-                               max_m, st, F.num_sms, F.timer, F.flops);
-          } else if (F.fp32_schur) {
-            KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                       lf_schur_kernel<true, float><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
-                                                                                     F.flops + KC_UPDATE));
-            KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                       lf_schur_kernel<false, float><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
-                                                                                       F.flops + KC_UPDATE));
-          } else {
-            KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                       lf_schur_kernel<true, double><<<dim3(gx_win, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
-                                                                                      F.flops + KC_UPDATE));
-            KEP_LAUNCH(F.timer, KC_UPDATE, st,
-                       lf_schur_kernel<false, double><<<dim3(gx_upd, nb), 256, 0, st>>>(F.T, F.S, F.cbpool, F.W, B,
-                                                                                        F.flops + KC_UPDATE));
+        if (F.graphs && F.graphs->enabled && F.capture_stream && !F.timer->enabled) {
+          // the pass as a CUDA graph: captured once per batch, pass length and storage, replayed
+          const std::vector<uint64_t> key = {
+              static_cast<uint64_t>(l), static_cast<uint64_t>(e), static_cast<uint64_t>(nb),
+              static_cast<uint64_t>(steps), static_cast<uint64_t>(G), static_cast<uint64_t>(F.emul_min),
+              (emul ? 1ull : 0ull) | (F.fp32_schur ? 2ull : 0ull),
+              reinterpret_cast<uint64_t>(F.SS.s[0].F), reinterpret_cast<uint64_t>(F.SS.s[G - 1].F),
+              reinterpret_cast<uint64_t>(F.W.done), reinterpret_cast<uint64_t>(F.emul_ws),
+              reinterpret_cast<uint64_t>(F.d_emul_off), reinterpret_cast<uint64_t>(F.SS.P21[0])};
+          GraphEntry* ge = F.graphs->find(key);
+          if (!ge) {
+            GraphEntry ne;
+            int64_t before[KC_COUNT];
+            for (int c = 0; c < KC_COUNT; ++c) before[c] = F.timer->launches[c];
+            // captured on the context's own capture stream (the legacy default stream, which a
+            // caller may use, cannot be captured); the graph is then launched on st
+            cudaStream_t cs = F.capture_stream;
+            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return KEP_ERR_CUDA;
+            issue_pass(cs, steps);
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) return KEP_ERR_CUDA;
+            const cudaError_t ie = cudaGraphInstantiate(&ne.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) return KEP_ERR_CUDA;
+            for (int c = 0; c < KC_COUNT; ++c) {
+              ne.launches[c] = F.timer->launches[c] - before[c];
+              F.timer->launches[c] = before[c];
+            }
+            F.graphs->entries.emplace_back(key, ne);
+            ge = &F.graphs->entries.back().second;
           }
-          KEP_LAUNCH(F.timer, KC_APPLY, st, lf_swap_kernel<<<nb, 256, 0, st>>>(F.T, F.S, F.W, B));
+          if (cudaGraphLaunch(ge->exec, st) != cudaSuccess) return KEP_ERR_CUDA;
+          for (int c = 0; c < KC_COUNT; ++c) F.timer->launches[c] += ge->launches[c];
+        } else {
+          issue_pass(st, steps);
         }
-        // one more panel call finalises fronts whose last block was accepted
-        KEP_LAUNCH(F.timer, KC_PANEL, st, lf_panel_kernel<<<nb, kPanelThreads, 0, st>>>(F.T, F.S, F.W, B));
         if (cudaMemcpyAsync(F.h_done, F.W.done + e, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
           return KEP_ERR_CUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;
@@ -875,17 +941,20 @@ kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, i
       e = e1;
     }
   }
-  KEP_LAUNCH(F.timer, KC_REDUCE, st, reduce_inertia_kernel<<<1, 1024, 0, st>>>(F.S, P.nfronts, F.d_red));
-  if (cudaMemcpyAsync(F.h_red, F.d_red, 6 * sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  KEP_LAUNCH(F.timer, KC_REDUCE, st, reduce_inertia_kernel<<<G, 1024, 0, st>>>(F.SS, P.nfronts, F.d_red));
+  if (cudaMemcpyAsync(F.h_red, F.d_red, 6 * G * sizeof(long long), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return KEP_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return KEP_ERR_CUDA;
   F.timer->collect();
   if (cudaGetLastError() != cudaSuccess) return KEP_ERR_CUDA;
-  out->neg = F.h_red[0];
-  out->zero = F.h_red[1];
-  out->pos = F.h_red[2];
-  out->delayed = F.h_red[3];
-  *status_bits = static_cast<int>(F.h_red[4]);
+  for (int g = 0; g < G; ++g) {
+    const long long* r = F.h_red + 6 * g;
+    out[g].neg = r[0];
+    out[g].zero = r[1];
+    out[g].pos = r[2];
+    out[g].delayed = r[3];
+    status_bits[g] = static_cast<int>(r[4]);
+  }
   return KEP_OK;
 }
 

@@ -49,6 +49,9 @@ struct kep_ctx {
   int64_t slot_zero[2] = {0, 0};
   double* d_cbpool = nullptr;
   kep::LargeWork W{};
+  kep::LargeWork W0{};              // W's entry arrays as allocated by kep_analyze (one shift)
+  kep::GraphCache graphs;           // step passes of the factorization as CUDA graphs
+  cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on
   long long* d_red = nullptr;
   unsigned long long* d_flops = nullptr;   // per kernel class (+1: FP64 work the tensor flush stands for)
   long long* h_red = nullptr;       // pinned
@@ -78,6 +81,12 @@ struct kep_ctx {
   int64_t df_items_cap[2] = {0, 0};
   int32_t* d_df_ctr = nullptr;          // 1 + 2 nlevels (in allocs)
   int32_t* d_df_flags = nullptr;        // in mem_allocs
+  int32_t* d_df_pcnt = nullptr;         // in mem_allocs, as many as the flags
+  int64_t df_nflags = 0;
+  std::vector<int64_t> df_part_base[2];
+  int64_t* d_df_part_base[2] = {nullptr, nullptr};   // in mem_allocs (nfronts each)
+  double* d_df_part = nullptr;          // in mem_allocs
+  int64_t df_part_cap = 0;
   int32_t* d_df_fbase = nullptr;        // in mem_allocs
   int32_t* h_df_err = nullptr;          // pinned
   int32_t df_epoch = 0;
@@ -86,9 +95,25 @@ struct kep_ctx {
   int64_t emul_min_front = 512;
   void* emul_ws = nullptr;          // tensor-core update workspace (in mem_allocs)
   int64_t emul_bytes = 0;           // its size
-  int64_t* d_emul_off = nullptr;    // per level position: workspace offset within its batch (in mem_allocs)
-  int64_t emul_min_planned = -1;    // min_front the batches below were formed for
-  std::vector<int32_t> h_emul_end;  // per level position starting a batch: the batch's end
+  // multisection: G shifts factored in the same launches (kep_factor_multi).  Shift G - 1 uses
+  // slot 0; shifts 0 .. G - 2 use their own slots, contribution-block pools and L21 workspaces
+  // (in mem_allocs).  Entry lists: per level, each front G times (front-major).
+  int32_t multi_cap = 0;            // shifts the extra resources serve (0: none)
+  kep::FactorSlot mslot[kep::kMaxShifts]{};
+  double* mpool[kep::kMaxShifts] = {};
+  double* mp21[kep::kMaxShifts] = {};
+  int32_t ent_G = 0;                // G the entry lists below were built for
+  int32_t* d_ent_front = nullptr;   // (in mem_allocs)
+  int8_t* d_ent_shift = nullptr;
+  std::vector<int32_t> h_ent_front;
+  int32_t w_cap_entries = 0;        // entries the LargeWork arrays hold
+  // tensor-core batches, per G (1 and the multisection G): workspace offsets per entry, batch ends
+  struct EmulPlan {
+    int64_t min_planned = -1;
+    int32_t G = 0;
+    std::vector<int32_t> h_end;
+    int64_t* d_off = nullptr;       // (in mem_allocs)
+  } emul_plan[2];
   // eigenpair driver state (owned by driver.cu)
   void* driver = nullptr;
   void driver_release();

@@ -10,6 +10,9 @@ namespace kep {
 #define KEP_HD __host__ __device__ __forceinline__
 #define KEP_D __device__ __forceinline__
 
+// shift of batch entry b (entries of a multisection step carry one; a single factorization: 0)
+KEP_D int32_t entry_shift(const Batch& B, int32_t b) { return B.sh ? B.sh[b] : 0; }
+
 // Element (i, j), i >= j, of a front stored as L storage (columns < p, ld = ldL) plus a
 // contribution block (columns >= p, c x c).
 struct FrontView {

@@ -224,25 +224,66 @@ struct LargeWork {
   int32_t cap;          // capacity (entries)
 };
 
+// The factorizations one launch sequence serves: shift g of a multisection step factors
+// ca[g] * A + cb[g] * B into slot s[g] with its own contribution-block pool and L21 workspace
+// (g = 0 only for a single factorization).
+constexpr int kMaxShifts = 8;
+struct SlotSet {
+  FactorSlot s[kMaxShifts];
+  double* cbpool[kMaxShifts];
+  double* P21[kMaxShifts];
+  int32_t n;
+};
+
+// Entries of one tree level's launches: entry b is front lf[b] of shift sh[b] (sh null: shift 0).
+struct Batch {
+  const int32_t* lf;
+  const int8_t* sh;
+  int32_t e0;           // first entry of this batch within the level
+};
+
+// CUDA graphs of the factorization's step passes (one per level batch and pass length), replayed
+// by later factorizations with the same storage; launch counts per class are replayed with them.
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches[KC_COUNT] = {};
+};
+struct GraphCache {
+  std::vector<std::pair<std::vector<uint64_t>, GraphEntry>> entries;
+  bool enabled = true;
+  GraphEntry* find(const std::vector<uint64_t>& key) {
+    for (auto& e : entries) if (e.first == key) return &e.second;
+    return nullptr;
+  }
+  void clear() {
+    for (auto& e : entries) if (e.second.exec) cudaGraphExecDestroy(e.second.exec);
+    entries.clear();
+  }
+};
+
 struct FactorLaunch {
   const Plan* plan;
   FrontTables T;
-  FactorSlot S;
-  double* cbpool;
+  SlotSet SS;
   LargeWork W;
-  const int32_t* d_level_fronts;
-  int32_t* h_done;          // pinned, >= max level width
-  long long* d_red;         // 6 entries
-  long long* h_red;         // pinned
+  int32_t G = 1;            // shifts: every level lists its fronts G times (front-major)
+  const int32_t* d_ent_front;   // per entry (level-major, G entries per front): the front
+  const int8_t* d_ent_shift;    //   and the shift (null for G = 1)
+  const int32_t* h_ent_front;   // host copy
+  int32_t* h_done;          // pinned, >= max level width x G
+  long long* d_red;         // 6 entries per shift
+  long long* h_red;         // pinned, 6 per shift
   cudaStream_t stream;
   int num_sms;
   Timer* timer;
   int64_t emul_min;         // fronts with m_alloc >= this use the tensor-core flush (0: never)
   bool fp32_schur = false;  // Schur tiles in FP32 arithmetic (reduced-precision factor for refined solves)
   void* emul_ws;            // its workspace
-  const int64_t* d_emul_off;      // per level position: byte offset of the front's workspace in its batch
-  const int32_t* h_emul_end;      // per level position starting a batch of such fronts: its end (level index)
+  const int64_t* d_emul_off;      // per entry: byte offset of the entry's workspace in its batch
+  const int32_t* h_emul_end;      // per entry starting a batch of such entries: its end (level-relative)
   unsigned long long* flops;   // per kernel class: algorithmic flops, counted on the device
+  GraphCache* graphs = nullptr;   // step passes as CUDA graphs (null: direct launches)
+  cudaStream_t capture_stream = nullptr;   // the stream the graphs are captured on
 };
 
 struct SolveLaunch {
@@ -267,20 +308,27 @@ struct SolveLaunch {
   int32_t* df_flags;          // per possible pivot block of every front (at df_fbase[front])
   const int32_t* df_fbase;
   int32_t epoch;              // this solve's number (flags compare against 2 epoch + 1 / + 2)
+  double* df_part;            // backward partial sums of the contribution rows
+  const int64_t* df_part_base;   // per front: its first partial sum
+  int32_t* df_pcnt;           // per pivot block (at df_fbase): finished partial-sum chunks
+  int64_t df_nflags;
   cudaStream_t stream;
   int num_sms;
   Timer* timer;
 };
 
-kep_status run_factor(FactorLaunch& F, double ca, double cb, kep_inertia* out, int* status_bits);
+// Factor the G factorizations of F.SS (shift g: ca[g] A + cb[g] B); out[g], status_bits[g] per shift.
+kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_inertia* out, int* status_bits);
 size_t emul_workspace_bytes(int64_t cap_rows);
-void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
-                        const int32_t* lf, int32_t e0, int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint,
-                        cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops);
+void emul_init();
+void launch_emul_update(bool window, const FrontTables& T, const SlotSet& SS, const LargeWork& W, const Batch& B,
+                        int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint, cudaStream_t st, int num_sms,
+                        Timer* timer, unsigned long long* flops);
 int32_t emul_max_batch();
 kep_status run_solve(SolveLaunch& L, const double* b, double* x);
 void build_df_items(const Plan& P, const int32_t* nelim, const int32_t* din, std::vector<int2>& items,
-                    std::vector<int32_t>& fwd_off, std::vector<int32_t>& bwd_off, int64_t& bwd_start);
+                    std::vector<int32_t>& fwd_off, std::vector<int32_t>& bwd_off, int64_t& bwd_start,
+                    std::vector<int64_t>& part_base, int64_t& part_total);
 int64_t df_flag_bases(const Plan& P, std::vector<int32_t>& fbase);
 kep_status run_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* a, const double* b,
                     const double* x, double* ya, double* yb, cudaStream_t st, int num_sms,

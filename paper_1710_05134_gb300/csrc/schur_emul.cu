@@ -97,8 +97,11 @@ KEP_HD EmulArgs emul_args(void* ws, int64_t cap_rows) {
 struct EmulBatch {
   unsigned char* ws;
   const int64_t* off;
+  const int32_t* lf;    // the level's entries: front and shift (Batch)
+  const int8_t* sh;
   int32_t e0, nb;
 };
+KEP_D int32_t emul_shift(const EmulBatch& B, int32_t b) { return B.sh ? B.sh[b] : 0; }
 KEP_D EmulArgs entry_args(const EmulBatch& B, int32_t e, int64_t cap_rows) {
   return emul_args(B.ws + B.off[e], cap_rows);
 }
@@ -187,12 +190,12 @@ KEP_D bool emul_range(const LargeWork& W, int32_t b, int32_t m, int32_t& c0, int
 // slice and block, consecutive threads writing consecutive rows.
 constexpr int kSThreads = 256;
 template <bool kWin>
-__global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, FactorSlot S, LargeWork W, const int32_t* lf,
-                                                             EmulBatch BA) {
+__global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, SlotSet SS, LargeWork W, EmulBatch BA) {
   __shared__ int smx[2][kSThreads];
   __shared__ int su[kWindow];
   const int32_t b = BA.e0 + blockIdx.y;
-  const int32_t t = lf[b];
+  const int32_t t = BA.lf[b];
+  const FactorSlot& S = SS.s[emul_shift(BA, b)];
   const EmulArgs E = entry_args(BA, blockIdx.y, T.m_alloc[t]);
   const int32_t m = T.m_sym[t] + S.d_in[t];
   int32_t c0, c1, s, ce;
@@ -382,8 +385,8 @@ KEP_D void add_levels(const float (&x)[8], long long& vh, long long& vl) {
 constexpr int kMaxBatch = 512;              // fronts per tensor-core launch
 
 template <bool kWin>
-__global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTables T, FactorSlot S, double* cbpool,
-                                                                       LargeWork W, const int32_t* lf, EmulBatch BA,
+__global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTables T, SlotSet SS,
+                                                                       LargeWork W, EmulBatch BA,
                                                                        unsigned long long* flops) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
@@ -395,8 +398,8 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   __shared__ int pre[kMaxBatch + 1];
   __shared__ int enI[kMaxBatch], enJ[kMaxBatch], eKS[kMaxBatch], eS[kMaxBatch], eCE[kMaxBatch];
   for (int e = threadIdx.x; e < BA.nb; e += blockDim.x) {
-    const int32_t b = BA.e0 + e, t = lf[b];
-    const int32_t m = T.m_sym[t] + S.d_in[t];
+    const int32_t b = BA.e0 + e, t = BA.lf[b];
+    const int32_t m = T.m_sym[t] + SS.s[emul_shift(BA, b)].d_in[t];
     int32_t c0, c1, s, ce;
     int nI = 0, nJ = 0, KS = 0, ns = 0;
     if (emul_range<kWin>(W, b, m, c0, c1, s, ce)) {
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
       for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
         int e, I, J;
         if (!locate(slot, e, I, J)) continue;
-        const EmulArgs E = entry_args(BA, e, T.m_alloc[lf[BA.e0 + e]]);
+        const EmulArgs E = entry_args(BA, e, T.m_alloc[BA.lf[BA.e0 + e]]);
         const int KS = eKS[e];
         for (int kk = 0; kk < KS; ++kk, ++f) {
           const int st = static_cast<int>(f % kStages);
@@ -541,8 +544,9 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
     for (int slot = blockIdx.x; slot < nslots && ok; slot += gridDim.x) {
       int e, I, J;
       if (!locate(slot, e, I, J)) continue;
-      const int32_t t = lf[BA.e0 + e];
-      const FrontView v = front_view(T, S, cbpool, t, S.d_in[t]);
+      const int32_t t = BA.lf[BA.e0 + e];
+      const int32_t g = emul_shift(BA, BA.e0 + e);
+      const FrontView v = front_view(T, SS.s[g], SS.cbpool[g], t, SS.s[g].d_in[t]);
       const EmulArgs E = entry_args(BA, e, T.m_alloc[t]);
       const int32_t s = eS[e], ce = eCE[e];
       const int NH = (eKS[e] + kHalf - 1) / kHalf;
@@ -611,7 +615,8 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (threadIdx.x == 0 && abort_flag) atomicOr(&S.status[0], ST_TIMEOUT);
+  if (threadIdx.x == 0 && abort_flag)
+    for (int g = 0; g < SS.n; ++g) atomicOr(&SS.s[g].status[0], ST_TIMEOUT);
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, kTmemCols);
@@ -619,6 +624,17 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
 }
 
 }  // namespace
+
+void emul_init() {
+  // once per process (a function-local static is initialised once even when contexts on several
+  // host threads get here together); called before any stream capture
+  static const bool attr_set = [] {
+    cudaFuncSetAttribute(lf_flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
+    cudaFuncSetAttribute(lf_flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
+    return true;
+  }();
+  (void)attr_set;
+}
 
 size_t emul_workspace_bytes(int64_t cap_rows) {
   const int64_t R = digit_pitch(cap_rows);
@@ -628,32 +644,27 @@ size_t emul_workspace_bytes(int64_t cap_rows) {
 // Window update (window = true) or flush for the batch entries e0 .. e0 + nb - 1 (fronts on the
 // tensor-core path; entry e's workspace at ws + d_off[e]); the kernels skip entries without that
 // update this step.
-void launch_emul_update(bool window, const FrontTables& T, const FactorSlot& S, double* cbpool, const LargeWork& W,
-                        const int32_t* lf, int32_t e0, int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint,
-                        cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops) {
-  // once per process (a function-local static is initialised once even when contexts on several
-  // host threads get here together)
-  static const bool attr_set = [] {
-    cudaFuncSetAttribute(lf_flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
-    cudaFuncSetAttribute(lf_flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
-    return true;
-  }();
-  (void)attr_set;
+void launch_emul_update(bool window, const FrontTables& T, const SlotSet& SS, const LargeWork& W, const Batch& B,
+                        int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint, cudaStream_t st, int num_sms,
+                        Timer* timer, unsigned long long* flops) {
+  emul_init();
   EmulBatch BA;
   BA.ws = static_cast<unsigned char*>(ws);
   BA.off = d_off;
-  BA.e0 = e0;
+  BA.lf = B.lf;
+  BA.sh = B.sh;
+  BA.e0 = B.e0;
   BA.nb = nb;
   const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + 31) / 32,
                                                                           std::max(1, num_sms * 8 / nb))));
   if (window) {
-    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<true><<<dim3(gs, nb), kSThreads, 0, st>>>(T, S, W, lf, BA));
+    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<true><<<dim3(gs, nb), kSThreads, 0, st>>>(T, SS, W, BA));
     KEP_LAUNCH(timer, KC_FLUSH_TC, st,
-               lf_flush_tc_kernel<true><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, BA, flops));
+               lf_flush_tc_kernel<true><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, SS, W, BA, flops));
   } else {
-    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<false><<<dim3(gs, nb), kSThreads, 0, st>>>(T, S, W, lf, BA));
+    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<false><<<dim3(gs, nb), kSThreads, 0, st>>>(T, SS, W, BA));
     KEP_LAUNCH(timer, KC_FLUSH_TC, st,
-               lf_flush_tc_kernel<false><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, S, cbpool, W, lf, BA, flops));
+               lf_flush_tc_kernel<false><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, SS, W, BA, flops));
   }
 }
 

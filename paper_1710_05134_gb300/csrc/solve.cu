@@ -256,7 +256,14 @@ struct DfArgs {
   const int32_t* fbase;    // per front: its first flag
   int32_t epoch;
   int32_t* err;            // set when a wait gave up
+  // backward only: partial sums of the contribution rows, per front at part_base[front],
+  // (pivot block x chunk) x (kSolveBlk + 1) doubles; pcnt counts the finished chunks per block
+  double* part;
+  const int64_t* part_base;
+  int32_t* pcnt;
 };
+
+constexpr int kDfChunk = 1024;   // contribution rows per backward partial-sum item
 
 // rows [r0, r1) of work item round r of front t: pivot block r (r < npb), else the r - npb-th
 // block of 64 contribution rows
@@ -373,9 +380,12 @@ __global__ void sv_df_bwd_prep_kernel(FrontTables T, FactorSlot S, const int32_t
     vf[i] = xnew[rv[i]];
 }
 
-// backward, pivot block b (taken from the last block down): x(block) = L11(block)^{-T}
-// (D^{-1} y(block) - sum_{rows a below the block} L(a, block) x(a)); contribution rows first (their
-// x is known), then the later pivot blocks as they are published
+// backward.  Items with y < 0 (taken first): the partial sums sum_{a in chunk} L(a, block) x(a) of
+// pivot block b over one chunk of kDfChunk contribution rows (their x is known), stored for the
+// block's item.  Items with y >= 0, pivot block b = npb - 1 - y (from the last block down):
+// x(block) = L11(block)^{-T} (D^{-1} y(block) - sum_{rows a below the block} L(a, block) x(a)), the
+// contribution rows' part added from the stored partial sums in chunk order, the later pivot
+// blocks as they are published
 __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, FactorSlot S, DfArgs A,
                                                                double* vfac, double* xnew) {
   constexpr int kCols = (kSolveBlk + 1 + 7) / 8;
@@ -397,7 +407,9 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
     const int32_t m = T.m_sym[t] + d_in;
     const int32_t nel = S.nelim[t];
     const int32_t npb = (nel + kSolveBlk - 1) / kSolveBlk;
-    const int32_t b = npb - 1 - I.y;
+    const int32_t nch = (m - nel + kDfChunk - 1) / kDfChunk;
+    const bool partial = I.y < 0;
+    const int32_t b = partial ? (-1 - I.y) / max(nch, 1) : npb - 1 - I.y;
     const int8_t* piv = S.piv + T.piv_off[t];
     const double* L = S.F + T.front_off[t];
     const int64_t ld = T.m_alloc[t];
@@ -405,17 +417,33 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
     int32_t* fl = A.flags + A.fbase[t];
     const int32_t k0 = blk_start(piv, b, nel), k1 = blk_start(piv, b + 1, nel);
     const int32_t kb = k1 - k0;
+    double* pbase = A.part + A.part_base[t] + static_cast<int64_t>(b) * nch * (kSolveBlk + 1);
     double acc[kCols];
 #pragma unroll
     for (int j = 0; j < kCols; ++j) acc[j] = 0.0;
-    // contribution rows
-    for (int32_t a = nel + lane; a < m; a += 32) {
-      const double xa = __ldcg(vf + a);
+    if (partial) {
+      const int32_t ch = (-1 - I.y) % nch;
+      const int32_t a0 = nel + ch * kDfChunk, a1 = min(m, a0 + kDfChunk);
+      for (int32_t a = a0 + lane; a < a1; a += 32) {
+        const double xa = __ldcg(vf + a);
+#pragma unroll
+        for (int j = 0; j < kCols; ++j) {
+          const int32_t c = warp + 8 * j;
+          if (c < kb) acc[j] = fma(__ldg(L + static_cast<int64_t>(k0 + c) * ld + a), xa, acc[j]);
+        }
+      }
 #pragma unroll
       for (int j = 0; j < kCols; ++j) {
         const int32_t c = warp + 8 * j;
-        if (c < kb) acc[j] = fma(__ldg(L + static_cast<int64_t>(k0 + c) * ld + a), xa, acc[j]);
+        const double v = warp_sum(acc[j]);
+        if (lane == 0 && c < kb) pbase[static_cast<int64_t>(ch) * (kSolveBlk + 1) + c] = v;
       }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        atomicAdd(A.pcnt + A.fbase[t] + b, 1);
+      }
+      continue;
     }
     // later pivot blocks, last first
     bool ok = true;
@@ -444,6 +472,30 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
       const int32_t c = warp + 8 * j;
       const double v = warp_sum(acc[j]);
       if (lane == 0 && c < kb) part[c] = v;
+    }
+    // the contribution rows' partial sums, once all chunks of this block are in (chunk order)
+    if (nch > 0) {
+      if (tid == 0) {
+        bool done = false;
+        const long long t0 = global_ns();
+        unsigned ns = 32;
+        while (!done) {
+          done = ld_acquire(A.pcnt + A.fbase[t] + b) >= nch;
+          if (done) break;
+          if (ld_acquire(A.err) != 0) break;
+          if (global_ns() - t0 > kDfWaitNs) { atomicExch(A.err, 1); break; }
+          __nanosleep(ns);
+          if (ns < 256) ns *= 2;
+        }
+        s_ok = done ? 1 : 0;
+      }
+      __syncthreads();
+      if (!s_ok) return;
+      if (tid < kb) {
+        double sacc = 0.0;
+        for (int32_t ch = 0; ch < nch; ++ch) sacc += __ldcg(pbase + static_cast<int64_t>(ch) * (kSolveBlk + 1) + tid);
+        part[tid] += sacc;
+      }
     }
     for (int32_t e = tid; e < kb * kb; e += blockDim.x) {
       const int32_t c = e / kb, a = e % kb;
@@ -555,7 +607,8 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
   const Plan& P = *L.plan;
   cudaStream_t st = L.stream;
   const int g = L.num_sms * 4;
-  if (cudaMemsetAsync(L.df_counters, 0, sizeof(int32_t) * (1 + 2 * static_cast<size_t>(P.nlevels)), st) != cudaSuccess)
+  if (cudaMemsetAsync(L.df_counters, 0, sizeof(int32_t) * (1 + 2 * static_cast<size_t>(P.nlevels)), st) != cudaSuccess ||
+      cudaMemsetAsync(L.df_pcnt, 0, sizeof(int32_t) * static_cast<size_t>(L.df_nflags), st) != cudaSuccess)
     return KEP_ERR_CUDA;
   KEP_LAUNCH(L.timer, KC_PERM, st, gather_perm_kernel<<<g, 256, 0, st>>>(P.n, L.d_perm, b, L.bnew));
   auto df_args = [&](int32_t l, bool fwd) {
@@ -569,6 +622,9 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
     A.fbase = L.df_fbase;
     A.epoch = fwd ? 2 * L.epoch + 1 : 2 * L.epoch + 2;
     A.err = L.df_counters;
+    A.part = L.df_part;
+    A.part_base = L.df_part_base;
+    A.pcnt = L.df_pcnt;
     return A;
   };
   for (int32_t l = 0; l < P.nlevels; ++l) {
@@ -610,11 +666,14 @@ kep_status run_solve(SolveLaunch& L, const double* b, double* x) {
 // level_nbig_solve[l] fronts; forward rounds r = 0, 1, ... take pivot block r (then contribution
 // block r - npb) of every front that has one, backward rounds the pivot blocks from the last.
 void build_df_items(const Plan& P, const int32_t* nelim, const int32_t* din, std::vector<int2>& items,
-                    std::vector<int32_t>& fwd_off, std::vector<int32_t>& bwd_off, int64_t& bwd_start) {
+                    std::vector<int32_t>& fwd_off, std::vector<int32_t>& bwd_off, int64_t& bwd_start,
+                    std::vector<int64_t>& part_base, int64_t& part_total) {
   items.clear();
   fwd_off.assign(P.nlevels + 1, 0);
   bwd_off.assign(P.nlevels + 1, 0);
-  std::vector<int32_t> npb, nall;
+  part_base.assign(P.nfronts, 0);
+  part_total = 0;
+  std::vector<int32_t> npb, nall, nch;
   for (int pass = 0; pass < 2; ++pass) {
     const int64_t base = static_cast<int64_t>(items.size());
     if (pass == 1) bwd_start = base;
@@ -623,14 +682,23 @@ void build_df_items(const Plan& P, const int32_t* nelim, const int32_t* din, std
       const int32_t lb = P.level_ptr[l], nbig = P.level_nbig_solve[l];
       npb.assign(nbig, 0);
       nall.assign(nbig, 0);
+      nch.assign(nbig, 0);
       int32_t rounds = 0;
       for (int32_t q = 0; q < nbig; ++q) {
         const int32_t t = P.level_fronts[lb + q];
         const int32_t nel = nelim[t], m = P.m_sym[t] + din[t];
         npb[q] = (nel + kSolveBlk - 1) / kSolveBlk;
+        nch[q] = (m - nel + kDfChunk - 1) / kDfChunk;
         nall[q] = pass == 0 ? npb[q] + (m - nel + kSolveBlk - 1) / kSolveBlk : npb[q];
         rounds = std::max(rounds, nall[q]);
+        if (pass == 1) {
+          part_base[t] = part_total;
+          part_total += static_cast<int64_t>(npb[q]) * nch[q] * (kSolveBlk + 1);
+        }
       }
+      if (pass == 1)   // the contribution rows' partial sums first: they wait for nothing
+        for (int32_t q = 0; q < nbig; ++q)
+          for (int32_t v = 0; v < npb[q] * nch[q]; ++v) items.push_back(make_int2(q, -1 - v));
       for (int32_t r = 0; r < rounds; ++r)
         for (int32_t q = 0; q < nbig; ++q)
           if (r < nall[q]) items.push_back(make_int2(q, r));

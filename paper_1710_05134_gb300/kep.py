@@ -25,7 +25,7 @@ EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_g
             "kep_factor_pencil", "kep_solve", "kep_spmv", "kep_kth_eigenpair", "kep_set_timing",
             "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi", "kep_solve_refined",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
-            "kep_multisection_points", "kep_multisection_update",
+            "kep_multisection_points", "kep_multisection_update", "kep_set_graphs",
             "kep_set_schur_mode"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
 KEP_INIT_LANCZOS, KEP_INIT_GERSHGORIN = 0, 1
@@ -120,6 +120,7 @@ def lib() -> ctypes.CDLL:
         L.kep_solve_refined.argtypes = [P, P, P, I, D, ctypes.c_int32, P, P]
         L.kep_get_timing.argtypes = [P, ctypes.POINTER(Timing), I]
         L.kep_dense_inertia_noalloc.argtypes = [I64, P, P, I64, D, P, P]
+        L.kep_set_graphs.argtypes = [P, I]
         L.kep_multisection_points.argtypes = [D, D, ctypes.c_int32, P]
         L.kep_multisection_points.restype = I
         L.kep_multisection_update.argtypes = [I64, ctypes.c_int32, P, P, P, P, P, P]
@@ -308,6 +309,10 @@ class Problem:
                                            ctypes.byref(it), ctypes.byref(be))
         _check(code, "kep_solve_refined")
         return x, it.value, be.value
+
+    def set_graphs(self, enable: bool):
+        """Replay each factorization level's pivot-step passes as CUDA graphs (default on)."""
+        _check(lib().kep_set_graphs(self._h, 1 if enable else 0), "kep_set_graphs")
 
     def set_timing(self, enable: bool, classes=None):
         """Per-launch CUDA-event timing of this context's kernels (launch counts are always kept);

@@ -124,6 +124,58 @@ def test_factor_multi(kep, pen):
         assert np.linalg.norm(M @ y - rhs) <= 1e-11 * np.abs(M).sum(1).max() * np.linalg.norm(y)
 
 
+def test_factor_multi_batched_closed_form_and_groups(kep):
+    """kep_factor_multi factors up to 8 shifts in the same launches (each shift its own slot and
+    contribution blocks; the tensor-core update batched over all shifts' fronts).  Counts equal the
+    closed-form spectrum (n = 16,384 perfect diamond) for 8 shifts in one group, and for 11 shifts
+    (groups of 6 and 5); the last shift's factor stays for the solve."""
+    from gen import perfect_diamond_pencil
+    q = perfect_diamond_pencil(8, 8, 8)
+    cf = core.diamond_bloch_eigs(8, 8, 8, 1.0, 0.02)
+    with kep.Problem.from_pencil(q) as P:
+        P.set_schur_mode(True, min_front=512)
+        for count in (8, 11):
+            sig = core.certified_shifts(cf, count, 1e-6, seed=10 + count)
+            res = P.factor_multi(sig)
+            assert [r.neg for r in res] == [core.count_below(cf, s) for s in sig]
+            assert all(r.neg + r.zero + r.pos == q.n for r in res)
+        rhs = np.random.default_rng(3).normal(size=q.n)
+        y = P.solve(rhs)
+        M = (q.A() - sig[-1] * q.B()).tocsr()
+        assert np.linalg.norm(M @ y - rhs) <= 1e-12 * abs(M).sum(1).max() * np.linalg.norm(y)
+        # the same shifts one by one give the same counts (and the slot is reusable afterwards)
+        seq = [P.factor(s).neg for s in sig]
+        assert seq == [r.neg for r in res]
+
+
+def test_factor_multi_delays_and_hermitian(kep):
+    """Batched shifts with forced 2x2 pivots and delayed columns (zero diagonal of A - sigma B at
+    the first shift) match the oracle's dense Bunch-Kaufman counts; a complex Hermitian pencil's
+    batched counts match its dense spectrum."""
+    import scipy.sparse as sp
+    p = make_pair(4, 4, 4, seed=6)            # n = 2048
+    sigma = 0.3
+    a = p.a.copy()
+    rows = np.repeat(np.arange(p.n), np.diff(p.rowptr))
+    d = rows == p.colind
+    a[d] = sigma * p.b[d]
+    A = sp.csr_matrix((a, p.colind, p.rowptr), shape=(p.n, p.n)).toarray()
+    B = p.B().toarray()
+    sig = [sigma, sigma + 0.2, sigma - 0.7, sigma + 1.1]
+    with kep.Problem(p.n, p.rowptr, p.colind, a, p.b, p.coords) as P:
+        P.set_schur_mode(True, min_front=256)
+        res = P.factor_multi(sig)
+        for s, r in zip(sig, res):
+            assert (r.neg, r.zero, r.pos) == core.dense_inertia(A - s * B), s
+    h = make_pair(3, 3, 2, seed=21, phases="peierls")          # n = 576 complex
+    Ah, Bh = h.A().toarray(), h.B().toarray()
+    lam, _ = core.gen_eig(Ah, Bh)
+    hs = core.certified_shifts(lam, 5, 1e-8 * np.abs(Ah).sum(1).max(), seed=13)
+    with kep.Problem.from_pencil(h) as H:
+        res = H.factor_multi(hs)
+        assert [r.neg for r in res] == [core.count_below(lam, s) for s in hs]
+
+
 def test_fp32_factor_refined_solves(kep, pen):
     p, A, B, lam, X = pen
     sig = float(core.certified_shifts(lam, 1, 1e-6 * np.abs(A).sum(1).max(), seed=8)[0])
