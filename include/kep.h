@@ -95,9 +95,11 @@ typedef struct {
   int32_t b_factor;           /* where B's factor (the B-solves of Algorithms 2 and 3) lives:
                                  KEP_BFACTOR_AUTO (default) its own factor slot when a second
                                  factor fits in free device memory, else shared;
-                                 KEP_BFACTOR_SHARED the slot of the A - sigma B factorizations,
-                                 B factored again whenever a B-solve finds it replaced (one extra
-                                 factorization per Algorithm 2 step; the largest problems);
+                                 KEP_BFACTOR_SHARED the slot of the A - sigma B factorizations
+                                 (the largest problems): B is factored once (which also shows it
+                                 positive definite), later B-solves that find the slot replaced
+                                 run conjugate gradients to a relative residual of 1e-14 and
+                                 factor B again only if 500 iterations do not reach it;
                                  KEP_BFACTOR_OWN its own slot always */
 } kep_params;
 
@@ -182,10 +184,12 @@ kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, const int32_t
  *                       into eight 8-bit pieces per entry (column balancing, per-row power-of-two
  *                       scales, exact FP32 level sums, exact int64 combination): as accurate as an
  *                       FP64 update, on the tensor pipe.
- *   KEP_SCHUR_FP32      every Schur update in FP32 FMA (pivot blocks and L21 stay FP64): a
- *                       reduced-precision factor (backward error near FP32 rounding) for
- *                       kep_solve_refined; its inertia is that of a nearby matrix, so inertia
- *                       counts should come from the other modes.
+ *   KEP_SCHUR_FP32      a reduced-precision factor for kep_solve_refined: fronts of order >=
+ *                       min_front take the tensor-core update with four 8-bit pieces per entry
+ *                       (10 bf16 products per multiply-add instead of 36; about 31 bits of each
+ *                       row's scale), smaller fronts FP32 FMA tiles (pivot blocks and L21 stay
+ *                       FP64); backward error near FP32 rounding.  Its inertia is that of a nearby
+ *                       matrix, so inertia counts should come from the other modes.
  * Takes effect at the next factorization.  Errors: KEP_ERR_INVALID.
  */
 enum { KEP_SCHUR_FP64 = 0, KEP_SCHUR_EMULATED = 1, KEP_SCHUR_FP32 = 2 };

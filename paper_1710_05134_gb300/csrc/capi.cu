@@ -248,7 +248,9 @@ static kep_status factor_set(kep_ctx* c, int G, FactorSlot* const* slots, double
     c->capture_stream = nullptr;
   }
   F.capture_stream = c->capture_stream;
-  F.emul_min = c->schur_mode == KEP_SCHUR_EMULATED ? c->emul_min_front : 0;
+  // the tensor-core update for fronts of order >= emul_min_front: FP64-accurate (8 digits), or
+  // the reduced-precision factor's 4 digits; smaller fronts FP64 or FP32 FMA tiles
+  F.emul_min = c->schur_mode == KEP_SCHUR_FP64 ? 0 : c->emul_min_front;
   F.fp32_schur = c->schur_mode == KEP_SCHUR_FP32;
   F.emul_ws = nullptr;
   F.d_emul_off = nullptr;

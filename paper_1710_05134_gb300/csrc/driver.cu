@@ -145,6 +145,7 @@ struct Driver {
   double* coef = nullptr;   // device coefficients (cap_cols)
   double* partial = nullptr;
   int nblocks = 0;
+  double* cg = nullptr;     // 3 n: residual, direction, B times direction (B-solves by CG)
 };
 
 // splitmix64 (Steele, Lea, Flood 2014) as a counter-based generator; Box-Muller for N(0, 1).
@@ -182,7 +183,7 @@ void kep_ctx::driver_release() {
   Driver* d = static_cast<Driver*>(driver);
   if (!d) return;
   cudaFree(d->V); cudaFree(d->BV); cudaFree(d->w); cudaFree(d->u); cudaFree(d->u2);
-  cudaFree(d->coef); cudaFree(d->partial);
+  cudaFree(d->coef); cudaFree(d->partial); cudaFree(d->cg);
   delete d;
   driver = nullptr;
 }
@@ -264,10 +265,54 @@ struct Run {
     if (st == KEP_ERR_SINGULAR) return KEP_ERR_NOT_SPD;
     if (st != KEP_OK) return st;
     if (in.neg != 0 || in.zero != 0) return KEP_ERR_NOT_SPD;
+    b_spd = true;
+    return KEP_OK;
+  }
+
+  bool b_spd = false;       // B's factorization showed it positive definite
+
+  // x = B^{-1} b by conjugate gradients (B is positive definite): the B-solves of a shared slot
+  // once the slot holds another matrix.  Stops at ||b - B x||_2 <= 1e-14 ||b||_2; false (x not
+  // usable) when that takes more than 500 iterations.
+  kep_status cg_B(const double* b, double* x, bool& converged) {
+    converged = false;
+    if (!d->cg) {
+      if (cudaMalloc(&d->cg, sizeof(double) * 3 * n) != cudaSuccess) { cudaGetLastError(); return KEP_OK; }
+    }
+    double* r = d->cg;
+    double* pdir = d->cg + n;
+    double* q = d->cg + 2 * n;
+    CTRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    CTRY(cudaMemcpyAsync(pdir, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    CTRY(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+    double rr = 0;
+    DTRY(dots(r, 1, r, &rr));
+    const double stop = 1e-28 * rr;
+    for (int it = 0; it < 500; ++it) {
+      if (rr <= stop) { converged = true; return KEP_OK; }
+      DTRY(ctx_spmv_dev(c, pdir, nullptr, q));
+      double pq = 0;
+      DTRY(dots(pdir, 1, q, &pq));
+      if (!(pq > 0)) return KEP_OK;
+      const double alpha = rr / pq;
+      ops.axpby(alpha, pdir, 1.0, x);
+      ops.axpby(-alpha, q, 1.0, r);
+      double rr1 = 0;
+      DTRY(dots(r, 1, r, &rr1));
+      ops.axpby(1.0, r, rr1 / rr, pdir);
+      rr = rr1;
+    }
+    converged = rr <= stop;
     return KEP_OK;
   }
 
   kep_status solve_B(const double* b, double* x) {
+    if (!b_factored() && bslot == 0 && b_spd) {
+      // the shared slot holds A - sigma B: conjugate gradients instead of factoring B again
+      bool ok = false;
+      DTRY(cg_B(b, x, ok));
+      if (ok) return KEP_OK;
+    }
     if (!b_factored()) DTRY(factor_B());   // shared slot, or a re-plan of the storage dropped it
     return ctx_solve_dev(c, bslot, b, x);
   }

@@ -868,10 +868,10 @@ kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_i
           KEP_LAUNCH(F.timer, KC_APPLY, sx, lf_apply_kernel<<<dim3(gx_apply, nb), 128, 0, sx>>>(F.T, F.SS, F.W, B));
           if (emul) {
             // in-window and trailing updates on the tensor cores (FP64-accurate splitting)
-            launch_emul_update(true, F.T, F.SS, F.W, B, nb, F.emul_ws, F.d_emul_off + lb + e, max_m, sx, F.num_sms,
-                               F.timer, F.flops);
-            launch_emul_update(false, F.T, F.SS, F.W, B, nb, F.emul_ws, F.d_emul_off + lb + e, max_m, sx, F.num_sms,
-                               F.timer, F.flops);
+            launch_emul_update(true, F.fp32_schur, F.T, F.SS, F.W, B, nb, F.emul_ws, F.d_emul_off + lb + e, max_m, sx,
+                               F.num_sms, F.timer, F.flops);
+            launch_emul_update(false, F.fp32_schur, F.T, F.SS, F.W, B, nb, F.emul_ws, F.d_emul_off + lb + e, max_m, sx,
+                               F.num_sms, F.timer, F.flops);
           } else if (F.fp32_schur) {
             KEP_LAUNCH(F.timer, KC_UPDATE, sx,
                        lf_schur_kernel<true, float><<<dim3(gx_win, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,

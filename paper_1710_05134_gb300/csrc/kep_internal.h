@@ -321,9 +321,10 @@ struct SolveLaunch {
 kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_inertia* out, int* status_bits);
 size_t emul_workspace_bytes(int64_t cap_rows);
 void emul_init();
-void launch_emul_update(bool window, const FrontTables& T, const SlotSet& SS, const LargeWork& W, const Batch& B,
-                        int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint, cudaStream_t st, int num_sms,
-                        Timer* timer, unsigned long long* flops);
+// low: the reduced-precision splitting (4 digits, KEP_SCHUR_FP32) instead of the FP64-accurate one
+void launch_emul_update(bool window, bool low, const FrontTables& T, const SlotSet& SS, const LargeWork& W,
+                        const Batch& B, int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint,
+                        cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops);
 int32_t emul_max_batch();
 kep_status run_solve(SolveLaunch& L, const double* b, double* x);
 void build_df_items(const Plan& P, const int32_t* nelim, const int32_t* din, std::vector<int2>& items,

@@ -31,6 +31,7 @@
 // while the epilogue reads the other); both operands are staged in shared memory by bulk copies
 // in a five-step pipeline.
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -40,18 +41,26 @@ namespace kep {
 
 namespace {
 
-constexpr int kSlices = 8;
+constexpr int kSlices = 8;                    // digits of the FP64-accurate splitting
+constexpr int kSlicesLow = 4;                 // digits of the reduced-precision splitting (KEP_SCHUR_FP32)
 constexpr int kKB = kWindow / 8;              // 8-column blocks of a window
 constexpr int kTM = 128;                      // tile rows (i): tensor-memory lanes
 constexpr int kTN = 32;                       // tile columns (j) per digit of W
 constexpr int kStages = 5;                    // shared-memory pipeline depth (16 columns each)
-constexpr uint32_t kStageA = 2 * kSlices * kTM * 16;   // [k-block 2][slice 8][row 128][16 B]
-constexpr uint32_t kStageB = 2 * kSlices * kTN * 16;   // [k-block 2][slice 8][row 32][16 B]
-constexpr uint32_t kStageBytes = kStageA + kStageB;
-constexpr size_t kFlushSmem = static_cast<size_t>(kStages) * kStageBytes + 1024;
+// per digit count S: one pipeline stage holds [k-block 2][slice S][row 128][16 B] of L digits and
+// [k-block 2][slice S][row 32][16 B] of W digits; tensor memory holds 2 buffers x S level
+// accumulators x 32 columns
+template <int S>
+struct Split {
+  static constexpr uint32_t kStageA = 2 * S * kTM * 16;
+  static constexpr uint32_t kStageB = 2 * S * kTN * 16;
+  static constexpr uint32_t kStageBytes = kStageA + kStageB;
+  static constexpr size_t kSmem = static_cast<size_t>(kStages) * kStageBytes + 1024;
+  static constexpr uint32_t kTmemCols = 2 * S * kTN <= 256 ? 256u : 512u;
+  static constexpr int kShift = 8 * (S + 1);  // 2^{e_i + f_j - kShift}: weight of the lowest level kept
+};
 constexpr int kEpiWarps = 16;                 // epilogue: warp w reads lanes 32 (w % 4), columns 8 (w / 4)
 constexpr int kFlushThreads = (kEpiWarps + 2) * 32;   // + one copy warp, one MMA-issue warp
-constexpr uint32_t kTmemCols = 512;           // 2 buffers x 8 level accumulators x 32 columns
 constexpr int kHalf = 8;                      // 16-column steps per accumulation (128 columns)
 constexpr uint64_t kWaitNs = 2000000000ull;   // bounded waits: 2 s
 // longest sleep between two tries of a wait, per role (the copy and MMA warps must react fast,
@@ -71,11 +80,13 @@ struct EmulArgs {
 // halves, then the slice, then [128 rows][8 columns]; for the W rows the same with blocks of 32.
 // One step of one tile is then a contiguous 32 KiB (L) and 8 KiB (W) run whose order is that of
 // the shared-memory operands.
+template <int S>
 KEP_D int64_t ldig_off(int a, int32_t q, int64_t row) {      // q: 8-column block
-  return (((((row >> 7) * (kWindow / 16) + (q >> 1)) * 2 + (q & 1)) * kSlices + a) * kTM + (row & (kTM - 1))) * 8;
+  return (((((row >> 7) * (kWindow / 16) + (q >> 1)) * 2 + (q & 1)) * S + a) * kTM + (row & (kTM - 1))) * 8;
 }
+template <int S>
 KEP_D int64_t wdig_off(int a, int32_t q, int64_t row) {
-  return (((((row >> 5) * (kWindow / 16) + (q >> 1)) * 2 + (q & 1)) * kSlices + a) * kTN + (row & (kTN - 1))) * 8;
+  return (((((row >> 5) * (kWindow / 16) + (q >> 1)) * 2 + (q & 1)) * S + a) * kTN + (row & (kTN - 1))) * 8;
 }
 
 KEP_HD int64_t digit_pitch(int64_t cap_rows) { return (cap_rows + kTM - 1) / kTM * kTM + kTM; }
@@ -149,12 +160,14 @@ KEP_D unsigned long long fixed64(double x, int u, int e) {
 // bf16 bit pattern of the integer d, |d| <= 128 (exact: at most 8 significant bits)
 KEP_D uint32_t digit_bits(int d) { return __float_as_uint(__int2float_rn(d)) >> 16; }
 
-// The eight balanced digits of one value, times its sign, as bf16 bit patterns.
-KEP_D void balanced_digits(double x, int u, int e, uint32_t (&d)[kSlices]) {
+// The leading S of the eight balanced digits of one value, times its sign, as bf16 bit patterns
+// (S < 8 drops the rest: a truncation below 2^{-8S} of the row scale).
+template <int S>
+KEP_D void balanced_digits(double x, int u, int e, uint32_t (&d)[S]) {
   const unsigned long long Y = fixed64(x, u, e) + 0x0080808080808080ull;   // pre-carry of the low 7
   const bool neg = x < 0.0;
 #pragma unroll
-  for (int a = 0; a < kSlices; ++a) {
+  for (int a = 0; a < S; ++a) {
     const int v = a == 0 ? static_cast<int>(Y >> 56) : static_cast<int>((Y >> (56 - 8 * a)) & 0xff) - 128;
     d[a] = digit_bits(neg ? -v : v);
   }
@@ -189,7 +202,7 @@ KEP_D bool emul_range(const LargeWork& W, int32_t b, int32_t m, int32_t& c0, int
 // taking the 8-column blocks g, g + NG, ...; each 16-byte store holds one row's 8 digits of one
 // slice and block, consecutive threads writing consecutive rows.
 constexpr int kSThreads = 256;
-template <bool kWin>
+template <bool kWin, int ND>
 __global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, SlotSet SS, LargeWork W, EmulBatch BA) {
   __shared__ int smx[2][kSThreads];
   __shared__ int su[kWindow];
@@ -244,7 +257,7 @@ __global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, Slot
     for (int32_t q = g; q < nq; q += NG) {
 #pragma unroll 1
       for (int which = 0; which < (row < wrows ? 2 : 1); ++which) {
-        uint32_t pk[kSlices][4];
+        uint32_t pk[ND][4];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const int32_t c = q * 8 + e;
@@ -255,17 +268,17 @@ __global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, Slot
             x = which == 0 ? L[static_cast<int64_t>(c0 + c) * ld + s + row]
                            : wval(L, ld, s + row, c0 + c, Dd, De, pv);
           }
-          uint32_t d[kSlices];
-          balanced_digits(x, which == 0 ? u : -u, which == 0 ? el : ew, d);
+          uint32_t d[ND];
+          balanced_digits<ND>(x, which == 0 ? u : -u, which == 0 ? el : ew, d);
 #pragma unroll
-          for (int a = 0; a < kSlices; ++a) {
+          for (int a = 0; a < ND; ++a) {
             if (e % 2 == 0) pk[a][e / 2] = d[a];
             else pk[a][e / 2] |= d[a] << 16;
           }
         }
 #pragma unroll
-        for (int a = 0; a < kSlices; ++a)
-          *reinterpret_cast<uint4*>(which == 0 ? E.Ls + ldig_off(a, q, row) : E.Ws + wdig_off(a, q, row)) =
+        for (int a = 0; a < ND; ++a)
+          *reinterpret_cast<uint4*>(which == 0 ? E.Ls + ldig_off<ND>(a, q, row) : E.Ws + wdig_off<ND>(a, q, row)) =
               make_uint4(pk[a][0], pk[a][1], pk[a][2], pk[a][3]);
       }
     }
@@ -384,7 +397,7 @@ KEP_D void add_levels(const float (&x)[8], long long& vh, long long& vl) {
 
 constexpr int kMaxBatch = 512;              // fronts per tensor-core launch
 
-template <bool kWin>
+template <bool kWin, int S>
 __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTables T, SlotSet SS,
                                                                        LargeWork W, EmulBatch BA,
                                                                        unsigned long long* flops) {
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
         const int64_t c = min(nI, nJ / 4);
         const int64_t ntiles = 2 * c * (c + 1) + (nI - c) * static_cast<int64_t>(nJ);
         atomicAdd(&flops[KC_FLUSH_TC],
-                  static_cast<unsigned long long>(2ll * kTM * (kSlices * (kSlices + 1) / 2) * kTN * 16 * KS * ntiles));
+                  static_cast<unsigned long long>(2ll * kTM * (S * (S + 1) / 2) * kTN * 16 * KS * ntiles));
         atomicAdd(&flops[KC_COUNT], static_cast<unsigned long long>(2 * static_cast<int64_t>(r) * (w * h - w * (w - 1) / 2)));
       }
       eS[e] = s;
@@ -452,7 +465,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
     abort_flag = 0;
   }
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_slot, kTmemCols);
+    tc::tmem_alloc(&tmem_slot, Split<S>::kTmemCols);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -477,10 +490,11 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
             ok = false;
             break;
           }
-          unsigned char* sa = sbase + static_cast<size_t>(st) * kStageBytes;
-          tc::mbar_arrive_expect_tx(&full_bar[st], kStageBytes);
-          tc::bulk_g2s(sa, E.Ls + ldig_off(0, 2 * kk, I * kTM), kStageA, &full_bar[st]);
-          tc::bulk_g2s(sa + kStageA, E.Ws + wdig_off(0, 2 * kk, J * kTN), kStageB, &full_bar[st]);
+          unsigned char* sa = sbase + static_cast<size_t>(st) * Split<S>::kStageBytes;
+          tc::mbar_arrive_expect_tx(&full_bar[st], Split<S>::kStageBytes);
+          tc::bulk_g2s(sa, E.Ls + ldig_off<S>(0, 2 * kk, I * kTM), Split<S>::kStageA, &full_bar[st]);
+          tc::bulk_g2s(sa + Split<S>::kStageA, E.Ws + wdig_off<S>(0, 2 * kk, J * kTN), Split<S>::kStageB,
+                       &full_bar[st]);
         }
       }
       if (!ok) {
@@ -507,7 +521,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
             break;
           }
           tc::fence_after_sync();
-          const uint32_t dbase = tmem + static_cast<uint32_t>(buf * kSlices * kTN);
+          const uint32_t dbase = tmem + static_cast<uint32_t>(buf * S * kTN);
           const int k1 = min(KS, (hh + 1) * kHalf);
           for (int kk = hh * kHalf; kk < k1; ++kk, ++f) {
             const int st = static_cast<int>(f % kStages);
@@ -516,13 +530,13 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
               break;
             }
             tc::fence_after_sync();
-            const uint32_t sa = s0 + st * kStageBytes, sb = sa + kStageA;
-            const uint64_t bdesc = tc::smem_desc(sb, kStageB / 2, 128);
-            const uint64_t adesc = tc::smem_desc(sa, kStageA / 2, 128);
+            const uint32_t sa = s0 + st * Split<S>::kStageBytes, sb = sa + Split<S>::kStageA;
+            const uint64_t bdesc = tc::smem_desc(sb, Split<S>::kStageB / 2, 128);
+            const uint64_t adesc = tc::smem_desc(sa, Split<S>::kStageA / 2, 128);
 #pragma unroll
-            for (int a = 0; a < kSlices; ++a)   // levels a+2 .. 9 at columns 32 a ..; slice a of L
+            for (int a = 0; a < S; ++a)   // levels a+2 .. S+1 at columns 32 a ..; slice a of L
               tc::mma_bf16(dbase + static_cast<uint32_t>(a * kTN), adesc + static_cast<uint64_t>(a * (kTM * 16 / 16)),
-                           bdesc, tc::idesc_bf16(kTM, (kSlices - a) * kTN),
+                           bdesc, tc::idesc_bf16(kTM, (S - a) * kTN),
                            (kk > hh * kHalf || a > 0) ? 1u : 0u);
             tc::mma_commit(&empty_bar[st]);
           }
@@ -576,21 +590,29 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
           break;
         }
         tc::fence_after_sync();
-        const uint32_t tb = trow + static_cast<uint32_t>(buf * kSlices * kTN);
+        const uint32_t tb = trow + static_cast<uint32_t>(buf * S * kTN);
 #pragma unroll
         for (int cg = 0; cg < kCols / 4; ++cg) {
-          uint32_t x[8][4];
+          uint32_t x[S][4];
 #pragma unroll
-          for (int g = 0; g < 8; ++g) tc::tmem_ld4(tb + g * kTN + c_lo + cg * 4, x[g]);
+          for (int g = 0; g < S; ++g) tc::tmem_ld4(tb + g * kTN + c_lo + cg * 4, x[g]);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int g = 0; g < 8; ++g) tc::tmem_keep(x[g]);
+          for (int g = 0; g < S; ++g) tc::tmem_keep(x[g]);
 #pragma unroll
           for (int ee = 0; ee < 4; ++ee) {
-            float xs[8];
+            float xs[S];
 #pragma unroll
-            for (int g = 0; g < 8; ++g) xs[g] = __uint_as_float(x[g][ee]);
-            add_levels(xs, vh[cg * 4 + ee], vl[cg * 4 + ee]);
+            for (int g = 0; g < S; ++g) xs[g] = __uint_as_float(x[g][ee]);
+            if constexpr (S == kSlices) {
+              add_levels(xs, vh[cg * 4 + ee], vl[cg * 4 + ee]);
+            } else {
+              // levels 2 .. S+1 in base 256 (each sum an exact integer of at most 2^23)
+              long long v = 0;
+#pragma unroll
+              for (int g = 0; g < S; ++g) v = v * 256 + level_int(xs[g]);
+              vl[cg * 4 + ee] += v;
+            }
           }
         }
         // this buffer is free for the MMAs of a later half window
@@ -602,7 +624,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
         break;
       }
       if (rowok) {
-        const int ei = E.eL[i - s] - 72;
+        const int ei = E.eL[i - s] - Split<S>::kShift;
         // all loads first (the stores below could alias them as far as the compiler knows)
         double cv[kCols];
 #pragma unroll
@@ -619,7 +641,7 @@ __global__ void __launch_bounds__(kFlushThreads, 1) lf_flush_tc_kernel(FrontTabl
     for (int g = 0; g < SS.n; ++g) atomicOr(&SS.s[g].status[0], ST_TIMEOUT);
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, kTmemCols);
+    tc::tmem_dealloc(tmem, Split<S>::kTmemCols);
   }
 }
 
@@ -629,8 +651,14 @@ void emul_init() {
   // once per process (a function-local static is initialised once even when contexts on several
   // host threads get here together); called before any stream capture
   static const bool attr_set = [] {
-    cudaFuncSetAttribute(lf_flush_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
-    cudaFuncSetAttribute(lf_flush_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kFlushSmem));
+    cudaFuncSetAttribute(lf_flush_tc_kernel<true, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(Split<kSlices>::kSmem));
+    cudaFuncSetAttribute(lf_flush_tc_kernel<false, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(Split<kSlices>::kSmem));
+    cudaFuncSetAttribute(lf_flush_tc_kernel<true, kSlicesLow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(Split<kSlicesLow>::kSmem));
+    cudaFuncSetAttribute(lf_flush_tc_kernel<false, kSlicesLow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(Split<kSlicesLow>::kSmem));
     return true;
   }();
   (void)attr_set;
@@ -644,9 +672,9 @@ size_t emul_workspace_bytes(int64_t cap_rows) {
 // Window update (window = true) or flush for the batch entries e0 .. e0 + nb - 1 (fronts on the
 // tensor-core path; entry e's workspace at ws + d_off[e]); the kernels skip entries without that
 // update this step.
-void launch_emul_update(bool window, const FrontTables& T, const SlotSet& SS, const LargeWork& W, const Batch& B,
-                        int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint, cudaStream_t st, int num_sms,
-                        Timer* timer, unsigned long long* flops) {
+void launch_emul_update(bool window, bool low, const FrontTables& T, const SlotSet& SS, const LargeWork& W,
+                        const Batch& B, int32_t nb, void* ws, const int64_t* d_off, int64_t rows_hint,
+                        cudaStream_t st, int num_sms, Timer* timer, unsigned long long* flops) {
   emul_init();
   EmulBatch BA;
   BA.ws = static_cast<unsigned char*>(ws);
@@ -657,14 +685,19 @@ void launch_emul_update(bool window, const FrontTables& T, const SlotSet& SS, co
   BA.nb = nb;
   const int gs = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((rows_hint + 31) / 32,
                                                                           std::max(1, num_sms * 8 / nb))));
+  auto go = [&](auto win, auto nd) {
+    constexpr bool W_ = decltype(win)::value;
+    constexpr int S_ = decltype(nd)::value;
+    KEP_LAUNCH(timer, KC_SLICE, st, (lf_slice_kernel<W_, S_><<<dim3(gs, nb), kSThreads, 0, st>>>(T, SS, W, BA)));
+    KEP_LAUNCH(timer, KC_FLUSH_TC, st,
+               (lf_flush_tc_kernel<W_, S_><<<num_sms, kFlushThreads, Split<S_>::kSmem, st>>>(T, SS, W, BA, flops)));
+  };
+  using T8 = std::integral_constant<int, kSlices>;
+  using TL = std::integral_constant<int, kSlicesLow>;
   if (window) {
-    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<true><<<dim3(gs, nb), kSThreads, 0, st>>>(T, SS, W, BA));
-    KEP_LAUNCH(timer, KC_FLUSH_TC, st,
-               lf_flush_tc_kernel<true><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, SS, W, BA, flops));
+    if (low) go(std::true_type{}, TL{}); else go(std::true_type{}, T8{});
   } else {
-    KEP_LAUNCH(timer, KC_SLICE, st, lf_slice_kernel<false><<<dim3(gs, nb), kSThreads, 0, st>>>(T, SS, W, BA));
-    KEP_LAUNCH(timer, KC_FLUSH_TC, st,
-               lf_flush_tc_kernel<false><<<num_sms, kFlushThreads, kFlushSmem, st>>>(T, SS, W, BA, flops));
+    if (low) go(std::false_type{}, TL{}); else go(std::false_type{}, T8{});
   }
 }
 

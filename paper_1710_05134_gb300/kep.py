@@ -287,8 +287,9 @@ class Problem:
 
     def set_schur_mode(self, emulated: bool, min_front: int = 512, *, fp32: bool = False):
         """Deferred Schur updates of fronts of order >= min_front on the tensor cores (FP64-accurate
-        splitting) when emulated, else FP64 FMA everywhere; fp32: every Schur update in FP32 (a
-        reduced-precision factor for solve_refined)."""
+        splitting) when emulated, else FP64 FMA everywhere; fp32: a reduced-precision factor for
+        solve_refined (fronts of order >= min_front: 4-digit tensor-core splitting, smaller ones
+        FP32 tiles)."""
         mode = KEP_SCHUR_FP32 if fp32 else (KEP_SCHUR_EMULATED if emulated else KEP_SCHUR_FP64)
         _check(lib().kep_set_schur_mode(self._h, mode, int(min_front)), "kep_set_schur_mode")
 

@@ -88,3 +88,21 @@ def test_not_spd_B_rejected(kep):
     with pytest.raises(kep.KepError) as e:
         P.kth_eigenpair(p.k)
     assert e.value.code == kep.KEP_ERR_NOT_SPD
+
+
+def test_kth_eigenpair_shared_b_slot(kep, small):
+    """Algorithm 4 with B's factor in the slot of the shifted factorizations (the layout of the
+    largest problems): B is factored once, the later B-solves run conjugate gradients.  Same
+    interval, counts and lambda_k as with B's own slot, and no further factorization of B."""
+    p, A, B, lam, X = small
+    k = p.k
+    rng = np.random.default_rng(17)
+    sv = rng.normal(size=2 * p.n)
+    with kep.Problem.from_pencil(p) as P:
+        lo, xo, ro = P.kth_eigenpair(k, start_vectors=sv, b_factor="own")
+        ls, xs, rs = P.kth_eigenpair(k, start_vectors=sv, b_factor="shared")
+    _check_pair(p, A, B, lam, X, k, ls, xs, rs)
+    assert abs(ls - lo) <= 1e-12 * np.abs(A).sum(1).max()
+    assert (rs["init_nu_lo"], rs["init_nu_hi"], rs["nu_lo"], rs["nu_hi"]) == \
+        (ro["init_nu_lo"], ro["init_nu_hi"], ro["nu_lo"], ro["nu_hi"])
+    assert rs["n_factor"] == ro["n_factor"]          # B factored once in both layouts

@@ -7,7 +7,7 @@ finite differences in test_oracle_next.py), and the oracle's Gershgorin interval
 import numpy as np
 import pytest
 
-from gen import make_pair
+from gen import make_pair, workload
 from oracle import core, three_stage as ts
 from tests.gpu_util import require_gpu
 
@@ -193,6 +193,37 @@ def test_fp32_factor_refined_solves(kep, pen):
     assert be0 > 1e-12                          # FP32 Schur arithmetic shows without refinement
     assert be <= 1e-13 and be_own <= 2e-13 and 1 <= it <= 10
     assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-10
+
+
+def test_fp32_tensor_core_factor_refined_solves(kep):
+    """The reduced-precision factor with fronts on the tensor cores (4-digit splitting, fronts of
+    order >= 64 here): its plain solve shows the reduced precision, its refined solves reach a
+    backward error of 1e-13 and the oracle's dense solution; the FP64-accurate factor afterwards is
+    unaffected (its counts equal the dense spectrum's)."""
+    p = workload("small")                     # n = 2,048
+    A, B = p.A().toarray(), p.B().toarray()
+    lam, _ = core.gen_eig(A, B)
+    nrm = np.abs(A).sum(1).max()
+    sig = float(core.certified_shifts(lam, 1, 1e-6 * nrm, seed=19)[0])
+    M = A - sig * B
+    nM = np.abs(M).sum(1).max()
+    rng = np.random.default_rng(5)
+    with kep.Problem.from_pencil(p) as P:
+        P.set_schur_mode(False, min_front=64, fp32=True)
+        P.factor(sig)
+        for _ in range(2):
+            rhs = rng.normal(size=p.n)
+            x0 = P.solve(rhs)
+            be0 = np.abs(rhs - M @ x0).max() / (nM * np.abs(x0).max() + np.abs(rhs).max())
+            x, it, be = P.solve_refined(rhs, tol=1e-13)
+            be_own = np.abs(rhs - M @ x).max() / (nM * np.abs(x).max() + np.abs(rhs).max())
+            assert 1e-12 < be0 < 1e-5                # reduced precision, but a usable factor
+            assert be <= 1e-13 and be_own <= 2e-13 and 1 <= it <= 20
+            x_ref = np.linalg.solve(M, rhs)
+            assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-10
+        P.set_schur_mode(True, min_front=64)
+        for s in core.certified_shifts(lam, 4, 1e-8 * nrm, seed=20):
+            assert P.factor(s).neg == core.count_below(lam, s)
 
 
 def test_fp32_factor_refined_near_singular(kep, pen):
