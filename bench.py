@@ -255,10 +255,12 @@ def _cpu_sample_pencil():
     return make_pair(s["nx"], s["ny"], s["nz"], seed=0, vacancies=s["vacancies"])
 
 
-VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_min_front", "gershgorin_multisection8",
+VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_schur", "gershgorin_multisection8",
             "stage3_f32_ir", "hermitian_mid")
 # variants on a workload of their own (run after the main problem is released)
-SEPARATE_VARIANTS = ("multisection_batch", "graph_replay")
+SEPARATE_VARIANTS = ("multisection_batch", "graph_replay", "hermitian_full")
+# run only when named (minutes): the n = 524,288 complex workload at its stated size
+EXPLICIT_VARIANTS = ("hermitian_full",)
 
 
 def measure_variants(P, p, torch, kth, which="all"):
@@ -288,13 +290,16 @@ def measure_variants(P, p, torch, kth, which="all"):
         out["fp32_factor_ir"] = measure_fp32_factor(P, p, torch)
     if "two_shifts_in_flight" in want:
         out["two_shifts_in_flight"] = measure_two_in_flight(P, p, torch)
-    if "autotune_min_front" in want:
+    if "autotune_schur" in want:
         from paper_1710_05134_gb300 import tune
         try:
-            out["autotune_min_front"] = tune.tune_min_front(P, [0.31, 0.33], sync=sync)
+            r = tune.tune_schur(P, [0.31, 0.33], sync=sync)
+            out["autotune_schur"] = {"best": list(r["best"]), "nu": r["nu"],
+                                     "seconds": {f"{k[0]}/{k[1]}": v for k, v in r["seconds"].items()}}
         except Exception as exc:
-            out["autotune_min_front"] = {"error": str(exc)}
-        P.set_schur_mode(True)                         # back to the default for what follows
+            out["autotune_schur"] = {"error": str(exc)}
+        P.set_schur_mode(True)                         # back to the defaults for what follows
+        P.set_schur_tile(64)
     # Algorithm 4 variants
     for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),
                      ("stage3_f32_ir", {"solve_precision": "f32_ir"})):
@@ -446,17 +451,19 @@ def measure_two_in_flight(P, p, torch):
     return res
 
 
-def measure_hermitian(torch):
-    """A complex Hermitian pencil (the n = 49,768 generator with Peierls phases on every atom
-    pair), through the real embedding of order 2n: analysis, factorization, Algorithm 4 and the
-    complex derivatives."""
+def measure_hermitian(torch, name: str = "mid_peierls", refined: bool = False):
+    """A complex Hermitian pencil (the generator with Peierls phases on every atom pair: n = 49,768
+    for mid_peierls, n = 524,288 for scale_peierls, the differentiation workload), through the
+    real embedding of order 2n (each complex variable's two rows ordered together): analysis,
+    factorization, Algorithm 4 and the complex derivatives."""
     import paper_1710_05134_gb300 as kep
     from gen import workload
     sync = torch.cuda.synchronize
-    ph = workload("mid_peierls")
-    res = {"n": ph.n, "nnz": int(ph.rowptr[-1]), "k": ph.k}
+    ph = workload(name)
+    res = {"workload": name, "n": ph.n, "nnz": int(ph.rowptr[-1]), "k": ph.k,
+           "ordering": "refined" if refined else "default"}
     t0 = time.perf_counter()
-    with kep.Problem.from_pencil(ph) as H:
+    with kep.Problem.from_pencil(ph, refined_order=refined) as H:
         res["analyze_s"] = time.perf_counter() - t0
         inf = H.info
         res.update(embedding_n=inf.n, max_front=inf.max_front, flops_per_factorization=inf.flops_factor)
@@ -465,6 +472,7 @@ def measure_hermitian(torch):
         nus = [H.factor(0.30 + 0.013 * i).neg for i in range(3)]
         sync(); res["factor_s"] = (time.perf_counter() - t0) / 3
         res["nu"] = nus
+        res["device_free_gb_before_kth"] = torch.cuda.mem_get_info()[0] / 1e9
         t0 = time.perf_counter()
         try:
             lam, x, rep = H.kth_eigenpair(ph.k)
@@ -684,13 +692,17 @@ def main():
                            "seconds": time.perf_counter() - t0})
     validation["ok"] = validation["monotone"] and validation.get("equal", True)
     if args.variants and rank == 0:
-        sep = SEPARATE_VARIANTS if args.variants == "all" else [v for v in args.variants.split(",")
-                                                               if v in SEPARATE_VARIANTS]
+        sep = [v for v in SEPARATE_VARIANTS if v not in EXPLICIT_VARIANTS] if args.variants == "all" else \
+            [v for v in args.variants.split(",") if v in SEPARATE_VARIANTS]
         variants = variants or {}
         for name in sep:
             try:
-                variants[name] = measure_multisection_batch(torch) if name == "multisection_batch" \
-                    else measure_graph_replay(torch)
+                if name == "multisection_batch":
+                    variants[name] = measure_multisection_batch(torch)
+                elif name == "graph_replay":
+                    variants[name] = measure_graph_replay(torch)
+                else:
+                    variants[name] = measure_hermitian(torch, "scale_peierls", refined=True)
             except Exception as exc:
                 variants[name] = {"error": str(exc)}
 

@@ -195,6 +195,18 @@ kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, const int32_t
 enum { KEP_SCHUR_FP64 = 0, KEP_SCHUR_EMULATED = 1, KEP_SCHUR_FP32 = 2 };
 kep_status kep_set_schur_mode(kep_ctx* ctx, int mode, int64_t min_front);
 
+/*
+ * kep_set_schur_tile - edge of the tiles of the Schur updates that do not run on the tensor cores
+ * (fronts below the tensor-core threshold; FP64, or FP32 in KEP_SCHUR_FP32): 64 (default) or 32.
+ * A tile-shape choice with no effect on the result's accuracy, for the autotuner.  Takes effect at
+ * the next factorization.  Errors: KEP_ERR_INVALID.
+ */
+kep_status kep_set_schur_tile(kep_ctx* ctx, int edge);
+
+/* The current Schur settings of ctx (any pointer may be NULL): mode (KEP_SCHUR_*), tensor-core
+ * threshold, tile edge. */
+kep_status kep_get_schur_config(const kep_ctx* ctx, int* mode, int64_t* min_front, int* tile);
+
 /* Fill *info with the symbolic facts of ctx. */
 kep_status kep_get_info(const kep_ctx* ctx, kep_info* info);
 

@@ -146,6 +146,41 @@ Quotient build_quotient(int64_t n, const std::vector<int64_t>& rp, const std::ve
   return q;
 }
 
+// Quotient of a complex Hermitian pencil's real embedding (order n = 2 h, rows r and r + h the
+// real and imaginary parts of one complex variable, with equal closed neighbourhoods by
+// construction): supernode s = {s, s + h}, weight 2, adjacency that of row s folded onto the pairs.
+// The ordering then sees the complex pattern, and each complex variable's two rows stay together.
+Quotient build_pair_quotient(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci) {
+  Quotient q;
+  const int32_t h = static_cast<int32_t>(n / 2);
+  q.ns = h;
+  q.sn_of.resize(n);
+  for (int64_t i = 0; i < n; ++i) q.sn_of[i] = static_cast<int32_t>(i % h);
+  q.w.assign(h, 2);
+  q.mem_ptr.resize(h + 1);
+  q.mem.resize(n);
+  for (int32_t s = 0; s < h; ++s) {
+    q.mem_ptr[s] = 2 * static_cast<int64_t>(s);
+    q.mem[2 * s] = s;
+    q.mem[2 * s + 1] = s + h;
+  }
+  q.mem_ptr[h] = n;
+  q.qrp.assign(h + 1, 0);
+  std::vector<int32_t> tmp;
+  for (int32_t s = 0; s < h; ++s) {
+    tmp.clear();
+    for (int64_t e = rp[s]; e < rp[s + 1]; ++e) {
+      const int32_t t = ci[e] % h;
+      if (t != s) tmp.push_back(t);
+    }
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    q.qci.insert(q.qci.end(), tmp.begin(), tmp.end());
+    q.qrp[s + 1] = static_cast<int64_t>(q.qci.size());
+  }
+  return q;
+}
+
 struct ND {
   const Quotient& q;
   const double* coords;          // per row (n x 3) or null
@@ -482,8 +517,8 @@ void plan_memory(Plan& P, int32_t slack_base) {
 
 kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                       const std::vector<double>& av, const std::vector<double>& bv,
-                      const double* coords, bool graph_order, bool refined, int32_t slack_base, Plan& P,
-                      std::string& err) {
+                      const double* coords, bool graph_order, bool refined, bool pairs, int32_t slack_base,
+                      Plan& P, std::string& err) {
   P = Plan();
   P.n = n;
   P.nnz = rp[n];
@@ -493,7 +528,8 @@ kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vect
     for (int64_t e = rp[i]; e < rp[i + 1]; ++e) s += std::fabs(av[e]);
     P.norm_a_inf = std::max(P.norm_a_inf, s);
   }
-  Quotient q = build_quotient(n, rp, ci);
+  if (pairs && (n % 2 != 0)) { err = "paired ordering needs an even order"; return KEP_ERR_INVALID; }
+  Quotient q = pairs ? build_pair_quotient(n, rp, ci) : build_quotient(n, rp, ci);
   ND nd(q, graph_order ? nullptr : coords, /*leaf rows*/ 64);
   nd.refined = refined;
   std::vector<int32_t> all(q.ns);

@@ -252,6 +252,7 @@ static kep_status factor_set(kep_ctx* c, int G, FactorSlot* const* slots, double
   // the reduced-precision factor's 4 digits; smaller fronts FP64 or FP32 FMA tiles
   F.emul_min = c->schur_mode == KEP_SCHUR_FP64 ? 0 : c->emul_min_front;
   F.fp32_schur = c->schur_mode == KEP_SCHUR_FP32;
+  F.schur_tile = c->schur_tile;
   F.emul_ws = nullptr;
   F.d_emul_off = nullptr;
   F.h_emul_end = nullptr;
@@ -641,7 +642,8 @@ kep_status kep_analyze(int64_t n, const int64_t* rowptr, const int32_t* colind, 
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return KEP_ERR_CUDA; }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   std::string err;
-  kep_status st = build_plan(n, cnt, ci, av, bv, coords, (flags & KEP_ORDER_GRAPH) != 0, (flags & KEP_ORDER_REFINED) != 0, 8, c->plan, err);
+  kep_status st = build_plan(n, cnt, ci, av, bv, coords, (flags & KEP_ORDER_GRAPH) != 0, (flags & KEP_ORDER_REFINED) != 0,
+                             (flags & kOrderPairs) != 0, 8, c->plan, err);
   if (st != KEP_OK) { delete c; return st; }
   const Plan& P = c->plan;
 #define UP(dst, vec) do { st = dev_upload(c, &dst, vec); if (st != KEP_OK) { kep_destroy(c); return st; } } while (0)
@@ -723,7 +725,8 @@ kep_status kep_symbolic_info(int64_t n, const int64_t* rowptr, const int32_t* co
   if (ps != KEP_OK) return ps;
   Plan P;
   std::string err;
-  const kep_status st = build_plan(n, FP.cnt, FP.ci, FP.av, FP.bv, coords, (flags & KEP_ORDER_GRAPH) != 0, (flags & KEP_ORDER_REFINED) != 0, 8, P, err);
+  const kep_status st = build_plan(n, FP.cnt, FP.ci, FP.av, FP.bv, coords, (flags & KEP_ORDER_GRAPH) != 0, (flags & KEP_ORDER_REFINED) != 0,
+                                   false, 8, P, err);
   if (st != KEP_OK) return st;
   info->n = P.n;
   info->nnz = P.nnz;
@@ -747,6 +750,20 @@ kep_status kep_set_schur_mode(kep_ctx* c, int mode, int64_t min_front) {
     return KEP_ERR_INVALID;
   c->schur_mode = mode;
   c->emul_min_front = min_front;
+  return KEP_OK;
+}
+
+kep_status kep_set_schur_tile(kep_ctx* c, int edge) {
+  if (!c || (edge != 32 && edge != 64)) return KEP_ERR_INVALID;
+  c->schur_tile = edge;
+  return KEP_OK;
+}
+
+kep_status kep_get_schur_config(const kep_ctx* c, int* mode, int64_t* min_front, int* tile) {
+  if (!c) return KEP_ERR_INVALID;
+  if (mode) *mode = c->schur_mode;
+  if (min_front) *min_front = c->emul_min_front;
+  if (tile) *tile = c->schur_tile;
   return KEP_OK;
 }
 

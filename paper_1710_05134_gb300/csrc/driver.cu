@@ -396,17 +396,39 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   if (params) prm = *params; else kep_default_params(&prm);
   if (prm.m_max < 1 || prm.max_lanczos < 2 || prm.max_si < 1) return KEP_ERR_INVALID;
   if (prm.b_factor < KEP_BFACTOR_AUTO || prm.b_factor > KEP_BFACTOR_OWN) return KEP_ERR_INVALID;
-  const int64_t cap = std::min<int64_t>(n + 1, std::max(prm.max_lanczos, prm.max_si) + 2);
+  int64_t cap = std::min<int64_t>(n + 1, std::max(prm.max_lanczos, prm.max_si) + 2);
   Driver* d = static_cast<Driver*>(c->driver);
   if (!d || d->cap_cols < cap) {
     c->driver_release();
     d = new Driver();
     c->driver = d;
-    d->cap_cols = cap;
     d->nblocks = std::max(1, std::min<int>(c->num_sms * 4, static_cast<int>((n + 255) / 256)));
-    if (cudaMalloc(&d->V, sizeof(double) * n * cap) != cudaSuccess ||
-        cudaMalloc(&d->BV, sizeof(double) * n * cap) != cudaSuccess ||
-        cudaMalloc(&d->w, sizeof(double) * n) != cudaSuccess ||
+    // the Lanczos bases V and B V: the columns asked for, fewer (at least 64) when device memory is
+    // short (the largest problems: 2 GB stay free for the work vectors and the solves' buffers);
+    // the iterations then stop at the basis size
+    const int64_t cap_min = std::min<int64_t>(cap, 64);
+    {
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const int64_t room = static_cast<int64_t>(free_b) - (2ll << 30);
+        const int64_t fit = room > 0 ? room / (16 * n) : 0;
+        cap = std::max(cap_min, std::min(cap, fit));
+      } else {
+        cudaGetLastError();
+      }
+    }
+    while (true) {
+      if (cudaMalloc(&d->V, sizeof(double) * n * cap) == cudaSuccess) {
+        if (cudaMalloc(&d->BV, sizeof(double) * n * cap) == cudaSuccess) break;
+        cudaFree(d->V);
+      }
+      d->V = d->BV = nullptr;
+      cudaGetLastError();
+      if (cap == cap_min) { c->driver_release(); return KEP_ERR_NOMEM; }
+      cap = std::max(cap_min, cap * 3 / 4);
+    }
+    d->cap_cols = cap;
+    if (cudaMalloc(&d->w, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&d->u, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&d->u2, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&d->coef, sizeof(double) * cap) != cudaSuccess ||
@@ -415,6 +437,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
       return KEP_ERR_NOMEM;
     }
   }
+  cap = std::min(cap, d->cap_cols);
   Run R;
   R.c = c; R.d = d; R.n = n; R.norm_a = c->plan.norm_a_inf;
   R.ops.n = n; R.ops.num_blocks = d->nblocks; R.ops.partial = d->partial; R.ops.stream = c->stream;

@@ -18,6 +18,7 @@
 //   inertia    the sign rule for 1x1 and 2x2 pivots of D, summed per front.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "kep_device.cuh"
 
@@ -25,8 +26,11 @@ namespace kep {
 
 namespace {
 
-constexpr int kTile = 64;          // Schur-update tile edge
+constexpr int kTile = 64;          // default FP64 Schur-update tile edge (32 or 64, chosen per context)
 constexpr int kRowTile = 64;       // rows per CTA in the row-parallel kernels
+
+template <typename X>
+struct TypeTag { using type = X; };
 
 KEP_D int32_t children_delays(const FrontTables& T, const FactorSlot& S, int32_t t, bool& bad) {
   int32_t d = 0;
@@ -615,19 +619,20 @@ __global__ void __launch_bounds__(128) lf_apply_kernel(FrontTables T, SlotSet SS
 // Schur update of the trailing matrix: C(i, j) -= sum_c L(i, c) (L D)(j, c) over the q accepted
 // pivots, for s = k + q <= j <= i < m.  64 x 64 tiles, 256 threads with 4 x 4 register tiles.
 // ------------------------------------------------------------------------------------------
-// Block partition of a trailing region that starts at s: blocks of kTile rows/columns, split at p
+// Block partition of a trailing region that starts at s: blocks of TS rows/columns, split at p
 // (the boundary between L storage and the contribution block), up to m.
+template <int TS>
 struct Part {
   int32_t s, p, m, nL, base2, nR;
   KEP_D void init(int32_t s_, int32_t p_, int32_t m_) {
     s = s_; p = p_; m = m_;
-    nL = s < p ? (p - s + kTile - 1) / kTile : 0;
+    nL = s < p ? (p - s + TS - 1) / TS : 0;
     base2 = s > p ? s : p;
-    nR = nL + (m > base2 ? (m - base2 + kTile - 1) / kTile : 0);
+    nR = nL + (m > base2 ? (m - base2 + TS - 1) / TS : 0);
   }
-  KEP_D int32_t lo(int32_t b) const { return b < nL ? s + b * kTile : base2 + (b - nL) * kTile; }
+  KEP_D int32_t lo(int32_t b) const { return b < nL ? s + b * TS : base2 + (b - nL) * TS; }
   KEP_D int32_t hi(int32_t b) const {
-    return b < nL ? min(s + (b + 1) * kTile, p) : min(base2 + (b - nL + 1) * kTile, m);
+    return b < nL ? min(s + (b + 1) * TS, p) : min(base2 + (b - nL + 1) * TS, m);
   }
 };
 
@@ -637,13 +642,15 @@ struct Part {
 //  WINDOW = false: the deferred update of everything right of the window with all pivots the
 //                  window accepted (c0 = window start, c1 = its last accepted pivot + 1,
 //                  s = ce' = window end, ce = m), issued once per window ("flush").
-// 64 x 64 tiles, 256 threads with 4 x 4 FP64 register tiles, the pivot range in chunks of 32.
+// TS x TS tiles (TS = 32 or 64, the context's choice), 256 threads with (TS/16) x (TS/16) register
+// tiles, the pivot range in chunks of 32.
 // R: arithmetic of the tiles (double, or float for the reduced-precision factorization mode)
-template <bool WINDOW, typename R>
+template <bool WINDOW, typename R, int TS>
 __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, SlotSet SS, LargeWork W, Batch B,
                                                        unsigned long long* flops) {
-  __shared__ R Ai[kPanel][kTile + 1];
-  __shared__ R Wj[kPanel][kTile + 1];
+  constexpr int RT = TS / 16;
+  __shared__ R Ai[kPanel][TS + 1];
+  __shared__ R Wj[kPanel][TS + 1];
   const int32_t b = B.e0 + blockIdx.y;
   int32_t c0, c1, s, ce;
   if (WINDOW) {
@@ -662,7 +669,7 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, SlotSet SS
   const FrontView v = front_view(T, S, SS.cbpool[g], t, d_in);
   if (!WINDOW) ce = v.m;
   if (c1 <= c0 || s >= ce) return;
-  Part P;
+  Part<TS> P;
   P.init(s, v.p, v.m);
   int32_t nJ = 0;
   while (nJ < P.nR && P.lo(nJ) < ce) ++nJ;
@@ -692,17 +699,17 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, SlotSet SS
     const int32_t bi = bj + static_cast<int32_t>(tile - stj);
     const int32_t I0 = P.lo(bi), I1 = P.hi(bi);
     const int32_t J0 = P.lo(bj), J1 = min(P.hi(bj), ce);
-    R acc[4][4];
+    R acc[RT][RT];
 #pragma unroll
-    for (int32_t x = 0; x < 4; ++x)
+    for (int32_t x = 0; x < RT; ++x)
 #pragma unroll
-      for (int32_t y = 0; y < 4; ++y) acc[x][y] = R(0);
+      for (int32_t y = 0; y < RT; ++y) acc[x][y] = R(0);
     for (int32_t k0 = c0; k0 < c1; k0 += kPanel) {
       const int32_t kn = min(kPanel, c1 - k0);
       __syncthreads();
       // A_I = L(I, chunk) and W_J = L(J, chunk) D (a 2x2 block mixes its two columns)
-      for (int32_t e = threadIdx.x; e < kPanel * kTile; e += blockDim.x) {
-        const int32_t r = e % kTile, cc = e / kTile;
+      for (int32_t e = threadIdx.x; e < kPanel * TS; e += blockDim.x) {
+        const int32_t r = e % TS, cc = e / TS;
         double ai = 0.0, wj = 0.0;
         if (cc < kn) {
           const int32_t c = k0 + cc;
@@ -726,23 +733,23 @@ __global__ void __launch_bounds__(256) lf_schur_kernel(FrontTables T, SlotSet SS
       }
       __syncthreads();
       for (int32_t cc = 0; cc < kn; ++cc) {
-        R a[4], wv[4];
+        R a[RT], wv[RT];
 #pragma unroll
-        for (int32_t x = 0; x < 4; ++x) a[x] = Ai[cc][ty + 16 * x];
+        for (int32_t x = 0; x < RT; ++x) a[x] = Ai[cc][ty + 16 * x];
 #pragma unroll
-        for (int32_t y = 0; y < 4; ++y) wv[y] = Wj[cc][tx + 16 * y];
+        for (int32_t y = 0; y < RT; ++y) wv[y] = Wj[cc][tx + 16 * y];
 #pragma unroll
-        for (int32_t x = 0; x < 4; ++x)
+        for (int32_t x = 0; x < RT; ++x)
 #pragma unroll
-          for (int32_t y = 0; y < 4; ++y) acc[x][y] = fma(a[x], wv[y], acc[x][y]);
+          for (int32_t y = 0; y < RT; ++y) acc[x][y] = fma(a[x], wv[y], acc[x][y]);
       }
     }
 #pragma unroll
-    for (int32_t y = 0; y < 4; ++y) {
+    for (int32_t y = 0; y < RT; ++y) {
       const int32_t j = J0 + tx + 16 * y;
       if (j >= J1) continue;
 #pragma unroll
-      for (int32_t x = 0; x < 4; ++x) {
+      for (int32_t x = 0; x < RT; ++x) {
         const int32_t i = I0 + ty + 16 * x;
         if (i < I1 && i >= j) *v.at(i, j) -= static_cast<double>(acc[x][y]);
       }
@@ -848,10 +855,11 @@ kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_i
       const int64_t per_front = std::max<int64_t>((target + nb - 1) / nb, F.num_sms);
       const int gx_rows = grid_cap(rowtiles, per_front);
       const int gx_apply = grid_cap(rowtiles + max_p / 32 + 2, per_front);
-      const int64_t tb = (max_m + kTile - 1) / kTile + 1;
+      const int TS = F.schur_tile == 32 ? 32 : kTile;
+      const int64_t tb = (max_m + TS - 1) / TS + 1;
       const int64_t per_front_upd = std::max<int64_t>((F.num_sms * 4 + nb - 1) / nb, 2 * F.num_sms);
       const int gx_upd = grid_cap(tb * (tb + 1) / 2, per_front_upd);
-      const int gx_win = grid_cap(tb * (kWindow / kTile + 1), per_front_upd);
+      const int gx_win = grid_cap(tb * (kWindow / TS + 1), per_front_upd);
       int64_t steps = (max_p + kPanel - 1) / kPanel + 1;
       // a guard, not a tuning knob: every step eliminates or moves on from a block, and a column
       // that fails the threshold is retried at most once per pass over the remaining columns
@@ -872,20 +880,27 @@ kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_i
                                F.num_sms, F.timer, F.flops);
             launch_emul_update(false, F.fp32_schur, F.T, F.SS, F.W, B, nb, F.emul_ws, F.d_emul_off + lb + e, max_m, sx,
                                F.num_sms, F.timer, F.flops);
-          } else if (F.fp32_schur) {
-            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
-                       lf_schur_kernel<true, float><<<dim3(gx_win, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
-                                                                                     F.flops + KC_UPDATE));
-            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
-                       lf_schur_kernel<false, float><<<dim3(gx_upd, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
-                                                                                       F.flops + KC_UPDATE));
           } else {
-            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
-                       lf_schur_kernel<true, double><<<dim3(gx_win, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
-                                                                                      F.flops + KC_UPDATE));
-            KEP_LAUNCH(F.timer, KC_UPDATE, sx,
-                       lf_schur_kernel<false, double><<<dim3(gx_upd, nb), 256, 0, sx>>>(F.T, F.SS, F.W, B,
-                                                                                        F.flops + KC_UPDATE));
+            // FP64 (or, for the reduced-precision factor, FP32) tiles of the context's edge
+            auto upd = [&](auto win, auto real, auto edge) {
+              constexpr bool W_ = decltype(win)::value;
+              using R_ = typename decltype(real)::type;
+              constexpr int T_ = decltype(edge)::value;
+              KEP_LAUNCH(F.timer, KC_UPDATE, sx,
+                         (lf_schur_kernel<W_, R_, T_><<<dim3(W_ ? gx_win : gx_upd, nb), 256, 0, sx>>>(
+                             F.T, F.SS, F.W, B, F.flops + KC_UPDATE)));
+            };
+            auto both = [&](auto real, auto edge) {
+              upd(std::true_type{}, real, edge);
+              upd(std::false_type{}, real, edge);
+            };
+            using E32 = std::integral_constant<int, 32>;
+            using E64 = std::integral_constant<int, kTile>;
+            if (F.fp32_schur) {
+              if (TS == 32) both(TypeTag<float>{}, E32{}); else both(TypeTag<float>{}, E64{});
+            } else {
+              if (TS == 32) both(TypeTag<double>{}, E32{}); else both(TypeTag<double>{}, E64{});
+            }
           }
         }
         KEP_LAUNCH(F.timer, KC_PANEL, sx, lf_panel_kernel<<<nb, kPanelThreads, 0, sx>>>(F.T, F.SS, F.W, B));
@@ -898,6 +913,7 @@ kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_i
           const std::vector<uint64_t> key = {
               static_cast<uint64_t>(l), static_cast<uint64_t>(e), static_cast<uint64_t>(nb),
               static_cast<uint64_t>(steps), static_cast<uint64_t>(G), static_cast<uint64_t>(F.emul_min),
+              static_cast<uint64_t>(TS),
               (emul ? 1ull : 0ull) | (F.fp32_schur ? 2ull : 0ull),
               reinterpret_cast<uint64_t>(F.SS.s[0].F), reinterpret_cast<uint64_t>(F.SS.s[G - 1].F),
               reinterpret_cast<uint64_t>(F.W.done), reinterpret_cast<uint64_t>(F.emul_ws),

@@ -189,7 +189,8 @@ extern "C" kep_status kep_analyze_hermitian(int64_t n, const int64_t* rowptr, co
   }
   kep_ctx* c = nullptr;
   const kep_status st = kep_analyze(N, cnt.data(), ci.data(), av.data(), bv.data(),
-                                    KEP_PATTERN_FULL | (flags & (KEP_ORDER_GRAPH | KEP_ORDER_REFINED)), coords ? co.data() : nullptr, &c);
+                                    KEP_PATTERN_FULL | (flags & (KEP_ORDER_GRAPH | KEP_ORDER_REFINED)) | kOrderPairs,
+                                    coords ? co.data() : nullptr, &c);
   if (st != KEP_OK) return st;
   c->herm_n = n;
   c->herm_nnz = nnz_in;

@@ -93,6 +93,7 @@ struct kep_ctx {
   kep::Timer timer;
   int schur_mode = KEP_SCHUR_EMULATED;
   int64_t emul_min_front = 512;
+  int schur_tile = 64;              // edge of the FP64/FP32 Schur tiles (kep_set_schur_tile)
   void* emul_ws = nullptr;          // tensor-core update workspace (in mem_allocs)
   int64_t emul_bytes = 0;           // its size
   // multisection: G shifts factored in the same launches (kep_factor_multi).  Shift G - 1 uses

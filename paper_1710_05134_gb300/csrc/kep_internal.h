@@ -135,11 +135,15 @@ struct Plan {
 
 // Build the plan from a full symmetric CSR pattern (both triangles, sorted, no duplicates).
 // coords: optional n*3. graph_order forces the coordinate-free ordering; refined selects the
-// cut search with minimum-vertex-cover separators.
+// cut search with minimum-vertex-cover separators; pairs orders rows r and r + n/2 together (the
+// real embedding of a complex Hermitian pencil).
 kep_status build_plan(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                       const std::vector<double>& av, const std::vector<double>& bv,
-                      const double* coords, bool graph_order, bool refined, int32_t slack_base, Plan& plan,
-                      std::string& err);
+                      const double* coords, bool graph_order, bool refined, bool pairs, int32_t slack_base,
+                      Plan& plan, std::string& err);
+
+// kep_analyze flag used by kep_analyze_hermitian only: order the embedding's rows in pairs
+constexpr int kOrderPairs = 1 << 20;
 
 // (Re)compute the slack-dependent memory plan.
 void plan_memory(Plan& plan, int32_t slack_base);
@@ -278,6 +282,7 @@ struct FactorLaunch {
   Timer* timer;
   int64_t emul_min;         // fronts with m_alloc >= this use the tensor-core flush (0: never)
   bool fp32_schur = false;  // Schur tiles in FP32 arithmetic (reduced-precision factor for refined solves)
+  int schur_tile = 64;      // edge of the FP64/FP32 Schur tiles: 32 or 64
   void* emul_ws;            // its workspace
   const int64_t* d_emul_off;      // per entry: byte offset of the entry's workspace in its batch
   const int32_t* h_emul_end;      // per entry starting a batch of such entries: its end (level-relative)

@@ -26,7 +26,7 @@ EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_g
             "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi", "kep_solve_refined",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
             "kep_multisection_points", "kep_multisection_update", "kep_set_graphs",
-            "kep_set_schur_mode"]
+            "kep_set_schur_mode", "kep_set_schur_tile", "kep_get_schur_config"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
 KEP_INIT_LANCZOS, KEP_INIT_GERSHGORIN = 0, 1
 KEP_SOLVE_F64, KEP_SOLVE_F32_IR = 0, 1
@@ -128,6 +128,10 @@ def lib() -> ctypes.CDLL:
         L.kep_dense_inertia_noalloc.restype = I
         L.kep_set_schur_mode.argtypes = [P, I, I64]
         L.kep_set_schur_mode.restype = I
+        L.kep_set_schur_tile.argtypes = [P, I]
+        L.kep_set_schur_tile.restype = I
+        L.kep_get_schur_config.argtypes = [P, P, P, P]
+        L.kep_get_schur_config.restype = I
         L.kep_destroy.argtypes = [P]
         L.kep_destroy.restype = None
         L.kep_status_str.argtypes = [I]
@@ -292,6 +296,17 @@ class Problem:
         FP32 tiles)."""
         mode = KEP_SCHUR_FP32 if fp32 else (KEP_SCHUR_EMULATED if emulated else KEP_SCHUR_FP64)
         _check(lib().kep_set_schur_mode(self._h, mode, int(min_front)), "kep_set_schur_mode")
+
+    def set_schur_tile(self, edge: int):
+        """Edge (32 or 64) of the Schur tiles of fronts below the tensor-core threshold."""
+        _check(lib().kep_set_schur_tile(self._h, int(edge)), "kep_set_schur_tile")
+
+    def schur_config(self) -> dict:
+        """{"mode": KEP_SCHUR_*, "min_front": tensor-core threshold, "tile": tile edge}."""
+        mode, mf, tile = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().kep_get_schur_config(self._h, ctypes.byref(mode), ctypes.byref(mf), ctypes.byref(tile)),
+               "kep_get_schur_config")
+        return {"mode": mode.value, "min_front": mf.value, "tile": tile.value}
 
     def solve_refined(self, rhs, tol: float = 1e-13, max_iter: int = 100):
         """(x, GMRES steps, backward error): GMRES-based iterative refinement preconditioned by the

@@ -247,3 +247,25 @@ def test_solve_two_by_two_pivots_and_delays_dataflow(kep):
         xr = np.linalg.solve(M, b)
         assert np.abs(x - xr).max() <= 1e-8 * np.abs(xr).max()
         assert np.linalg.norm(M @ x - b) <= 1e-12 * np.linalg.norm(M, np.inf) * np.linalg.norm(x)
+
+
+def test_schur_tile_32_parity(kep, small):
+    """The 32 x 32 FP64 Schur tiles (the autotuner's other tile shape) give the same exact counts
+    as the dense spectrum and solves of the same accuracy, with every front below the tensor-core
+    threshold."""
+    p, A, B, lam = small
+    nrm = np.abs(A).sum(1).max()
+    with kep.Problem.from_pencil(p) as P:
+        P.set_schur_mode(False)
+        P.set_schur_tile(32)
+        assert P.schur_config()["tile"] == 32
+        for s in core.certified_shifts(lam, 8, 1e-8 * nrm, seed=23):
+            r = P.factor(s)
+            ref = core.count_below(lam, s)
+            assert (r.neg, r.zero, r.pos) == (ref, 0, p.n - ref), s
+        b = np.random.default_rng(12).normal(size=p.n)
+        x = P.solve(b)
+        M = A - s * B
+        assert np.linalg.norm(M @ x - b) <= 1e-13 * np.linalg.norm(M, np.inf) * np.linalg.norm(x)
+        with pytest.raises(kep.KepError):
+            P.set_schur_tile(48)

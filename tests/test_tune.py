@@ -59,3 +59,38 @@ def test_changing_counts_are_rejected():
         tune.tune_min_front(P, [0.1], candidates=(512, 1024), clock=clk)
     with pytest.raises(ValueError):
         tune.tune_min_front(P, [], clock=clk)
+
+
+class _Fake2(_Fake):
+    def __init__(self, clock, cost, nu_of=lambda s, mf, tile: int(100 * s)):
+        super().__init__(clock, None)
+        self.cost2, self.nu_of2 = cost, nu_of
+        self.tile = 64
+
+    def set_schur_tile(self, edge):
+        self.tile = edge
+
+    def factor(self, s):
+        self.clock.t += self.cost2(self.mf, self.tile)
+        self.calls.append((self.mf, self.tile, s))
+
+        class R:
+            pass
+        r = R()
+        r.neg = self.nu_of2(s, self.mf, self.tile)
+        return r
+
+
+def test_joint_threshold_and_tile():
+    clk = _Clock()
+    cost = lambda mf, tile: 1.0 + abs(mf - 512) / 1000.0 + (0.1 if tile == 64 else 0.0)
+    P = _Fake2(clk, cost)
+    out = tune.tune_schur(P, [0.3], thresholds=(256, 512, 1024), tiles=(32, 64), clock=clk)
+    assert out["best"] == (512, 32) and (P.mf, P.tile) == (512, 32)
+    assert len(out["seconds"]) == 6 and len(P.calls) == 6 * 2
+    clk2 = _Clock()
+    P2 = _Fake2(clk2, lambda mf, tile: 1.0)
+    assert tune.tune_schur(P2, [0.3], clock=clk2)["best"] == (1024, 64)      # ties: larger values
+    P3 = _Fake2(_Clock(), lambda mf, tile: 1.0, nu_of=lambda s, mf, tile: 5 if tile == 32 else 6)
+    with pytest.raises(RuntimeError):
+        tune.tune_schur(P3, [0.3], clock=P3.clock)
