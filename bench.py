@@ -478,9 +478,11 @@ def measure_hermitian(torch, name: str = "mid_peierls", refined: bool = False):
             lam, x, rep = H.kth_eigenpair(ph.k)
         except Exception as exc:
             res["kth_error"] = str(exc)
+            res["storage_replans"] = H.info.replans
             return res
         res.update(time_to_lambda_k_s=time.perf_counter() - t0, lambda_k=lam, rel_res=rep["rel_res"],
-                   n_factor=rep["n_factor"], n_si_iter=rep["n_si_iter"])
+                   n_factor=rep["n_factor"], n_si_iter=rep["n_si_iter"], t_stage=rep["t_stage"],
+                   storage_replans=H.info.replans)
         xd = torch.from_numpy(x).cuda()
         H.grad(lam, xd)
         sync(); t0 = time.perf_counter()

@@ -71,6 +71,8 @@ typedef struct {
   int64_t nnz_factor;         /* #nzf: entries of L and D (symbolic, without delays) */
   double flops_factor;        /* multiply-add = 2 flops, symbolic count for one factorization */
   int64_t front_bytes;        /* device bytes of one factor slot's front storage */
+  int64_t replans;            /* times the storage was re-planned because delayed pivots overflowed
+                                 a front's slack (only the overflowing fronts grow) */
 } kep_info;
 
 /* Parameters of Algorithm 4 (Section 3.4) and of the stage-3 iteration. */

@@ -483,12 +483,21 @@ struct ND {
 // and the per-level L21 panel workspace.  Leaves never receive delayed columns (no slack).
 void plan_memory(Plan& P, int32_t slack_base) {
   const int32_t nt = P.nfronts;
-  P.slack.resize(nt); P.m_alloc.resize(nt); P.p_alloc.resize(nt);
-  P.front_off.assign(nt + 1, 0); P.vec_off.assign(nt + 1, 0); P.piv_off.assign(nt + 1, 0);
+  P.slack.resize(nt);
   for (int32_t t = 0; t < nt; ++t) {
     const bool leaf = P.child_ptr[t + 1] == P.child_ptr[t];
-    int32_t s = leaf ? 0 : slack_base + static_cast<int32_t>(static_cast<int64_t>(P.m_sym[t]) * slack_base / 128);
-    P.slack[t] = s;
+    P.slack[t] = leaf ? 0 : slack_base + static_cast<int32_t>(static_cast<int64_t>(P.m_sym[t]) * slack_base / 128);
+  }
+  P.slack_base = slack_base;
+  layout_memory(P);
+}
+
+void layout_memory(Plan& P) {
+  const int32_t nt = P.nfronts;
+  P.m_alloc.resize(nt); P.p_alloc.resize(nt);
+  P.front_off.assign(nt + 1, 0); P.vec_off.assign(nt + 1, 0); P.piv_off.assign(nt + 1, 0);
+  for (int32_t t = 0; t < nt; ++t) {
+    const int32_t s = P.slack[t];
     P.m_alloc[t] = P.m_sym[t] + s;
     P.p_alloc[t] = P.p_sym[t] + s;
     int64_t sz = static_cast<int64_t>(P.m_alloc[t]) * P.p_alloc[t];
@@ -500,7 +509,6 @@ void plan_memory(Plan& P, int32_t slack_base) {
   P.front_total = P.front_off[nt];
   P.vec_total = P.vec_off[nt];
   P.piv_total = P.piv_off[nt];
-  P.slack_base = slack_base;
   P.p21_off.assign(nt, 0);
   P.max_large_rows = 0;
   if (P.level_ptr.size() != static_cast<size_t>(P.nlevels) + 1) return;

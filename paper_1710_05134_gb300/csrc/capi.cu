@@ -133,11 +133,30 @@ void release_memory(kep_ctx* c) {
   }
 }
 
-// Delayed pivots overflowed a front's slack: grow the slack of every non-leaf front and rebuild
-// the slack-dependent storage (the ordering, tree and index maps stay).
-static kep_status replan(kep_ctx* c, int32_t slack_base) {
+// Delayed pivots overflowed the slack of some fronts of the given factorizations: grow those
+// fronts' slack to what they had to hold (plus a quarter and 16), or, when no front recorded a
+// size, every non-leaf front's slack twofold; then rebuild the slack-dependent storage (the
+// ordering, tree and index maps stay).  Only the fronts that overflowed grow, so the storage of the
+// largest problems stays within the device.
+static kep_status replan(kep_ctx* c, const std::vector<const FactorSlot*>& failed) {
+  Plan& P = c->plan;
+  std::vector<int32_t> din(P.nfronts);
+  bool grew = false;
+  for (const FactorSlot* S : failed) {
+    if (cudaMemcpy(din.data(), S->d_in, sizeof(int32_t) * P.nfronts, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return KEP_ERR_CUDA;
+    for (int32_t t = 0; t < P.nfronts; ++t)
+      if (din[t] < -1) {
+        const int64_t need = -static_cast<int64_t>(din[t]) - 1;
+        const int32_t ns = static_cast<int32_t>(need + need / 4 + 16);
+        if (ns > P.slack[t]) { P.slack[t] = ns; grew = true; }
+      }
+  }
+  if (!grew)
+    for (int32_t t = 0; t < P.nfronts; ++t)
+      if (P.child_ptr[t + 1] != P.child_ptr[t]) P.slack[t] = std::max(2 * P.slack[t], 16);
   release_memory(c);
-  plan_memory(c->plan, slack_base);
+  layout_memory(P);
   ++c->replans;
   return setup_memory(c);
 }
@@ -319,8 +338,8 @@ kep_status ctx_factor(kep_ctx* c, int slot, double ca, double cb, kep_inertia* o
     KEP_TRY(alloc_slot(c, slot));
     int bits = 0;
     kep_status st = ctx_factor_once(c, slot, ca, cb, out, &bits);
-    if (st == KEP_ERR_POOL && (bits & ST_POOL) && attempt < 4) {
-      KEP_TRY(replan(c, c->plan.slack_base * 4));
+    if (st == KEP_ERR_POOL && (bits & ST_POOL) && attempt < 8) {
+      KEP_TRY(replan(c, {&c->slot[slot]}));
       continue;
     }
     return herm_counts(c, st, out);
@@ -714,6 +733,7 @@ kep_status kep_get_info(const kep_ctx* c, kep_info* info) {
   info->nnz_factor = P.nnz_factor;
   info->flops_factor = P.flops;
   info->front_bytes = P.front_total * 8;
+  info->replans = c->replans;
   return KEP_OK;
 }
 
@@ -736,6 +756,7 @@ kep_status kep_symbolic_info(int64_t n, const int64_t* rowptr, const int32_t* co
   info->nnz_factor = P.nnz_factor;
   info->flops_factor = P.flops;
   info->front_bytes = P.front_total * 8;
+  info->replans = 0;
   return KEP_OK;
 }
 
@@ -1038,6 +1059,7 @@ kep_status kep_factor_multi(kep_ctx* c, const double* sigmas, int32_t ns, kep_in
   }
   for (int attempt = 0;; ++attempt) {
     bool redo = false;
+    std::vector<const FactorSlot*> failed;
     for (int32_t q0 = 0; q0 < ns && !redo; q0 += G) {
       const int gs = static_cast<int>(std::min<int32_t>(G, ns - q0));
       KEP_TRY(alloc_slot(c, 0));
@@ -1068,7 +1090,11 @@ kep_status kep_factor_multi(kep_ctx* c, const double* sigmas, int32_t ns, kep_in
       }
       KEP_TRY(factor_set(c, gs, slots, pools, p21, ca, cb, in, bits));
       for (int j = 0; j < gs; ++j) redo = redo || (bits[j] & ST_POOL);
-      if (redo) break;
+      if (redo) {
+        for (int j = 0; j < gs; ++j)
+          if (bits[j] & ST_POOL) failed.push_back(slots[j]);
+        break;
+      }
       KEP_TRY(record_slot(c, 0, bits[gs - 1]));
       for (int j = 0; j < gs; ++j) {
         out[q0 + j] = in[j];
@@ -1079,8 +1105,8 @@ kep_status kep_factor_multi(kep_ctx* c, const double* sigmas, int32_t ns, kep_in
       }
     }
     if (!redo) return KEP_OK;
-    if (attempt >= 4) return KEP_ERR_POOL;
-    KEP_TRY(replan(c, c->plan.slack_base * 4));
+    if (attempt >= 8) return KEP_ERR_POOL;
+    KEP_TRY(replan(c, failed));
   }
 }
 

@@ -51,11 +51,13 @@ __global__ void lf_init_kernel(FrontTables T, SlotSet SS, LargeWork W, Batch B) 
   const int32_t g = entry_shift(B, b);
   const FactorSlot& S = SS.s[g];
   double* const cbpool = SS.cbpool[g];
-  bool bad = false;
-  const int32_t d_in = children_delays(T, S, t, bad);
-  if (d_in > T.m_alloc[t] - T.m_sym[t]) bad = true;
+  bool child_bad = false;
+  const int32_t d_in = children_delays(T, S, t, child_bad);
+  const bool over = d_in > T.m_alloc[t] - T.m_sym[t];
+  const bool bad = child_bad || over;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S.d_in[t] = bad ? -1 : d_in;
+    // a failed front records how many delayed columns it would have had to hold
+    S.d_in[t] = bad ? -((over && !child_bad) ? d_in : 0) - 1 : d_in;
     S.nelim[t] = 0;
     S.d_out[t] = 0;
     S.cnt[3 * t] = S.cnt[3 * t + 1] = S.cnt[3 * t + 2] = 0;

@@ -147,6 +147,8 @@ constexpr int kOrderPairs = 1 << 20;
 
 // (Re)compute the slack-dependent memory plan.
 void plan_memory(Plan& plan, int32_t slack_base);
+// Offsets and sizes of the slack-dependent storage from the per-front slack plan.slack.
+void layout_memory(Plan& plan);
 
 // ---------------------------------------------------------------------------------------------
 // Device layout
@@ -179,6 +181,8 @@ struct FrontTables {
 
 
 // One numeric factorization (a "slot"): dynamic per-front state + factor storage.
+// d_in of a front whose storage could not take the delayed columns it received: -(need + 1), need
+// the delayed columns it had to hold (0 when it failed because a child had failed)
 struct FactorSlot {
   double* F;            // fronts (column-major, ld = m_alloc), lower triangle meaningful
   int32_t* rowvar;      // per front, m_alloc: variable (new numbering) at each factor position
