@@ -258,9 +258,10 @@ def _cpu_sample_pencil():
 VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_schur", "gershgorin_multisection8",
             "stage3_f32_ir", "hermitian_mid")
 # variants on a workload of their own (run after the main problem is released)
-SEPARATE_VARIANTS = ("multisection_batch", "graph_replay", "hermitian_full")
-# run only when named (minutes): the n = 524,288 complex workload at its stated size
-EXPLICIT_VARIANTS = ("hermitian_full",)
+SEPARATE_VARIANTS = ("multisection_batch", "graph_replay", "hermitian_full", "precision_full")
+# run only when named (minutes each): the n = 524,288 complex workload and the n = 1,500,000
+# mixed-precision workload at their stated sizes
+EXPLICIT_VARIANTS = ("hermitian_full", "precision_full")
 
 
 def measure_variants(P, p, torch, kth, which="all"):
@@ -448,6 +449,51 @@ def measure_two_in_flight(P, p, torch):
     finally:
         if Q is not None:
             Q.close()
+    return res
+
+
+def measure_precision(torch):
+    """The mixed-precision workload (n = 1,500,000: 375,000 atoms, amorphous-like jitter 0.3 A,
+    k = 0.3 n, refined nested dissection): Algorithm 4 with FP64-accurate stage-3 solves, then
+    again with stage 3 on the reduced-precision factor and every shifted solve refined in FP64 to
+    a backward error <= 1e-13.  Both runs draw the same start vectors, so stages 1-2 (the FP64
+    inertia factorizations) take the same path; reported: the lambda_k difference relative to
+    ||A||_inf, the angle between the two eigenvectors in the B inner product, and the speed-ups."""
+    import paper_1710_05134_gb300 as kep
+    from gen import workload
+    p = workload("precision")
+    normA = float(np.abs(p.A()).sum(1).max())
+    res = {"workload": "precision", "n": p.n, "nnz": int(p.rowptr[-1]), "k": p.k,
+           "desc": "periodic diamond 25x25x75 cells, 375,000 atoms, jitter 0.3 A, k = 0.3 n",
+           "norm_A_inf": normA}
+    t0 = time.perf_counter()
+    with kep.Problem.from_pencil(p, refined_order=True) as P:
+        res["analyze_s"] = time.perf_counter() - t0
+        inf = P.info
+        res.update(max_front=inf.max_front, flops_per_factorization=inf.flops_factor,
+                   slot_gb=inf.slot_bytes / 1e9)
+        xs = {}
+        for mode in ("f64", "f32_ir"):
+            torch.cuda.synchronize(); t0 = time.perf_counter()
+            try:
+                lam, x, rep = P.kth_eigenpair(p.k, solve_precision=mode)
+            except Exception as exc:
+                res[mode] = {"error": str(exc), "seconds": time.perf_counter() - t0}
+                continue
+            torch.cuda.synchronize()
+            res[mode] = {"time_to_lambda_k_s": time.perf_counter() - t0, "lambda_k": lam,
+                         "rel_res": rep["rel_res"], "n_factor": rep["n_factor"],
+                         "n_si_iter": rep["n_si_iter"], "t_stage": rep["t_stage"],
+                         "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"]}
+            xs[mode] = x
+        a, b = res.get("f64", {}), res.get("f32_ir", {})
+        if "lambda_k" in a and "lambda_k" in b:
+            _, bx = P.spmv(xs["f32_ir"])
+            cos = abs(float(np.dot(xs["f64"], bx)))    # both B-normalised
+            res.update(lambda_err_rel=abs(a["lambda_k"] - b["lambda_k"]) / normA,
+                       eigvec_sin_angle_B=float(np.sqrt(max(0.0, 1.0 - min(cos, 1.0) ** 2))),
+                       speedup_total=a["time_to_lambda_k_s"] / b["time_to_lambda_k_s"],
+                       speedup_stage3=a["t_stage"][2] / b["t_stage"][2])
     return res
 
 
@@ -703,6 +749,8 @@ def main():
                     variants[name] = measure_multisection_batch(torch)
                 elif name == "graph_replay":
                     variants[name] = measure_graph_replay(torch)
+                elif name == "precision_full":
+                    variants[name] = measure_precision(torch)
                 else:
                     variants[name] = measure_hermitian(torch, "scale_peierls", refined=True)
             except Exception as exc:

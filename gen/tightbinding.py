@@ -299,6 +299,9 @@ def workload(name: str, seed: int = 0) -> Pencil:
     * ``scale_peierls``: the ``scale`` pencil with Peierls phases (complex Hermitian, n = 524,288,
                     the differentiation workload).
     * ``batch``:    32x16x16 cells, 65,536 atoms, n = 262,144 (the multisection workload).
+    * ``precision``: 25x25x75 cells (the most nearly cubic periodic block with exactly 375,000
+                    atoms), amorphous-like jitter 0.3 A, n = 1,500,000, k = 0.3 n (the
+                    mixed-precision workload).
     """
     if name == "small":
         return make_pair(4, 4, 4, seed=seed)
@@ -314,6 +317,10 @@ def workload(name: str, seed: int = 0) -> Pencil:
         return make_pair(32, 32, 18, seed=seed, vacancies=16384, phases="peierls")
     if name == "batch":
         return make_pair(32, 16, 16, seed=seed)
+    if name == "precision":
+        p = make_pair(25, 25, 75, seed=seed, jitter=0.3)
+        p.k = (3 * p.n) // 10
+        return p
     if name.startswith("cells:"):
         nx, ny, nz = (int(v) for v in name[6:].split("x"))
         return make_pair(nx, ny, nz, seed=seed)

@@ -73,6 +73,10 @@ typedef struct {
   int64_t front_bytes;        /* device bytes of one factor slot's front storage */
   int64_t replans;            /* times the storage was re-planned because delayed pivots overflowed
                                  a front's slack (only the overflowing fronts grow) */
+  int64_t cb_bytes;           /* device bytes of the contribution-block arena (the peak of the
+                                 level schedule's first-fit placement) */
+  int64_t slot_bytes;         /* device bytes one factorization holds: front storage, pivots, D,
+                                 solve vectors, contribution blocks and the L21 workspace */
 } kep_info;
 
 /* Parameters of Algorithm 4 (Section 3.4) and of the stage-3 iteration. */

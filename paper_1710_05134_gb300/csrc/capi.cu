@@ -734,6 +734,8 @@ kep_status kep_get_info(const kep_ctx* c, kep_info* info) {
   info->flops_factor = P.flops;
   info->front_bytes = P.front_total * 8;
   info->replans = c->replans;
+  info->cb_bytes = P.cb_total * 8;
+  info->slot_bytes = shift_bytes(P);
   return KEP_OK;
 }
 
@@ -757,6 +759,8 @@ kep_status kep_symbolic_info(int64_t n, const int64_t* rowptr, const int32_t* co
   info->flops_factor = P.flops;
   info->front_bytes = P.front_total * 8;
   info->replans = 0;
+  info->cb_bytes = P.cb_total * 8;
+  info->slot_bytes = shift_bytes(P);
   return KEP_OK;
 }
 

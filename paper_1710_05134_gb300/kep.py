@@ -54,7 +54,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nfronts", ctypes.c_int64),
                 ("nlevels", ctypes.c_int64), ("max_front", ctypes.c_int64),
                 ("nnz_factor", ctypes.c_int64), ("flops_factor", ctypes.c_double),
-                ("front_bytes", ctypes.c_int64), ("replans", ctypes.c_int64)]
+                ("front_bytes", ctypes.c_int64), ("replans", ctypes.c_int64),
+                ("cb_bytes", ctypes.c_int64), ("slot_bytes", ctypes.c_int64)]
 
 
 class Params(ctypes.Structure):
