@@ -256,7 +256,7 @@ def _cpu_sample_pencil():
 
 
 VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_schur", "gershgorin_multisection8",
-            "stage3_f32_ir", "hermitian_mid")
+            "stage3_f32_ir", "kth_interp", "hermitian_mid")
 # variants on a workload of their own (run after the main problem is released)
 SEPARATE_VARIANTS = ("multisection_batch", "graph_replay", "hermitian_full", "precision_full")
 # run only when named (minutes each): the n = 524,288 complex workload and the n = 1,500,000
@@ -303,7 +303,8 @@ def measure_variants(P, p, torch, kth, which="all"):
         P.set_schur_tile(64)
     # Algorithm 4 variants
     for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),
-                     ("stage3_f32_ir", {"solve_precision": "f32_ir"})):
+                     ("stage3_f32_ir", {"solve_precision": "f32_ir"}),
+                     ("kth_interp", {"split": "interp"})):
         if name not in want:
             continue
         sync(); t0 = time.perf_counter()
@@ -316,7 +317,11 @@ def measure_variants(P, p, torch, kth, which="all"):
         out[name] = {"time_to_lambda_k_s": t, "lambda_k": lam_v,
                      "n_factor": rep["n_factor"], "n_bisect": rep["n_bisect"], "n_si_iter": rep["n_si_iter"],
                      "init_interval": [rep["init_lo"], rep["init_hi"]], "t_stage": rep["t_stage"],
-                     "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"]}
+                     "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"],
+                     "nu_interval": [rep["nu_lo"], rep["nu_hi"]], "rel_res": rep["rel_res"]}
+        if kth:
+            normA = float(np.abs(p.A()).sum(1).max())
+            out[name]["lambda_diff_rel_to_bisection_run"] = abs(lam_v - kth["lambda_k"]) / normA
     if "hermitian_mid" in want:
         out["hermitian_mid"] = measure_hermitian(torch)
     return out
@@ -458,7 +463,8 @@ def measure_precision(torch):
     again with stage 3 on the reduced-precision factor and every shifted solve refined in FP64 to
     a backward error <= 1e-13.  Both runs draw the same start vectors, so stages 1-2 (the FP64
     inertia factorizations) take the same path; reported: the lambda_k difference relative to
-    ||A||_inf, the angle between the two eigenvectors in the B inner product, and the speed-ups."""
+    ||A||_inf, the angle between the two eigenvectors in the B inner product, and the speed-ups.
+    A third run takes Algorithm 1' with the interpolating shift rule (FP64 solves)."""
     import paper_1710_05134_gb300 as kep
     from gen import workload
     p = workload("precision")
@@ -473,10 +479,11 @@ def measure_precision(torch):
         res.update(max_front=inf.max_front, flops_per_factorization=inf.flops_factor,
                    slot_gb=inf.slot_bytes / 1e9)
         xs = {}
-        for mode in ("f64", "f32_ir"):
+        runs = {"f64": {}, "f32_ir": {"solve_precision": "f32_ir"}, "f64_interp": {"split": "interp"}}
+        for mode, kw in runs.items():
             torch.cuda.synchronize(); t0 = time.perf_counter()
             try:
-                lam, x, rep = P.kth_eigenpair(p.k, solve_precision=mode)
+                lam, x, rep = P.kth_eigenpair(p.k, **kw)
             except Exception as exc:
                 res[mode] = {"error": str(exc), "seconds": time.perf_counter() - t0}
                 continue
@@ -484,7 +491,8 @@ def measure_precision(torch):
             res[mode] = {"time_to_lambda_k_s": time.perf_counter() - t0, "lambda_k": lam,
                          "rel_res": rep["rel_res"], "n_factor": rep["n_factor"],
                          "n_si_iter": rep["n_si_iter"], "t_stage": rep["t_stage"],
-                         "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"]}
+                         "n_refine": rep["n_refine"], "solve_berr": rep["solve_berr"],
+                         "n_bisect": rep["n_bisect"]}
             xs[mode] = x
         a, b = res.get("f64", {}), res.get("f32_ir", {})
         if "lambda_k" in a and "lambda_k" in b:
@@ -494,6 +502,10 @@ def measure_precision(torch):
                        eigvec_sin_angle_B=float(np.sqrt(max(0.0, 1.0 - min(cos, 1.0) ** 2))),
                        speedup_total=a["time_to_lambda_k_s"] / b["time_to_lambda_k_s"],
                        speedup_stage3=a["t_stage"][2] / b["t_stage"][2])
+        c = res.get("f64_interp", {})
+        if "lambda_k" in a and "lambda_k" in c:
+            res.update(interp_lambda_diff_rel=abs(a["lambda_k"] - c["lambda_k"]) / normA,
+                       interp_speedup_total=a["time_to_lambda_k_s"] / c["time_to_lambda_k_s"])
     return res
 
 

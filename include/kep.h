@@ -107,11 +107,16 @@ typedef struct {
                                  run conjugate gradients to a relative residual of 1e-14 and
                                  factor B again only if 500 iterations do not reach it;
                                  KEP_BFACTOR_OWN its own slot always */
+  int32_t split;              /* Algorithm 1''s shift rule: KEP_SPLIT_BISECT (default: the paper's
+                                 midpoints, or multisection with nshift) or KEP_SPLIT_INTERP (the
+                                 interpolating rule of kep_interp_point, one shift per step; the
+                                 root-finder variant of Sections 2.1 and 5; nshift must be 1) */
 } kep_params;
 
 enum { KEP_INIT_LANCZOS = 0, KEP_INIT_GERSHGORIN = 1 };
 enum { KEP_BFACTOR_AUTO = 0, KEP_BFACTOR_SHARED = 1, KEP_BFACTOR_OWN = 2 };
 enum { KEP_SOLVE_F64 = 0, KEP_SOLVE_F32_IR = 1 };
+enum { KEP_SPLIT_BISECT = 0, KEP_SPLIT_INTERP = 1 };
 
 /* Report of kep_kth_eigenpair. */
 typedef struct {
@@ -323,6 +328,50 @@ kep_status kep_multisection_points(double lo, double hi, int32_t nshift, double*
  */
 kep_status kep_multisection_update(int64_t k, int32_t count, const double* sigmas, const int64_t* nus,
                                    double* lo, double* hi, int64_t* nu_lo, int64_t* nu_hi);
+
+/*
+ * Interpolating shift rule for Algorithm 1' (host only, no device).  Section 2.1 notes that
+ * bisection's midpoint may be replaced by another root-finder on the count function nu(sigma)
+ * (non-decreasing, integer-valued), and Section 5 that any derivative-free method that keeps the
+ * root bracketed locates lambda_k.  This rule is such a method; its output contract is Algorithm
+ * 1''s (nu_lo < k <= nu_hi, nu_hi - nu_lo <= m_max), reached in fewer factorizations when the
+ * density of eigenvalues is smooth.
+ *
+ * Each step moves the end farther from k in count: the target count is k - h (lower end) or
+ * k - 1 + h (upper end), h = max(1, m_max / 4), and the shift is the linear interpolation of sigma
+ * between the ends at their weighted counts w_lo, w_hi, kept (hi - lo) / 2^20 away from both ends.
+ * The weights are the true counts, except that an end kept through two consecutive steps has its
+ * count distance to k halved (the Illinois modification of regula falsi).  Safeguard: when the
+ * count width has not halved over the last three steps, the next shift is the midpoint.
+ *
+ * The state is caller-allocated; its fields are read-only to the caller (kep_interp_init sets
+ * them, kep_interp_update advances them).
+ */
+typedef struct {
+  double lo, hi;              /* the bracket: nu(lo) = nu_lo < k <= nu_hi = nu(hi) */
+  int64_t nu_lo, nu_hi;
+  double w_lo, w_hi;          /* the ends' counts as the interpolation weighs them */
+  int64_t width[4];           /* the last count widths nu_hi - nu_lo, newest at width[nwidth - 1] */
+  int32_t nwidth;             /* entries of width in use (at most 4) */
+  int32_t last;               /* the end the previous step replaced: +1 upper, -1 lower, 0 none */
+  int32_t bisect_next;        /* the next shift is the safeguard's midpoint */
+  int32_t reserved;
+} kep_interp_state;
+
+/* kep_interp_init - a new state for the bracket [lo, hi) of k.  Errors: KEP_ERR_INVALID unless
+ * lo < hi and nu_lo < k <= nu_hi, or for a null pointer. */
+kep_status kep_interp_init(int64_t k, double lo, double hi, int64_t nu_lo, int64_t nu_hi, kep_interp_state* st);
+
+/* kep_interp_point - the next shift (strictly inside the bracket).  Errors: KEP_ERR_INVALID for
+ * m_max < 1, a bracket that does not hold k, or a null pointer; KEP_ERR_CLUSTER when lo and hi are
+ * adjacent doubles (more than m_max eigenvalues within rounding of one value). */
+kep_status kep_interp_point(const kep_interp_state* st, int64_t k, int64_t m_max, double* sigma);
+
+/* kep_interp_update - the count nu = nu(sigma) at the shift kep_interp_point gave: the end on
+ * sigma's side is replaced and the weights and safeguard advance.  Errors: KEP_ERR_INVALID (state
+ * unchanged) when sigma is not strictly inside the bracket or nu lies outside [nu_lo, nu_hi] (a
+ * count that is not monotone in sigma means a wrong factorization). */
+kep_status kep_interp_update(kep_interp_state* st, int64_t k, double sigma, int64_t nu);
 
 /*
  * kep_set_values - new values of A and B on the pattern given to kep_analyze (same layout:

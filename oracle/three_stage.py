@@ -18,6 +18,11 @@ Algorithms of the paper, step by step and in its notation, on plain operators:
                           B^{-1} A (Section 4.2, dense, small n).
   * ``multisect_mmax``    Algorithm 1' with s points per step (s + 1 equal parts; s = 1 is
                           bisection).
+  * ``interp_mmax``       Algorithm 1' with the shift chosen by a bracketed, derivative-free
+                          root-finder on the count function nu(sigma) instead of the midpoint: the
+                          variant Section 2.1 describes and Section 5 proposes (any derivative-free
+                          method that keeps the root bracketed locates lambda_k).  The rule itself
+                          is this project's; its output contract is Algorithm 1''s.
 
 Operators come from ``DenseOps`` (dense numpy, small n) or ``SparseOps`` (scipy sparse LU for
 solves, (c3) for inertia).  Library solves serve as steps; the method's arithmetic is here.
@@ -336,6 +341,80 @@ def si_lanczos_kth(ops, k: int, iv: Interval, vt1: np.ndarray, tau_res: float = 
     raise RuntimeError("Algorithm 3 did not validate the interval's eigenpairs")
 
 
+class InterpBracket:
+    """State of the interpolating shift rule for Algorithm 1' (see ``interp_mmax``).
+
+    The bracket is [lower, upper) with nu(lower) = nu_lower < k <= nu_upper = nu(upper).  w_lower
+    and w_upper are the counts the interpolation assigns to the two ends: the true counts, except
+    that an end kept through two consecutive steps has its distance to k halved (the Illinois
+    modification of regula falsi, which stops one far end from holding the interpolant back).
+    widths holds the count widths nu_upper - nu_lower after each step (the first entry is the
+    initial width); bisect_next marks the safeguard's midpoint step."""
+
+    def __init__(self, k: int, lower: float, upper: float, nu_lower: int, nu_upper: int):
+        if not (lower < upper and nu_lower < k <= nu_upper):
+            raise ValueError("not a bracket of k")
+        self.lower, self.upper = float(lower), float(upper)
+        self.nu_lower, self.nu_upper = int(nu_lower), int(nu_upper)
+        self.w_lower, self.w_upper = float(nu_lower), float(nu_upper)
+        self.widths = [self.nu_upper - self.nu_lower]
+        self.last = 0
+        self.bisect_next = False
+
+    def point(self, k: int, m_max: int) -> float:
+        """The next shift.  The end farther from k in count is the one to move: the target count is
+        k - h below k (to move the lower end) or k - 1 + h (to move the upper end), h = m_max // 4
+        (at least 1), so that the moved end lands inside the final window.  Its shift is the linear
+        interpolation of sigma between the ends at their weighted counts, kept at least 2^-20 of the
+        bracket away from either end.  A safeguard step takes the midpoint instead."""
+        lo, hi = self.lower, self.upper
+        if self.bisect_next:
+            return 0.5 * (lo + hi)
+        h = max(1, m_max // 4)
+        move_lower = (k - self.nu_lower) > (self.nu_upper - k)
+        t = float(k - h) if move_lower else float(k - 1 + h)
+        t = min(max(t, self.w_lower + 0.5), self.w_upper - 0.5)
+        frac = (t - self.w_lower) / (self.w_upper - self.w_lower)
+        s = lo + frac * (hi - lo)
+        g = (hi - lo) / 1048576.0
+        return min(max(s, lo + g), hi - g)
+
+    def update(self, k: int, sigma: float, nu: int) -> None:
+        """Replace the end on sigma's side by (sigma, nu(sigma)); the safeguard bisects once when
+        the count width has not halved over the last three steps."""
+        if not (self.lower < sigma < self.upper and self.nu_lower <= nu <= self.nu_upper):
+            raise ValueError("shift outside the bracket or count not monotone")
+        was_bisect = self.bisect_next
+        if k <= nu:
+            self.upper, self.nu_upper, self.w_upper = sigma, int(nu), float(nu)
+            if self.last > 0 and not was_bisect:
+                self.w_lower = k - 0.5 * (k - self.w_lower)
+            self.last = 1
+        else:
+            self.lower, self.nu_lower, self.w_lower = sigma, int(nu), float(nu)
+            if self.last < 0 and not was_bisect:
+                self.w_upper = k + 0.5 * (self.w_upper - k)
+            self.last = -1
+        self.widths.append(self.nu_upper - self.nu_lower)
+        w = self.widths
+        self.bisect_next = (not was_bisect) and len(w) > 3 and 2 * w[-1] > w[-4]
+
+
+def interp_mmax(ops, k: int, iv: Interval, m_max: int = 20) -> Interval:
+    """Algorithm 1' with the interpolating shift rule (``InterpBracket``): until the interval holds
+    at most m_max eigenvalues, factor at the rule's shift and keep the side that brackets k.  Like
+    bisection it only needs nu at each shift, and the output interval satisfies the same contract
+    nu_l < k <= nu_u, nu_u - nu_l <= m_max."""
+    st = InterpBracket(k, iv.lower, iv.upper, iv.nu_lower, iv.nu_upper)
+    hist = []
+    while st.nu_upper - st.nu_lower > m_max:
+        s = st.point(k, m_max)
+        nu = ops.nu(s)
+        hist.append((s, nu))
+        st.update(k, s, nu)
+    return Interval(st.lower, st.upper, st.nu_lower, st.nu_upper, hist)
+
+
 @dataclass
 class ThreeStageResult:
     lam: float
@@ -348,11 +427,15 @@ class ThreeStageResult:
 
 def three_stage(ops, k: int, v1: np.ndarray, vt1: np.ndarray, m_max: int = 20,
                 tau_res: float = 1e-10, tau_diff: float = 1e-10, init: str = "lanczos",
-                nshift: int = 1) -> ThreeStageResult:
+                nshift: int = 1, split: str = "bisect") -> ThreeStageResult:
     """Algorithm 4: Algorithm 2 (or the Gershgorin interval of the variant), then Algorithm 1'
-    (bisection, or multisection with nshift points), then Algorithm 3."""
+    (bisection, multisection with nshift points, or the interpolating shift rule for
+    split="interp"), then Algorithm 3."""
     iv0 = gershgorin_interval(ops.A, ops.B) if init == "gershgorin" else lanczos_interval(ops, k, v1)
-    iv1 = multisect_mmax(ops, k, iv0, m_max, nshift)
+    if split == "interp":
+        iv1 = interp_mmax(ops, k, iv0, m_max)
+    else:
+        iv1 = multisect_mmax(ops, k, iv0, m_max, nshift)
     res = si_lanczos_kth(ops, k, iv1, vt1, tau_res, tau_diff)
     return ThreeStageResult(lam=res.lam, x=res.x, initial=iv0, narrowed=iv1, kth=res,
                             nfactor=ops.nfactor)

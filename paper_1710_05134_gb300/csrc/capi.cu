@@ -519,6 +519,7 @@ void kep_default_params(kep_params* p) {
   p->nshift = 1;
   p->solve_precision = KEP_SOLVE_F64;
   p->b_factor = KEP_BFACTOR_AUTO;
+  p->split = KEP_SPLIT_BISECT;
 }
 
 const char* kep_status_str(kep_status s) {

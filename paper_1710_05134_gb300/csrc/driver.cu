@@ -247,8 +247,14 @@ struct Run {
     if (policy == KEP_BFACTOR_OWN || c->slot_ready[1]) { bslot = 1; return KEP_OK; }
     size_t free_b = 0, total_b = 0;
     CTRY(cudaMemGetInfo(&free_b, &total_b));
-    const double need = 8.0 * static_cast<double>(c->plan.front_total) +
-                        4.0 * 2.0 * static_cast<double>(c->plan.vec_total) + (2ll << 30);
+    // a second slot must fit beside what the shifted factorizations still allocate: their own slot
+    // (allocated at the first factorization) and the tensor-core workspace (at most 24 GB)
+    const Plan& P = c->plan;
+    const double slot = 8.0 * static_cast<double>(P.front_total) + 8.0 * static_cast<double>(P.vec_total) +
+                        17.0 * static_cast<double>(P.piv_total);
+    double need = slot + (2ll << 30);
+    if (!c->slot_ready[0]) need += slot;
+    if (c->emul_bytes == 0) need += static_cast<double>(24ll << 30);
     bslot = static_cast<double>(free_b) > need ? 1 : 0;
     return KEP_OK;
   }
@@ -386,6 +392,73 @@ extern "C" kep_status kep_multisection_update(int64_t k, int32_t count, const do
   return KEP_OK;
 }
 
+// Interpolating shift rule (the root-finder variant of Algorithm 1', Sections 2.1 and 5).
+static bool interp_bracket_ok(const kep_interp_state* st, int64_t k) {
+  return st->lo < st->hi && st->nu_lo < k && k <= st->nu_hi && st->w_lo < st->w_hi;
+}
+
+extern "C" kep_status kep_interp_init(int64_t k, double lo, double hi, int64_t nu_lo, int64_t nu_hi,
+                                      kep_interp_state* st) {
+  if (!st || !(lo < hi) || !(nu_lo < k && k <= nu_hi)) return KEP_ERR_INVALID;
+  *st = kep_interp_state{};
+  st->lo = lo; st->hi = hi; st->nu_lo = nu_lo; st->nu_hi = nu_hi;
+  st->w_lo = static_cast<double>(nu_lo); st->w_hi = static_cast<double>(nu_hi);
+  st->width[0] = nu_hi - nu_lo;
+  st->nwidth = 1;
+  return KEP_OK;
+}
+
+extern "C" kep_status kep_interp_point(const kep_interp_state* st, int64_t k, int64_t m_max, double* sigma) {
+  if (!st || !sigma || m_max < 1 || !interp_bracket_ok(st, k)) return KEP_ERR_INVALID;
+  const double lo = st->lo, hi = st->hi;
+  if (st->bisect_next) {
+    *sigma = 0.5 * (lo + hi);
+    return (*sigma > lo && *sigma < hi) ? KEP_OK : KEP_ERR_CLUSTER;
+  }
+  const int64_t h = std::max<int64_t>(1, m_max / 4);
+  // move the end that is farther from k in count, to inside the final window
+  const bool lower_end = (k - st->nu_lo) > (st->nu_hi - k);
+  double target = static_cast<double>(lower_end ? k - h : k - 1 + h);
+  target = std::min(std::max(target, st->w_lo + 0.5), st->w_hi - 0.5);
+  const double f = (target - st->w_lo) / (st->w_hi - st->w_lo);
+  const double span = hi - lo;
+  const double margin = span / 1048576.0;
+  double s = lo + f * span;
+  s = std::max(s, lo + margin);
+  s = std::min(s, hi - margin);
+  if (!(s > lo && s < hi)) s = 0.5 * (lo + hi);
+  if (!(s > lo && s < hi)) return KEP_ERR_CLUSTER;    // lo and hi are adjacent doubles
+  *sigma = s;
+  return KEP_OK;
+}
+
+extern "C" kep_status kep_interp_update(kep_interp_state* st, int64_t k, double sigma, int64_t nu) {
+  if (!st || !interp_bracket_ok(st, k)) return KEP_ERR_INVALID;
+  if (!(sigma > st->lo && sigma < st->hi) || nu < st->nu_lo || nu > st->nu_hi) return KEP_ERR_INVALID;
+  const bool midpoint = st->bisect_next != 0;
+  const double kd = static_cast<double>(k);
+  if (nu >= k) {
+    // the upper end moves; a lower end kept twice in a row is pulled halfway towards k
+    if (st->last == 1 && !midpoint) st->w_lo = kd - 0.5 * (kd - st->w_lo);
+    st->hi = sigma; st->nu_hi = nu; st->w_hi = static_cast<double>(nu);
+    st->last = 1;
+  } else {
+    if (st->last == -1 && !midpoint) st->w_hi = kd + 0.5 * (st->w_hi - kd);
+    st->lo = sigma; st->nu_lo = nu; st->w_lo = static_cast<double>(nu);
+    st->last = -1;
+  }
+  const int64_t wnow = st->nu_hi - st->nu_lo;
+  // keep the last four widths: the safeguard compares with the width three steps back
+  if (st->nwidth == 4) {
+    for (int i = 0; i < 3; ++i) st->width[i] = st->width[i + 1];
+    st->width[3] = wnow;
+  } else {
+    st->width[st->nwidth++] = wnow;
+  }
+  st->bisect_next = (!midpoint && st->nwidth == 4 && 2 * wnow > st->width[0]) ? 1 : 0;
+  return KEP_OK;
+}
+
 extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params* params, double* lambda,
                                         double* x_out, kep_report* report) {
   if (!c || !lambda) return KEP_ERR_INVALID;
@@ -396,6 +469,8 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   if (params) prm = *params; else kep_default_params(&prm);
   if (prm.m_max < 1 || prm.max_lanczos < 2 || prm.max_si < 1) return KEP_ERR_INVALID;
   if (prm.b_factor < KEP_BFACTOR_AUTO || prm.b_factor > KEP_BFACTOR_OWN) return KEP_ERR_INVALID;
+  if (prm.split != KEP_SPLIT_BISECT && prm.split != KEP_SPLIT_INTERP) return KEP_ERR_INVALID;
+  if (prm.split == KEP_SPLIT_INTERP && prm.nshift > 1) return KEP_ERR_INVALID;
   int64_t cap = std::min<int64_t>(n + 1, std::max(prm.max_lanczos, prm.max_si) + 2);
   Driver* d = static_cast<Driver*>(c->driver);
   if (!d || d->cap_cols < cap) {
@@ -524,6 +599,20 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   const int32_t ns = std::max(1, prm.nshift);
   std::vector<double> sig(ns);
   std::vector<int64_t> nus(ns);
+  if (prm.split == KEP_SPLIT_INTERP && nh - nl > prm.m_max) {
+    kep_interp_state is;
+    DTRY(kep_interp_init(k, lo, hi, nl, nh, &is));
+    while (is.nu_hi - is.nu_lo > prm.m_max) {
+      double s = 0;
+      int64_t v = 0;
+      DTRY(kep_interp_point(&is, k, prm.m_max, &s));
+      DTRY(R.nu_at(s, v));
+      DTRY(kep_interp_update(&is, k, s, v));
+      rep.n_bisect++;
+      if (rep.n_bisect > 200) return KEP_ERR_CLUSTER;
+    }
+    lo = is.lo; hi = is.hi; nl = is.nu_lo; nh = is.nu_hi;
+  }
   while (nh - nl > prm.m_max) {
     // the shifts in increasing order; once one of them reaches k the later ones are not needed
     DTRY(kep_multisection_points(lo, hi, ns, sig.data()));

@@ -26,11 +26,13 @@ EXPORTED = ["kep_default_params", "kep_analyze", "kep_analyze_hermitian", "kep_g
             "kep_set_timing_classes", "kep_grad", "kep_set_values", "kep_factor_multi", "kep_solve_refined",
             "kep_get_timing", "kep_destroy", "kep_status_str", "kep_dense_inertia_noalloc",
             "kep_multisection_points", "kep_multisection_update", "kep_set_graphs",
-            "kep_set_schur_mode", "kep_set_schur_tile", "kep_get_schur_config"]
+            "kep_set_schur_mode", "kep_set_schur_tile", "kep_get_schur_config",
+            "kep_interp_init", "kep_interp_point", "kep_interp_update"]
 KEP_SCHUR_FP64, KEP_SCHUR_EMULATED = 0, 1
 KEP_INIT_LANCZOS, KEP_INIT_GERSHGORIN = 0, 1
 KEP_SOLVE_F64, KEP_SOLVE_F32_IR = 0, 1
 KEP_BFACTOR_AUTO, KEP_BFACTOR_SHARED, KEP_BFACTOR_OWN = 0, 1, 2
+KEP_SPLIT_BISECT, KEP_SPLIT_INTERP = 0, 1
 KEP_SCHUR_FP32 = 2
 KERNEL_CLASSES = ["assemble", "panel", "l21", "apply", "update", "reduce", "solve_fwd", "solve_bwd",
                   "perm", "spmv", "vec", "slice", "flush_tc"]
@@ -63,7 +65,16 @@ class Params(ctypes.Structure):
                 ("max_lanczos", ctypes.c_int64), ("max_si", ctypes.c_int64),
                 ("start_vectors", ctypes.c_void_p), ("seed", ctypes.c_uint64),
                 ("init", ctypes.c_int32), ("nshift", ctypes.c_int32),
-                ("solve_precision", ctypes.c_int32), ("b_factor", ctypes.c_int32)]
+                ("solve_precision", ctypes.c_int32), ("b_factor", ctypes.c_int32),
+                ("split", ctypes.c_int32)]
+
+
+class InterpState(ctypes.Structure):
+    """kep_interp_state: the interpolating shift rule's bracket, weights and safeguard."""
+    _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("nu_lo", ctypes.c_int64),
+                ("nu_hi", ctypes.c_int64), ("w_lo", ctypes.c_double), ("w_hi", ctypes.c_double),
+                ("width", ctypes.c_int64 * 4), ("nwidth", ctypes.c_int32), ("last", ctypes.c_int32),
+                ("bisect_next", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -126,6 +137,12 @@ def lib() -> ctypes.CDLL:
         L.kep_multisection_points.restype = I
         L.kep_multisection_update.argtypes = [I64, ctypes.c_int32, P, P, P, P, P, P]
         L.kep_multisection_update.restype = I
+        L.kep_interp_init.argtypes = [I64, D, D, I64, I64, P]
+        L.kep_interp_init.restype = I
+        L.kep_interp_point.argtypes = [P, I64, I64, P]
+        L.kep_interp_point.restype = I
+        L.kep_interp_update.argtypes = [P, I64, D, I64]
+        L.kep_interp_update.restype = I
         L.kep_dense_inertia_noalloc.restype = I
         L.kep_set_schur_mode.argtypes = [P, I, I64]
         L.kep_set_schur_mode.restype = I
@@ -164,6 +181,27 @@ def multisection_update(k: int, sigmas, nus, lo: float, hi: float, nu_lo: int, n
     _check(lib().kep_multisection_update(int(k), cnt, s, v, ctypes.byref(lo_), ctypes.byref(hi_), ctypes.byref(nl_),
                                          ctypes.byref(nh_)), "kep_multisection_update")
     return lo_.value, hi_.value, nl_.value, nh_.value
+
+
+def interp_init(k: int, lo: float, hi: float, nu_lo: int, nu_hi: int) -> InterpState:
+    """A state of the interpolating shift rule for the bracket [lo, hi) of k (kep_interp_init;
+    host only)."""
+    st = InterpState()
+    _check(lib().kep_interp_init(int(k), float(lo), float(hi), int(nu_lo), int(nu_hi), ctypes.byref(st)),
+           "kep_interp_init")
+    return st
+
+
+def interp_point(st: InterpState, k: int, m_max: int) -> float:
+    """The rule's next shift (kep_interp_point; host only)."""
+    s = ctypes.c_double()
+    _check(lib().kep_interp_point(ctypes.byref(st), int(k), int(m_max), ctypes.byref(s)), "kep_interp_point")
+    return s.value
+
+
+def interp_update(st: InterpState, k: int, sigma: float, nu: int) -> None:
+    """Advance the rule with nu(sigma) (kep_interp_update; host only)."""
+    _check(lib().kep_interp_update(ctypes.byref(st), int(k), float(sigma), int(nu)), "kep_interp_update")
 
 
 def symbolic_info(n, rowptr, colind, coords=None, *, lower: bool = False, graph_order: bool = False,
@@ -423,10 +461,11 @@ class Problem:
     def kth_eigenpair(self, k: int, *, m_max: int = 20, tau_res: float = 1e-10, tau_diff: float = 1e-10,
                       max_lanczos: int = 200, max_si: int = 300, start_vectors=None, seed: int = 0x5eed,
                       want_vector: bool = True, init: str = "lanczos", nshift: int = 1,
-                      solve_precision: str = "f64", b_factor: str = "auto"):
+                      solve_precision: str = "f64", b_factor: str = "auto", split: str = "bisect"):
         """Algorithm 4: (lambda_k, x_k (B-normalized), report dict).  init: "lanczos" (Algorithm 2)
         or "gershgorin" (an interval holding the whole spectrum); nshift: shifts per Algorithm 1'
-        step (1 = bisection); b_factor: "auto", "shared" or "own" (where B's factor lives)."""
+        step (1 = bisection); b_factor: "auto", "shared" or "own" (where B's factor lives);
+        split: "bisect" (the paper's Algorithm 1') or "interp" (the interpolating shift rule)."""
         prm = Params()
         lib().kep_default_params(ctypes.byref(prm))
         prm.m_max, prm.tau_res, prm.tau_diff = int(m_max), float(tau_res), float(tau_diff)
@@ -435,6 +474,7 @@ class Problem:
         prm.nshift = int(nshift)
         prm.solve_precision = {"f64": KEP_SOLVE_F64, "f32_ir": KEP_SOLVE_F32_IR}[solve_precision]
         prm.b_factor = {"auto": KEP_BFACTOR_AUTO, "shared": KEP_BFACTOR_SHARED, "own": KEP_BFACTOR_OWN}[b_factor]
+        prm.split = {"bisect": KEP_SPLIT_BISECT, "interp": KEP_SPLIT_INTERP}[split]
         sv = None
         if start_vectors is not None:
             sv = np.ascontiguousarray(start_vectors, dtype=np.float64).reshape(-1)

@@ -163,3 +163,51 @@ def test_multisection_step_through_the_abi():
         k.multisection_update(3, pts, [0, 2, 1, 4, 5, 5, 5, 6], 0.0, 9.0, 0, 7)   # not monotone
     with pytest.raises(k.KepError):
         k.multisection_update(9, pts, nu, 0.0, 9.0, 0, 7)                        # k not bracketed
+
+
+def test_interp_rule_through_the_abi_matches_oracle():
+    """kep_interp_init / _point / _update (host only) against the oracle's statement of the same
+    rule (oracle.three_stage.InterpBracket) on count functions with no matrix: the same counts at
+    every step and shifts equal to rounding (a fused multiply-add may round the interpolation once
+    instead of twice), the same final bracket; malformed calls are refused."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import paper_1710_05134_gb300 as k
+    from paper_1710_05134_gb300 import kep as kb
+    from oracle import three_stage as ts
+    rng = np.random.default_rng(17)
+    N = 50000
+    spectra = [np.arange(1.0, N + 1.0), np.sort(rng.normal(size=N) ** 3),
+               np.sort(rng.standard_cauchy(N)),
+               np.sort(np.concatenate([rng.uniform(0, 1, N // 2), rng.uniform(9, 10, N - N // 2)]))]
+    for lam in spectra:
+        for kk in (1, 7, N // 3, N // 2, N // 2 + 1, N - 3):
+            lo, hi = float(lam[0] - 1.0), float(lam[-1] + 1.0)
+            st = kb.interp_init(kk, lo, hi, 0, N)
+            orc = ts.InterpBracket(kk, lo, hi, 0, N)
+            steps = 0
+            while st.nu_hi - st.nu_lo > 20:
+                s_c = kb.interp_point(st, kk, 20)
+                s_o = orc.point(kk, 20)
+                assert abs(s_c - s_o) <= 1e-13 * (orc.upper - orc.lower) + 4 * np.spacing(abs(s_o))
+                nu = int(np.searchsorted(lam, s_c, side="left"))
+                assert nu == int(np.searchsorted(lam, s_o, side="left"))
+                kb.interp_update(st, kk, s_c, nu)
+                orc.update(kk, s_o, nu)
+                assert (st.nu_lo, st.nu_hi, bool(st.bisect_next)) == (orc.nu_lower, orc.nu_upper, orc.bisect_next)
+                steps += 1
+                assert steps < 200
+            assert st.nu_lo < kk <= st.nu_hi and st.nu_hi - st.nu_lo <= 20
+            assert st.lo <= lam[kk - 1] < st.hi
+    st = kb.interp_init(5, 0.0, 1.0, 0, 10)
+    with pytest.raises(k.KepError):
+        kb.interp_init(11, 0.0, 1.0, 0, 10)                  # k not bracketed
+    with pytest.raises(k.KepError):
+        kb.interp_init(5, 1.0, 0.0, 0, 10)                   # empty bracket
+    with pytest.raises(k.KepError):
+        kb.interp_point(st, 5, 0)                            # m_max < 1
+    with pytest.raises(k.KepError):
+        kb.interp_update(st, 5, 1.5, 4)                      # shift outside the bracket
+    with pytest.raises(k.KepError):
+        kb.interp_update(st, 5, 0.5, 11)                     # count above nu_hi
+    assert (st.lo, st.hi, st.nu_lo, st.nu_hi) == (0.0, 1.0, 0, 10)   # unchanged by refused updates

@@ -106,3 +106,31 @@ def test_kth_eigenpair_shared_b_slot(kep, small):
     assert (rs["init_nu_lo"], rs["init_nu_hi"], rs["nu_lo"], rs["nu_hi"]) == \
         (ro["init_nu_lo"], ro["init_nu_hi"], ro["nu_lo"], ro["nu_hi"])
     assert rs["n_factor"] == ro["n_factor"]          # B factored once in both layouts
+
+
+@pytest.mark.parametrize("frac", [0.3, 0.5])
+def test_kth_eigenpair_interp_split_matches_oracle(kep, small, frac):
+    """Algorithm 1' with the interpolating shift rule (split="interp"): the same Algorithm 2
+    interval, the same sequence of counts and the same narrowed interval as the oracle's run from
+    the same start vectors, and lambda_k within the method's tolerance."""
+    p, A, B, lam, X = small
+    k = max(2, int(frac * p.n))
+    rng = np.random.default_rng(9)
+    v1, vt1 = rng.normal(size=p.n), rng.normal(size=p.n)
+    P = kep.Problem.from_pencil(p)
+    lam_g, x_g, rep = P.kth_eigenpair(k, start_vectors=np.concatenate([v1, vt1]), split="interp")
+    _check_pair(p, A, B, lam, X, k, lam_g, x_g, rep)
+    r = ts.three_stage(ts.DenseOps(A, B), k, v1, vt1, split="interp")
+    assert (rep["init_nu_lo"], rep["init_nu_hi"]) == (r.initial.nu_lower, r.initial.nu_upper)
+    assert (rep["nu_lo"], rep["nu_hi"]) == (r.narrowed.nu_lower, r.narrowed.nu_upper)
+    assert rep["n_bisect"] == len(r.narrowed.history)
+    w = r.initial.upper - r.initial.lower
+    assert abs(rep["sigma_lo"] - r.narrowed.lower) <= 1e-9 * w
+    assert abs(rep["sigma_hi"] - r.narrowed.upper) <= 1e-9 * w
+    nrm = np.abs(A).sum(1).max()
+    assert abs(lam_g - r.lam) <= 1e-10 * nrm
+    # the paper's bisection from the same interval takes at least as many factorizations here
+    rb = ts.multisect_mmax(ts.DenseOps(A, B), k, r.initial, 20, 1)
+    assert rep["n_bisect"] <= len(rb.history)
+    with pytest.raises(kep.KepError):
+        P.kth_eigenpair(k, split="interp", nshift=4)     # the rule takes one shift per step

@@ -90,3 +90,74 @@ def test_eig_grad_matches_finite_differences():
         gb = GB[i, j] + (GB[j, i] if i != j else 0.0)
         assert abs(fa - ga) <= 1e-6 * scale, (i, j, fa, ga)
         assert abs(fb - gb) <= 1e-6 * scale * max(1.0, abs(lam)), (i, j, fb, gb)
+
+
+class _CountOps:
+    """nu(sigma) = #{eigenvalues < sigma} of a sorted array (a count function with no matrix)."""
+
+    def __init__(self, lam):
+        self.lam = np.sort(np.asarray(lam, dtype=np.float64))
+        self.calls = 0
+
+    def nu(self, s):
+        self.calls += 1
+        return int(np.searchsorted(self.lam, s, side="left"))
+
+
+@pytest.mark.parametrize("k", [1234, 5000, 8765])
+def test_interp_linear_count_closed_form(k):
+    # eigenvalues 1..N: nu is linear between the ends, so linear interpolation lands exactly on the
+    # target counts k - 5 and k + 4 (h = m_max / 4 = 5): two steps, from either side
+    N = 10000
+    ops = _CountOps(np.arange(1, N + 1))
+    iv = ts.Interval(0.5, N + 0.5, 0, N)
+    r = ts.interp_mmax(ops, k, iv, 20)
+    assert len(r.history) == 2
+    assert (r.nu_lower, r.nu_upper) == (k - 5, k + 4)
+    assert abs(r.lower - (k - 4.5)) < 1e-9 and abs(r.upper - (k + 4.5)) < 1e-9
+
+
+def test_interp_contract_on_pencil(small):
+    p, A, B, lam, _ = small
+    k = p.k
+    for iv0 in (ts.gershgorin_interval(A, B), ts.lanczos_interval(ts.DenseOps(A, B), k,
+                                                                  np.random.default_rng(7).normal(size=p.n))):
+        r = ts.interp_mmax(ts.DenseOps(A, B), k, iv0, 20)
+        assert r.nu_lower < k <= r.nu_upper and r.nu_upper - r.nu_lower <= 20
+        assert r.lower <= lam[k - 1] < r.upper
+        assert core.count_below(lam, r.lower) == r.nu_lower and core.count_below(lam, r.upper) == r.nu_upper
+        rb = ts.bisect_mmax(ts.DenseOps(A, B), k, iv0, 20)
+        assert len(r.history) <= len(rb.history)
+
+
+@pytest.mark.parametrize("kind", ["cluster", "cauchy", "gap"])
+def test_interp_safeguard_bound(kind):
+    # spectra that defeat interpolation: a dense cluster beside a sparse part, heavy tails, and a
+    # wide gap right above k; the safeguard's midpoint steps keep the count at most about four
+    # times bisection's, and the contract holds
+    N = 200000
+    rng = np.random.default_rng(11)
+    if kind == "cluster":
+        lam = np.concatenate([np.linspace(0, 1, N // 2), 1 + 1e-7 * np.arange(N - N // 2)])
+    elif kind == "cauchy":
+        lam = rng.standard_cauchy(N)
+    else:
+        lam = np.concatenate([rng.uniform(0, 1, N // 2), rng.uniform(50, 51, N - N // 2)])
+    lam = np.sort(lam)
+    for k in (N // 10, N // 2, N // 2 + 1, 9 * N // 10):
+        iv = ts.Interval(lam[0] - 1.0, lam[-1] + 1.0, 0, N)
+        ops = _CountOps(lam)
+        r = ts.interp_mmax(ops, k, iv, 20)
+        rb = ts.bisect_mmax(_CountOps(lam), k, iv, 20)
+        assert r.nu_lower < k <= r.nu_upper and r.nu_upper - r.nu_lower <= 20
+        assert r.lower <= lam[k - 1] < r.upper
+        assert len(r.history) <= 4 * len(rb.history) + 4
+
+
+def test_three_stage_interp_matches_dense(small):
+    p, A, B, lam, _ = small
+    rng = np.random.default_rng(5)
+    r = ts.three_stage(ts.DenseOps(A, B), p.k, rng.normal(size=p.n), rng.normal(size=p.n), split="interp")
+    nrm = np.abs(A).sum(1).max()
+    assert abs(r.lam - lam[p.k - 1]) <= 1e-10 * nrm
+    assert r.narrowed.nu_upper - r.narrowed.nu_lower <= 20
