@@ -311,7 +311,8 @@ def measure_variants(P, p, torch, kth, which="all"):
         try:
             lam_v, _, rep = P.kth_eigenpair(p.k, want_vector=False, **kw)
         except Exception as exc:       # e.g. refinement that does not reach its tolerance
-            out[name] = {"error": str(exc), "seconds": time.perf_counter() - t0}
+            out[name] = {"error": str(exc), "seconds": time.perf_counter() - t0,
+                         "report": getattr(exc, "report", None)}
             continue
         t = time.perf_counter() - t0
         out[name] = {"time_to_lambda_k_s": t, "lambda_k": lam_v,

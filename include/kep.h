@@ -136,6 +136,8 @@ typedef struct {
   double t_stage[3];          /* seconds spent in stages 1, 2, 3 */
   int64_t n_refine;           /* refinement corrections in Algorithm 3 (KEP_SOLVE_F32_IR) */
   double solve_berr;          /* largest final backward error of those solves */
+  int64_t cap_cols;           /* Lanczos basis columns available to Algorithms 2 and 3 (fewer than
+                                 max_lanczos / max_si + 2 when device memory is short) */
 } kep_report;
 
 void kep_default_params(kep_params* p);
@@ -303,7 +305,8 @@ kep_status kep_spmv(kep_ctx* ctx, const double* x, double* ax, double* bx, int p
  * report   optional.
  * Returns KEP_ERR_CLUSTER when Algorithm 3 cannot validate the interval within max_si
  * iterations (multiple or clustered eigenvalues, Section 3.4), KEP_ERR_NOT_SPD if B's
- * factorization shows B is not positive definite.
+ * factorization shows B is not positive definite.  The report is written on errors too, with
+ * what the stages reached.
  */
 kep_status kep_kth_eigenpair(kep_ctx* ctx, int64_t k, const kep_params* params, double* lambda,
                              double* x, kep_report* report);

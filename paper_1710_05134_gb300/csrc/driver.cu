@@ -520,6 +520,13 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   R.opsh = R.ops;
   if (c->herm_n) R.opsh.n = c->herm_n;
   kep_report& rep = R.rep;
+  // the report is written on every return from here on, the partial one of a failed run included
+  struct ReportOut {
+    kep_report* dst;
+    const kep_report* src;
+    ~ReportOut() { if (dst) *dst = *src; }
+  } report_out{report, &rep};
+  rep.cap_cols = cap;
   std::vector<double> h_start(2 * n), tmp;
   if (prm.start_vectors) std::memcpy(h_start.data(), prm.start_vectors, sizeof(double) * 2 * n);
   else { gaussian_vector(prm.seed, n, h_start.data()); gaussian_vector(prm.seed + 1, n, h_start.data() + n); }

@@ -92,7 +92,7 @@ class Report(ctypes.Structure):
                 ("n_factor", ctypes.c_int64), ("n_lanczos", ctypes.c_int64),
                 ("n_bisect", ctypes.c_int64), ("n_si_iter", ctypes.c_int64),
                 ("si_iter_bound", ctypes.c_int64), ("t_stage", ctypes.c_double * 3),
-                ("n_refine", ctypes.c_int64), ("solve_berr", ctypes.c_double)]
+                ("n_refine", ctypes.c_int64), ("solve_berr", ctypes.c_double), ("cap_cols", ctypes.c_int64)]
 
     def asdict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_stage"}
@@ -485,9 +485,12 @@ class Problem:
         lam = ctypes.c_double()
         x = np.empty(self.n, dtype=self.vdtype) if want_vector else None
         rep = Report()
-        _check(lib().kep_kth_eigenpair(self._h, int(k), ctypes.byref(prm), ctypes.byref(lam),
-                                       x.ctypes.data if x is not None else None, ctypes.byref(rep)),
-               "kep_kth_eigenpair")
+        st = lib().kep_kth_eigenpair(self._h, int(k), ctypes.byref(prm), ctypes.byref(lam),
+                                     x.ctypes.data if x is not None else None, ctypes.byref(rep))
+        if st != KEP_OK:
+            err = KepError(st, "kep_kth_eigenpair")
+            err.report = rep.asdict()                  # what the stages reached
+            raise err
         return lam.value, x, rep.asdict()
 
 
