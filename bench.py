@@ -800,6 +800,7 @@ def main():
                 "fp64_peak_measured_tflops": fp64_peak / 1e12,
                 "factorization_fp64_equivalent_tflops": info.flops_factor * args.steps / (ms / 1e3) / 1e12,
                 "kernels_ms_warmup_step": {k: v[1] for k, v in warm_classes.items()},
+                "kernels_launches_warmup_step": {k: v[0] for k, v in warm_classes.items()},
                 "kernels_ms_timed": {k: v[1] for k, v in classes.items() if v[1] > 0}}
         if kth is not None:
             line["time_to_lambda_k"] = kth

@@ -138,6 +138,10 @@ typedef struct {
   double solve_berr;          /* largest final backward error of those solves */
   int64_t cap_cols;           /* Lanczos basis columns available to Algorithms 2 and 3 (fewer than
                                  max_lanczos / max_si + 2 when device memory is short) */
+  double last_res;            /* Algorithm 3's tests at its last iteration: largest residual of the
+                                 interval's pairs from the Lanczos relation (Eq. 2.12), */
+  double last_diff;           /* largest relative difference (Eq. 3.5; -1 when not formed), */
+  double last_res_explicit;   /* largest explicit residual of the last confirmation (0 if none) */
 } kep_report;
 
 void kep_default_params(kep_params* p);

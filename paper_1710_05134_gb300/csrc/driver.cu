@@ -744,10 +744,12 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
       if (!(lam_i[s_ord[ii]] + eta_i[s_ord[ii]] < lam_i[s_ord[ii + 1]] - eta_i[s_ord[ii + 1]])) ok = false;
     if (ok && rep.si_iter_bound == 0) rep.si_iter_bound = j;
     for (int64_t ii = 0; ii < mm; ++ii) if (!(rest[ii] < prm.tau_res)) ok = false;
+    rep.last_res = *std::max_element(rest.begin(), rest.end());
     // relative difference (Eq. 3.5) between iterations j-1 and j, through the Gram matrix
     bool diff_ok = prev_j == j - 1;
+    rep.last_diff = -1.0;
     if (diff_ok) {
-      for (int64_t ii = 0; ii < mm && diff_ok; ++ii) {
+      for (int64_t ii = 0; ii < mm; ++ii) {
         const double* cn = coef.data() + ii * (j + 1);
         const double* co = prev_c.data() + ii * j;    // length j (basis v_1..v_j)
         std::vector<double> cpad(j + 1, 0.0), dv(j + 1);
@@ -767,7 +769,9 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
         const double s = (dot >= 0 ? 1.0 : -1.0) * std::sqrt(no / std::max(nn, 1e-300));
         for (int64_t r = 0; r <= j; ++r) dv[r] = s * cn[r] - cpad[r];
         const double dn2 = gram(dv.data(), dv.data());
-        if (!(std::sqrt(std::max(dn2, 0.0)) / std::sqrt(std::max(no, 1e-300)) < prm.tau_diff)) diff_ok = false;
+        const double rd = std::sqrt(std::max(dn2, 0.0)) / std::sqrt(std::max(no, 1e-300));
+        rep.last_diff = std::max(rep.last_diff, rd);
+        if (!(rd < prm.tau_diff)) diff_ok = false;
       }
     }
     prev_c.assign(static_cast<size_t>(mm) * (j + 1), 0.0);
@@ -778,6 +782,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     if (!(ok && diff_ok)) continue;
     // confirm the residuals explicitly: ||(A - lambda B) x||_2 / ||x||_2 < tau_res for i <= m
     bool explicit_ok = true;
+    rep.last_res_explicit = 0.0;
     for (int64_t ii = 0; ii < mm && explicit_ok; ++ii) {
       CTRY(cudaMemcpyAsync(d->coef, coef.data() + ii * (j + 1), sizeof(double) * (j + 1), cudaMemcpyHostToDevice,
                            c->stream));
@@ -789,6 +794,7 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
       double rr = 0, xx = 0;
       for (int bb = 0; bb < d->nblocks; ++bb) { rr += part[2 * bb]; xx += part[2 * bb + 1]; }
       const double rel = std::sqrt(rr) / std::sqrt(std::max(xx, 1e-300));
+      rep.last_res_explicit = std::max(rep.last_res_explicit, rel);
       if (!(rel < prm.tau_res)) explicit_ok = false;
     }
     if (!explicit_ok) continue;

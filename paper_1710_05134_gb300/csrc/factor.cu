@@ -117,18 +117,7 @@ __global__ void lf_scatter_kernel(FrontTables T, SlotSet SS, Batch B) {
 
 // Extend-add of the s-th child of every front in the batch (one launch per child slot keeps
 // the additions of different children to one parent entry in a fixed order).
-constexpr int kExtThreads = 256;
-constexpr int kExtUnroll = 4;     // rows in flight per lane
-
-// Extend-add of child slot s of every front in the batch.  One warp per child column qj (lanes
-// over its rows): the column's parent position and both column base pointers are resolved once,
-// every lane then moves kExtUnroll rows at a time (child values and row maps loaded first, the
-// parent entries next, the sums stored last), so each lane has that many independent memory
-// chains in flight.  Child rows map into the parent in increasing order (Pi >= Pj), distinct
-// columns of one child land in distinct parent columns, and the children of a front are taken one
-// launch per slot, so no two threads ever add into the same entry: the sums do not depend on
-// scheduling.
-__global__ void __launch_bounds__(kExtThreads) lf_extend_kernel(FrontTables T, SlotSet SS, Batch B, int32_t s) {
+__global__ void lf_extend_kernel(FrontTables T, SlotSet SS, Batch B, int32_t s) {
   const int32_t b = B.e0 + blockIdx.y;
   const int32_t t = B.lf[b];
   const int32_t g = entry_shift(B, b);
@@ -143,41 +132,12 @@ __global__ void __launch_bounds__(kExtThreads) lf_extend_kernel(FrontTables T, S
   const int32_t ch = T.child_idx[c0 + s];
   const ChildCB cv = child_cb(T, S, cbpool, ch);
   const int32_t nc = cv.size();
-  const int32_t dout = cv.dout;
   const FrontView v = front_view(T, S, cbpool, t, d_in);
-  const int32_t* __restrict__ rmap = T.relmap + T.relmap_ptr[ch];
-  const int32_t nw = kExtThreads / 32, warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int32_t qj = blockIdx.x * nw + warp; qj < nc; qj += gridDim.x * nw) {
-    const int32_t Pj = parent_pos(T, ch, qj, dout, off, d_in);
-    // parent column Pj: rows Pi >= Pj, in the L storage (Pj < p, row Pi) or in the contribution
-    // block (row Pi - p)
-    const bool pl = Pj < v.p;
-    double* __restrict__ pc = pl ? v.L + static_cast<int64_t>(Pj) * v.ldL : v.C + static_cast<int64_t>(Pj - v.p) * v.c;
-    const int32_t prow = pl ? 0 : v.p;
-    // child column qj: a delayed column lives in the child's L storage (row nel + qi), the others
-    // in its block (row qi - dout)
-    const bool cl = qj < dout;
-    const double* __restrict__ cc = cl ? cv.L + static_cast<int64_t>(cv.nel + qj) * cv.ldL + cv.nel
-                                       : cv.C + static_cast<int64_t>(qj - dout) * cv.csym;
-    const int32_t crow = cl ? 0 : dout;
-    for (int32_t q0 = qj + lane; q0 < nc; q0 += 32 * kExtUnroll) {
-      double x[kExtUnroll], y[kExtUnroll];
-      int32_t pi[kExtUnroll];
-#pragma unroll
-      for (int u = 0; u < kExtUnroll; ++u) {
-        const int32_t qi = q0 + 32 * u;
-        pi[u] = -1;
-        x[u] = 0.0;
-        if (qi < nc) {
-          x[u] = __ldcs(cc + (qi - crow));
-          pi[u] = (qi < dout ? off + qi : d_in + __ldg(rmap + (qi - dout))) - prow;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kExtUnroll; ++u) y[u] = pi[u] >= 0 ? pc[pi[u]] : 0.0;
-#pragma unroll
-      for (int u = 0; u < kExtUnroll; ++u)
-        if (pi[u] >= 0) pc[pi[u]] = y[u] + x[u];
+  for (int32_t qj = blockIdx.x; qj < nc; qj += gridDim.x) {
+    const int32_t Pj = parent_pos(T, ch, qj, cv.dout, off, d_in);
+    for (int32_t qi = qj + threadIdx.x; qi < nc; qi += blockDim.x) {
+      const int32_t Pi = parent_pos(T, ch, qi, cv.dout, off, d_in);
+      *v.at(Pi, Pj) += cv.get(qi, qj);
     }
   }
 }
@@ -889,7 +849,7 @@ kep_status run_factor(FactorLaunch& F, const double* ca, const double* cb, kep_i
                      F.T, F.SS, B));
       for (int32_t s = 0; s < maxch; ++s)
         KEP_LAUNCH(F.timer, KC_ASSEMBLE, st,
-                   lf_extend_kernel<<<dim3(grid_cap((max_m + 7) / 8, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), kExtThreads, 0, st>>>(
+                   lf_extend_kernel<<<dim3(grid_cap(max_m, std::max<int64_t>(1, (target + nb - 1) / nb)), nb), 128, 0, st>>>(
                        F.T, F.SS, B, s));
       const int64_t rowtiles = (max_m + kRowTile - 1) / kRowTile;
       // CTAs per front: enough for the largest front of the batch (fronts of one level differ in
