@@ -93,7 +93,8 @@ class Report(ctypes.Structure):
                 ("n_bisect", ctypes.c_int64), ("n_si_iter", ctypes.c_int64),
                 ("si_iter_bound", ctypes.c_int64), ("t_stage", ctypes.c_double * 3),
                 ("n_refine", ctypes.c_int64), ("solve_berr", ctypes.c_double), ("cap_cols", ctypes.c_int64),
-                ("last_res", ctypes.c_double), ("last_diff", ctypes.c_double), ("last_res_explicit", ctypes.c_double)]
+                ("last_res", ctypes.c_double), ("last_diff", ctypes.c_double), ("last_res_explicit", ctypes.c_double),
+                ("polished", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def asdict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_stage"}
