@@ -142,10 +142,11 @@ typedef struct {
                                  interval's pairs from the Lanczos relation (Eq. 2.12), */
   double last_diff;           /* largest relative difference (Eq. 3.5; -1 when not formed), */
   double last_res_explicit;   /* largest explicit residual of the last confirmation (0 if none) */
-  int32_t polished;           /* 1 when the pairs were confirmed after one step of inverse iteration
-                                 with FP64-refined solves: the explicit residuals had stopped above
-                                 tau_res (a floor set by the solves' rounding) although the Lanczos
-                                 relation and the relative differences had converged */
+  int32_t restarted;          /* 1 when Algorithm 3 ran a second time with every shifted solve
+                                 refined in FP64: the explicit residuals had stopped above tau_res (a
+                                 floor set by the solves' rounding) although the Lanczos relation
+                                 and the relative differences had converged; n_si_iter then counts
+                                 the second run's iterations */
   int32_t reserved;
 } kep_report;
 

@@ -146,8 +146,6 @@ struct Driver {
   double* partial = nullptr;
   int nblocks = 0;
   double* cg = nullptr;     // 3 n: residual, direction, B times direction (B-solves by CG)
-  double* P = nullptr;      // polished vectors of Algorithm 3's pairs (p_cols x n)
-  int64_t p_cols = 0;
 };
 
 // splitmix64 (Steele, Lea, Flood 2014) as a counter-based generator; Box-Muller for N(0, 1).
@@ -185,7 +183,7 @@ void kep_ctx::driver_release() {
   Driver* d = static_cast<Driver*>(driver);
   if (!d) return;
   cudaFree(d->V); cudaFree(d->BV); cudaFree(d->w); cudaFree(d->u); cudaFree(d->u2);
-  cudaFree(d->coef); cudaFree(d->partial); cudaFree(d->cg); cudaFree(d->P);
+  cudaFree(d->coef); cudaFree(d->partial); cudaFree(d->cg);
   delete d;
   driver = nullptr;
 }
@@ -658,8 +656,9 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     DTRY(fs);
   }
   // w = (A - sigma B)^{-1} rhs with the factor in slot 0 (refined when it is a reduced one)
+  bool refine_all = f32ir;          // every solve refined (a reduced factor, or a restart)
   auto shifted_solve = [&](const double* rhs, double* out) -> kep_status {
-    if (!f32ir) return ctx_solve_dev(c, 0, rhs, out);
+    if (!refine_all) return ctx_solve_dev(c, 0, rhs, out);
     int32_t it = 0;
     double be = 0.0;
     const kep_status st = ctx_solve_refined_dev(c, rhs, out, 1e-13, 100, &it, &be);
@@ -681,9 +680,6 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
   bool converged = false;
   std::vector<double> res_lam, res_eta, best_coef;
   int64_t best_j = 0;
-  bool polish_tried = false, polished = false;
-  int64_t best_pick = 0;
-  std::vector<double> polish_lam;
   for (int64_t j = 1; j <= prm.max_si && j + 1 < cap; ++j) {
     double* vj = R.col(d->V, j - 1);
     double* bvj = R.col(d->BV, j - 1);
@@ -802,62 +798,29 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
       rep.last_res_explicit = std::max(rep.last_res_explicit, rel);
       if (!(rel < prm.tau_res)) explicit_ok = false;
     }
-    if (!explicit_ok && !polish_tried) {
+    if (!explicit_ok && !refine_all) {
       // The Lanczos relation and the relative differences say the interval's pairs have converged,
       // but their explicit residuals stay above tau_res: the rounding of the shifted solves sets a
-      // floor (the factor's backward error times ||A||).  Once per run, each pair gets one step of
-      // inverse iteration with solves refined in FP64 (GMRES, the factor as preconditioner):
-      // y_i = (A - sigma B)^{-1} B x_i shrinks every component along an eigenvector of eigenvalue
-      // lambda by |lambda_i - sigma| / |lambda - sigma|, which removes the solve errors, and the
-      // pairs are confirmed again with the Rayleigh quotient of y_i as their eigenvalue (inside
-      // the interval), which carries no solve error either.
-      polish_tried = true;
-      if (d->p_cols < mm) {
-        cudaFree(d->P);
-        d->P = nullptr;
-        d->p_cols = 0;
-        if (cudaMalloc(&d->P, sizeof(double) * n * mm) != cudaSuccess) { cudaGetLastError(); continue; }
-        d->p_cols = mm;
-      }
-      explicit_ok = true;
-      rep.last_res_explicit = 0.0;
-      polish_lam.assign(mm, 0.0);
-      for (int64_t ii = 0; ii < mm && explicit_ok; ++ii) {
-        double* y = d->P + static_cast<size_t>(ii) * n;
-        CTRY(cudaMemcpyAsync(d->coef, coef.data() + ii * (j + 1), sizeof(double) * (j + 1), cudaMemcpyHostToDevice,
-                             c->stream));
-        R.ops.combine(d->V, n, static_cast<int32_t>(j + 1), d->coef, 1.0, 0.0, d->w);
-        DTRY(ctx_spmv_dev(c, d->w, nullptr, d->u2));  // B x_i
-        int32_t it = 0;
-        double be = 0.0;
-        const kep_status ps = ctx_solve_refined_dev(c, d->u2, y, 1e-14, 10, &it, &be);
-        if (ps != KEP_OK && ps != KEP_ERR_NOT_CONVERGED) return ps;
-        rep.n_refine += it;
-        DTRY(ctx_spmv_dev(c, y, d->u, d->u2));
-        double yay = 0, yby = 0;
-        DTRY(R.dots(y, 1, d->u, &yay));
-        DTRY(R.dots(y, 1, d->u2, &yby));
-        const double rq = yay / yby;
-        if (!(rq >= lo && rq < hi)) { explicit_ok = false; break; }
-        R.ops.resid_partials(d->u, d->u2, rq, d->w);
-        std::vector<double> part(2 * d->nblocks);
-        DTRY(R.to_host(part.data(), d->partial, 2 * d->nblocks));
-        double rr = 0, xx = 0;
-        for (int bb = 0; bb < d->nblocks; ++bb) { rr += part[2 * bb]; xx += part[2 * bb + 1]; }
-        const double rel = std::sqrt(rr) / std::sqrt(std::max(xx, 1e-300));
-        rep.last_res_explicit = std::max(rep.last_res_explicit, rel);
-        if (!(rel < prm.tau_res)) explicit_ok = false;
-        polish_lam[ii] = rq;
-      }
-      polished = explicit_ok;
-      rep.polished = polished ? 1 : 0;
-      if (polished) lam_i = polish_lam;
+      // floor (the factor's backward error times ||A||), so the Ritz vectors are those of a pencil
+      // perturbed by that much.  Algorithm 3 is run again, once, from the same start vector with
+      // every shifted solve refined in FP64 (GMRES with the factor as preconditioner) to a backward
+      // error of 1e-13.
+      refine_all = true;
+      rep.restarted = 1;
+      alpha.clear(); beta.clear();
+      const double g0 = G[0];
+      std::fill(G.begin(), G.end(), 0.0);
+      G[0] = g0;
+      prev_c.clear();
+      prev_j = -1;
+      rep.si_iter_bound = 0;
+      j = 0;
+      continue;
     }
     if (!explicit_ok) continue;
     converged = true;
     // sort the interval's pairs increasingly and take the l-th (Algorithm 3, last two lines)
     const int64_t pick = s_ord[l - 1];
-    best_pick = pick;
     best_coef.assign(coef.begin() + pick * (j + 1), coef.begin() + (pick + 1) * (j + 1));
     best_j = j;
     res_lam = lam_i; res_eta = eta_i;
@@ -866,14 +829,9 @@ extern "C" kep_status kep_kth_eigenpair(kep_ctx* c, int64_t k, const kep_params*
     break;
   }
   if (!converged) return KEP_ERR_CLUSTER;
-  // x_k = V c (or its polished vector), B-normalized; explicit residuals for the report
-  if (polished) {
-    CTRY(cudaMemcpyAsync(d->w, d->P + static_cast<size_t>(best_pick) * n, sizeof(double) * n,
-                         cudaMemcpyDeviceToDevice, c->stream));
-  } else {
-    CTRY(cudaMemcpyAsync(d->coef, best_coef.data(), sizeof(double) * (best_j + 1), cudaMemcpyHostToDevice, c->stream));
-    R.ops.combine(d->V, n, static_cast<int32_t>(best_j + 1), d->coef, 1.0, 0.0, d->w);
-  }
+  // x_k = V c, B-normalized; explicit residuals for the report
+  CTRY(cudaMemcpyAsync(d->coef, best_coef.data(), sizeof(double) * (best_j + 1), cudaMemcpyHostToDevice, c->stream));
+  R.ops.combine(d->V, n, static_cast<int32_t>(best_j + 1), d->coef, 1.0, 0.0, d->w);
   DTRY(ctx_spmv_dev(c, d->w, d->u, d->u2));
   double xbx = 0;
   DTRY(R.dots(d->w, 1, d->u2, &xbx));

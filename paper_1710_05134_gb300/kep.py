@@ -94,7 +94,7 @@ class Report(ctypes.Structure):
                 ("si_iter_bound", ctypes.c_int64), ("t_stage", ctypes.c_double * 3),
                 ("n_refine", ctypes.c_int64), ("solve_berr", ctypes.c_double), ("cap_cols", ctypes.c_int64),
                 ("last_res", ctypes.c_double), ("last_diff", ctypes.c_double), ("last_res_explicit", ctypes.c_double),
-                ("polished", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("restarted", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def asdict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "t_stage"}

@@ -136,21 +136,21 @@ def test_kth_eigenpair_interp_split_matches_oracle(kep, small, frac):
         P.kth_eigenpair(k, split="interp", nshift=4)     # the rule takes one shift per step
 
 
-def test_kth_eigenpair_polish_after_inexact_solves(kep, small):
+def test_kth_eigenpair_restart_after_inexact_solves(kep, small):
     """Algorithm 3 on solves that carry rounding well above FP64's (every factor of the run taken in
     reduced precision, solves unrefined): the Lanczos relation and the relative differences
-    converge on the perturbed operator while the explicit residuals stop near 1e-6 ||A||.  The
-    driver then polishes the interval's pairs once (one step of inverse iteration with refined
-    solves, Rayleigh quotients) and returns lambda_k and x_k to the method's tolerances."""
+    converge on the perturbed operator while the explicit residuals stop far above tau_res.  The
+    driver then runs Algorithm 3 once more with every shifted solve refined in FP64 and returns
+    lambda_k and x_k to the method's tolerances."""
     p, A, B, lam, X = small
     k = p.k
     P = kep.Problem.from_pencil(p)
     P.set_schur_mode(True, fp32=True)
     lam_g, x_g, rep = P.kth_eigenpair(k, seed=3)
-    assert rep["polished"] == 1
+    assert rep["restarted"] == 1
     _check_pair(p, A, B, lam, X, k, lam_g, x_g, rep)
     # the FP64-accurate run does not need it
     P.set_schur_mode(True)
     lam_f, _, rep_f = P.kth_eigenpair(k, seed=3)
-    assert rep_f["polished"] == 0
+    assert rep_f["restarted"] == 0
     assert abs(lam_g - lam_f) <= 1e-10 * np.abs(A).sum(1).max()
