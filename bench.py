@@ -7,7 +7,9 @@ extend-add, Bunch-Kaufman pivoting, Schur updates, inertia reduction), one solve
 and one A/B sparse product.  Every step uses a new shift.  After the timed steps the counts are
 validated (non-decreasing in sigma, and equal to those of a second, independently ordered
 analysis at two of the timed shifts: Sylvester's law makes the count independent of the
-ordering and of every pivot choice), and Algorithm 4 runs once for the time to lambda_k.
+ordering and of every pivot choice), and Algorithm 4 runs once for the time to lambda_k with the
+paper's bisection in Algorithm 1', then once more with the interpolating shift rule (the
+root-finder variant the paper proposes; same start vectors, lambda_k compared).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead (bounded sample).
 """
@@ -565,6 +567,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end leg (at most --steps)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kth", action="store_true", help="skip Algorithm 4 (time to lambda_k)")
+    ap.add_argument("--no-kth-interp", action="store_true",
+                    help="skip the second Algorithm 4 run with the interpolating shift rule")
     ap.add_argument("--no-validate", action="store_true", help="skip the second-ordering count check")
     ap.add_argument("--variants", nargs="?", const="all", default=None,
                     help="also measure the next rows (all, or a comma list of: " + ", ".join(VARIANTS + SEPARATE_VARIANTS) + ")")
@@ -729,7 +733,22 @@ def main():
             P._last_x = xk
             kth = {"time_to_lambda_k_s": t_kth, "k": p.k, "lambda_k": lam, "report": rep}
         except Exception as exc:
-            kth = {"error": str(exc), "seconds": time.perf_counter() - t0}
+            kth = {"error": str(exc), "seconds": time.perf_counter() - t0,
+                   "report": getattr(exc, "report", None)}
+        # the same run with Algorithm 1''s interpolating shift rule (the root-finder variant the
+        # paper proposes): same start vectors, so stage 1 is the same; lambda_k must agree
+        if not args.no_kth_interp:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                lam_i, _, rep_i = P.kth_eigenpair(p.k, split="interp", want_vector=False)
+                kth_i = {"time_to_lambda_k_s": time.perf_counter() - t0, "lambda_k": lam_i, "report": rep_i}
+                if "lambda_k" in kth:
+                    kth_i["lambda_diff_rel"] = abs(lam_i - kth["lambda_k"]) / float(np.abs(p.A()).sum(1).max())
+            except Exception as exc:
+                kth_i = {"error": str(exc), "seconds": time.perf_counter() - t0,
+                         "report": getattr(exc, "report", None)}
+            kth["split_interp"] = kth_i
 
     variants = None
     if args.variants and rank == 0:

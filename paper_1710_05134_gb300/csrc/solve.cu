@@ -247,19 +247,6 @@ KEP_D bool df_wait(const int32_t* flag, int32_t want, int32_t* err) {
   }
 }
 
-constexpr int kDfGroup = 4;      // pivot blocks one dependency step may take
-
-// Thread 0: wait for flag j0 (flags j0, j0 + step, ... of consecutive blocks, step = +1 or -1 in
-// flag index), then count how many of the following ones are already published, up to kDfGroup
-// and below jend (exclusive, in the step's direction).  0 when the wait gave up.
-KEP_D int32_t df_wait_group(const int32_t* flags, int32_t j0, int32_t jend, int32_t step, int32_t want,
-                            int32_t* err) {
-  if (!df_wait(flags + j0, want, err)) return 0;
-  int32_t got = 1;
-  while (got < kDfGroup && j0 + got * step != jend && ld_acquire(flags + j0 + got * step) == want) ++got;
-  return got;
-}
-
 struct DfArgs {
   const int32_t* fronts;   // the level's dataflow fronts
   const int2* items;       // (front position, round) in the order items are taken
@@ -290,11 +277,10 @@ KEP_D void df_rows(const int8_t* piv, int32_t r, int32_t npb, int32_t nel, int32
 __global__ void __launch_bounds__(kDfThreads) sv_df_fwd_kernel(FrontTables T, FactorSlot S, DfArgs A,
                                                                double* vfac) {
   __shared__ double ys[kSolveBlk + 1];
-  __shared__ double ysg[2][kDfGroup * (kSolveBlk + 1)];   // solved values of a group of blocks
   __shared__ double red[4][kSolveBlk + 1];
   __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
   __shared__ int8_t pb[kSolveBlk + 1];
-  __shared__ int32_t s_item, s_cnt;
+  __shared__ int32_t s_item, s_ok;
   const int32_t tid = threadIdx.x, g = tid / kSolveBlk, rr = tid % kSolveBlk;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(A.counter, 1);
@@ -322,27 +308,23 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_fwd_kernel(FrontTables T, Fa
     const bool v0 = rr < nr, v1 = rr == 0 && nr > kSolveBlk;
     double acc0 = 0.0, acc1 = 0.0;
     bool ok = true;
-    int buf = 0;
-    // the earlier blocks in groups: wait for the next one, then take the following ones that are
-    // already published (at most kDfGroup), so that one pair of barriers serves several blocks
-    for (int32_t j = 0; j < ndep;) {
-      if (tid == 0) s_cnt = df_wait_group(fl, j, ndep, 1, A.epoch, A.err);
+    for (int32_t j = 0; j < ndep && ok; ++j) {
+      const int32_t c0 = blk_start(piv, j, nel), c1 = blk_start(piv, j + 1, nel);
+      if (tid == 0) s_ok = df_wait(fl + j, A.epoch, A.err) ? 1 : 0;
       __syncthreads();
-      const int32_t cnt = s_cnt;
-      if (cnt == 0) { ok = false; break; }
-      const int32_t c0 = blk_start(piv, j, nel), c1 = blk_start(piv, j + cnt, nel);
-      double* yb = ysg[buf];
-      for (int32_t q = tid; q < c1 - c0; q += kDfThreads) yb[q] = __ldcg(vf + c0 + q);
+      ok = s_ok != 0;
+      if (ok && tid < c1 - c0) ys[tid] = __ldcg(vf + c0 + tid);
       __syncthreads();
+      if (ok) {
 #pragma unroll 4
-      for (int32_t c = c0 + g; c < c1; c += 4) {
-        const double yc = yb[c - c0];
-        const double* col = L + static_cast<int64_t>(c) * ld + r0;
-        if (v0) acc0 = fma(__ldg(col + rr), yc, acc0);
-        if (v1) acc1 = fma(__ldg(col + kSolveBlk), yc, acc1);
+        for (int32_t c = c0 + g; c < c1; c += 4) {
+          const double yc = ys[c - c0];
+          const double* col = L + static_cast<int64_t>(c) * ld + r0;
+          if (v0) acc0 = fma(__ldg(col + rr), yc, acc0);
+          if (v1) acc1 = fma(__ldg(col + kSolveBlk), yc, acc1);
+        }
       }
-      buf ^= 1;
-      j += cnt;
+      __syncthreads();
     }
     if (!ok) return;
     red[g][rr] = acc0;
@@ -408,11 +390,10 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
                                                                double* vfac, double* xnew) {
   constexpr int kCols = (kSolveBlk + 1 + 7) / 8;
   __shared__ double xs[kSolveBlk + 1];
-  __shared__ double xsg[2][kDfGroup * (kSolveBlk + 1)];   // solution of a group of later blocks
   __shared__ double part[kSolveBlk + 1];
   __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
   __shared__ int8_t pb[kSolveBlk + 1];
-  __shared__ int32_t s_item, s_ok, s_cnt;
+  __shared__ int32_t s_item, s_ok;
   const int32_t tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(A.counter, 1);
@@ -464,30 +445,26 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
       }
       continue;
     }
-    // later pivot blocks, last first, in groups: wait for the next one, then take the following
-    // ones that are already published (at most kDfGroup)
+    // later pivot blocks, last first
     bool ok = true;
-    int buf = 0;
-    const int32_t fend = npb - 1 - b;                 // flag f belongs to block npb - 1 - f
-    for (int32_t f = 0; f < fend;) {
-      if (tid == 0) s_cnt = df_wait_group(fl, f, fend, 1, A.epoch, A.err);
+    for (int32_t bp = npb - 1; bp > b && ok; --bp) {
+      const int32_t s0 = blk_start(piv, bp, nel), s1 = blk_start(piv, bp + 1, nel);
+      if (tid == 0) s_ok = df_wait(fl + (npb - 1 - bp), A.epoch, A.err) ? 1 : 0;
       __syncthreads();
-      const int32_t cnt = s_cnt;
-      if (cnt == 0) { ok = false; break; }
-      const int32_t s0 = blk_start(piv, npb - f - cnt, nel), s1 = blk_start(piv, npb - f, nel);
-      double* xb = xsg[buf];
-      for (int32_t q = tid; q < s1 - s0; q += kDfThreads) xb[q] = __ldcg(vf + s0 + q);
+      ok = s_ok != 0;
+      if (ok && tid < s1 - s0) xs[tid] = __ldcg(vf + s0 + tid);
       __syncthreads();
-      for (int32_t a = s0 + lane; a < s1; a += 32) {
-        const double xa = xb[a - s0];
+      if (ok) {
+        for (int32_t a = s0 + lane; a < s1; a += 32) {
+          const double xa = xs[a - s0];
 #pragma unroll
-        for (int j = 0; j < kCols; ++j) {
-          const int32_t c = warp + 8 * j;
-          if (c < kb) acc[j] = fma(__ldg(L + static_cast<int64_t>(k0 + c) * ld + a), xa, acc[j]);
+          for (int j = 0; j < kCols; ++j) {
+            const int32_t c = warp + 8 * j;
+            if (c < kb) acc[j] = fma(__ldg(L + static_cast<int64_t>(k0 + c) * ld + a), xa, acc[j]);
+          }
         }
       }
-      buf ^= 1;
-      f += cnt;
+      __syncthreads();
     }
     if (!ok) return;
 #pragma unroll
