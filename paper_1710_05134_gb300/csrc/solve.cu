@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
   constexpr int kCols = (kSolveBlk + 1 + 7) / 8;
   __shared__ double xs[kSolveBlk + 1];
   __shared__ double part[kSolveBlk + 1];
-  __shared__ double Lb[kSolveBlk + 1][kSolveBlk + 2];   // diagonal block, [column][row]
+  __shared__ double LbT[kSolveBlk + 1][kSolveBlk + 2];  // diagonal block, [row][column]
   __shared__ int8_t pb[kSolveBlk + 1];
   __shared__ int32_t s_item, s_ok;
   const int32_t tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
     }
     for (int32_t e = tid; e < kb * kb; e += blockDim.x) {
       const int32_t c = e / kb, a = e % kb;
-      if (a > c) Lb[c][a] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
+      if (a > c) LbT[a][c] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
     }
     if (tid < kb) pb[tid] = piv[k0 + tid];
     __syncthreads();
@@ -518,30 +518,17 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
         const double a = S.Dd[po + c - 1], cc = S.Dd[po + c], bb = S.De[po + c - 1];
         z = (a * yc - bb * vf[c - 1]) / (a * cc - bb * bb);
       }
-      xs[tid] = z;
+      xs[tid] = z - part[tid];
     }
     __syncthreads();
+    // L11^T x = z - part, last row first in column (axpy) form: once x(c) is final, row c of L11
+    // is subtracted from the rows above it (lanes over those rows, no reductions on the chain).
+    // The entry (c, c-1) inside a 2x2 pair is not part of the unit triangle and is skipped.
     if (tid < 32) {
-      for (int32_t c = kb - 1; c >= 0;) {
-        if (pb[c] == 0) {                     // second of a pair at (c-1, c)
-          double s0 = 0.0, s1 = 0.0;
-          for (int32_t a = c + 1 + lane; a < kb; a += 32) {
-            s0 += Lb[c - 1][a] * xs[a];
-            s1 += Lb[c][a] * xs[a];
-          }
-          s0 = warp_sum(s0); s1 = warp_sum(s1);
-          if (lane == 0) {
-            xs[c] -= part[c] + s1;
-            xs[c - 1] -= part[c - 1] + s0;
-          }
-          c -= 2;
-        } else {
-          double s0 = 0.0;
-          for (int32_t a = c + 1 + lane; a < kb; a += 32) s0 += Lb[c][a] * xs[a];
-          s0 = warp_sum(s0);
-          if (lane == 0) xs[c] -= part[c] + s0;
-          c -= 1;
-        }
+      for (int32_t c = kb - 1; c > 0; --c) {
+        const double xc = xs[c];
+        const int32_t lim = pb[c] == 0 ? c - 1 : c;    // pb 0: second of a pair at (c-1, c)
+        for (int32_t a = lane; a < lim; a += 32) xs[a] -= LbT[c][a] * xc;
         __syncwarp();
       }
     }
