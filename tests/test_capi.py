@@ -84,6 +84,10 @@ def test_symbolic_info_closed_form_without_gpu():
     assert inf.n == m and inf.nnz == m * m and inf.nfronts == 1 and inf.max_front == m
     assert inf.nnz_factor == m * (m + 1) // 2
     assert inf.flops_factor == float((r * r + r).sum())
+    # one root front: its m x m storage, no contribution block (the arena keeps its minimum of 32
+    # doubles), and a slot that holds at least both
+    assert inf.front_bytes == 8 * m * m and inf.cb_bytes == 8 * 32
+    assert inf.slot_bytes >= inf.front_bytes + inf.cb_bytes
     # the lower triangle alone describes the same pattern
     keep = ci <= np.repeat(np.arange(m), m)
     rpl = np.concatenate([[0], np.cumsum(np.arange(1, m + 1))]).astype(np.int64)
