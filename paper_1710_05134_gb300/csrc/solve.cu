@@ -306,6 +306,13 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_fwd_kernel(FrontTables T, Fa
     const int32_t ndep = pivot ? I.y : npb;
     const int32_t i0 = r0 + rr;
     const bool v0 = rr < nr, v1 = rr == 0 && nr > kSolveBlk;
+    // a pivot item's diagonal block does not depend on the solve: it is staged before the waits,
+    // off the chain of diagonal solves (the first barrier of the loop below orders it)
+    if (pivot)
+      for (int32_t e = tid; e < nr * nr; e += blockDim.x) {
+        const int32_t c = e / nr, a = e % nr;
+        if (a > c) Lb[c][a] = L[static_cast<int64_t>(r0 + c) * ld + r0 + a];
+      }
     double acc0 = 0.0, acc1 = 0.0;
     bool ok = true;
     for (int32_t j = 0; j < ndep && ok; ++j) {
@@ -334,10 +341,6 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_fwd_kernel(FrontTables T, Fa
       if (tid < nr) vf[r0 + tid] -= red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
       __syncthreads();
       continue;
-    }
-    for (int32_t e = tid; e < nr * nr; e += blockDim.x) {
-      const int32_t c = e / nr, a = e % nr;
-      if (a > c) Lb[c][a] = L[static_cast<int64_t>(r0 + c) * ld + r0 + a];
     }
     if (tid < nr) {
       ys[tid] = vf[r0 + tid] - (red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid]);
@@ -445,6 +448,12 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
       }
       continue;
     }
+    // the diagonal block (transposed) is staged before the waits, off the chain of diagonal
+    // solves (the first barrier of the loop below, or the one after the partial sums, orders it)
+    for (int32_t e = tid; e < kb * kb; e += blockDim.x) {
+      const int32_t c = e / kb, a = e % kb;
+      if (a > c) LbT[a][c] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
+    }
     // later pivot blocks, last first
     bool ok = true;
     for (int32_t bp = npb - 1; bp > b && ok; --bp) {
@@ -496,10 +505,6 @@ __global__ void __launch_bounds__(kDfThreads) sv_df_bwd_kernel(FrontTables T, Fa
         for (int32_t ch = 0; ch < nch; ++ch) sacc += __ldcg(pbase + static_cast<int64_t>(ch) * (kSolveBlk + 1) + tid);
         part[tid] += sacc;
       }
-    }
-    for (int32_t e = tid; e < kb * kb; e += blockDim.x) {
-      const int32_t c = e / kb, a = e % kb;
-      if (a > c) LbT[a][c] = L[static_cast<int64_t>(k0 + c) * ld + k0 + a];
     }
     if (tid < kb) pb[tid] = piv[k0 + tid];
     __syncthreads();
