@@ -258,7 +258,7 @@ def _cpu_sample_pencil():
 
 
 VARIANTS = ("grad", "fp32_factor_ir", "two_shifts_in_flight", "autotune_schur", "gershgorin_multisection8",
-            "stage3_f32_ir", "kth_interp", "hermitian_mid")
+            "stage3_f32_ir", "hermitian_mid")
 # variants on a workload of their own (run after the main problem is released)
 SEPARATE_VARIANTS = ("multisection_batch", "graph_replay", "hermitian_full", "precision_full")
 # run only when named (minutes each): the n = 524,288 complex workload and the n = 1,500,000
@@ -305,8 +305,7 @@ def measure_variants(P, p, torch, kth, which="all"):
         P.set_schur_tile(64)
     # Algorithm 4 variants
     for name, kw in (("gershgorin_multisection8", {"init": "gershgorin", "nshift": 8}),
-                     ("stage3_f32_ir", {"solve_precision": "f32_ir"}),
-                     ("kth_interp", {"split": "interp"})):
+                     ("stage3_f32_ir", {"solve_precision": "f32_ir"})):
         if name not in want:
             continue
         sync(); t0 = time.perf_counter()
