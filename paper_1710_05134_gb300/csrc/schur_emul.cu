@@ -121,14 +121,16 @@ KEP_D int bexp(double x) {                    // biased exponent field (0 for ze
   return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
-// W(i, c) = sum_c' L(i, c') D(c', c) for the window's pivot c (2x2 blocks mix two columns)
-KEP_D double wval(const double* L, int64_t ld, int64_t i, int32_t c, const double* Dd, const double* De,
-                  const int8_t* pv) {
-  const double x = L[static_cast<int64_t>(c) * ld + i];
-  const int8_t pt = pv[c];
-  if (pt == 1) return x * Dd[c];
-  if (pt == 2) return x * Dd[c] + L[static_cast<int64_t>(c + 1) * ld + i] * De[c];
-  return L[static_cast<int64_t>(c - 1) * ld + i] * De[c - 1] + x * Dd[c];
+// W(i, c) = sum_c' L(i, c') D(c', c) for the window's pivot c (2x2 blocks mix two columns), from
+// the window's pivot types and D entries cached in shared memory (column cl of the window, global
+// column cg)
+KEP_D double wval_s(const double* L, int64_t ld, int64_t i, int32_t cg, int32_t cl, const double* wself,
+                    const double* woth, const int8_t* wpt) {
+  const double x = L[static_cast<int64_t>(cg) * ld + i];
+  const int8_t pt = wpt[cl];
+  if (pt == 1) return x * wself[cl];
+  if (pt == 2) return x * wself[cl] + L[static_cast<int64_t>(cg + 1) * ld + i] * woth[cl];
+  return L[static_cast<int64_t>(cg - 1) * ld + i] * woth[cl] + x * wself[cl];
 }
 
 // Balancing shift of pivot column c: floor(-e/2) for the exponent e of its pivot's magnitude (the
@@ -157,8 +159,13 @@ KEP_D unsigned long long fixed64(double x, int u, int e) {
   return M >> (-sh);
 }
 
-// bf16 bit pattern of the integer d, |d| <= 128 (exact: at most 8 significant bits)
-KEP_D uint32_t digit_bits(int d) { return __float_as_uint(__int2float_rn(d)) >> 16; }
+// bf16 bit pattern of the integer d, |d| <= 128 (exact: at most 8 significant bits).  The float
+// value comes from the magic-number construction (1.5 * 2^23 + d has unit spacing there, so the
+// integer added to its bit pattern is exact, and subtracting 1.5 * 2^23 leaves d), two ALU/FMA-pipe
+// operations instead of a conversion on the quarter-rate pipe.
+KEP_D uint32_t digit_bits(int d) {
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
+}
 
 // The leading S of the eight balanced digits of one value, times its sign, as bf16 bit patterns
 // (S < 8 drops the rest: a truncation below 2^{-8S} of the row scale).
@@ -206,6 +213,8 @@ template <bool kWin, int ND>
 __global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, SlotSet SS, LargeWork W, EmulBatch BA) {
   __shared__ int smx[2][kSThreads];
   __shared__ int su[kWindow];
+  __shared__ double wself[kWindow], woth[kWindow];   // W = L D coefficients of the window's columns
+  __shared__ int8_t wpt[kWindow];
   const int32_t b = BA.e0 + blockIdx.y;
   const int32_t t = BA.lf[b];
   const FactorSlot& S = SS.s[emul_shift(BA, b)];
@@ -219,7 +228,13 @@ __global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, Slot
   const double* Dd = S.Dd + po;
   const double* De = S.De + po;
   const int8_t* pv = S.piv + po;
-  for (int32_t c = threadIdx.x; c < r; c += blockDim.x) su[c] = balance_shift(Dd, De, pv, c0 + c);
+  for (int32_t c = threadIdx.x; c < r; c += blockDim.x) {
+    su[c] = balance_shift(Dd, De, pv, c0 + c);
+    const int8_t pt = pv[c0 + c];
+    wpt[c] = pt;
+    wself[c] = Dd[c0 + c];
+    woth[c] = pt == 1 ? 0.0 : (pt == 2 ? De[c0 + c] : De[c0 + c - 1]);
+  }
   __syncthreads();
   const int32_t nq = (r + 15) / 16 * 2;          // 8-column blocks covering the padded window
   const int NG = nq >= 8 ? 8 : (nq >= 4 ? 4 : 2);
@@ -237,7 +252,7 @@ __global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, Slot
         for (int32_t c = q * 8; c < min(q * 8 + 8, r); ++c) {
           const int u = su[c];
           const int bx = bexp(L[static_cast<int64_t>(c0 + c) * ld + s + row]);
-          const int by = row < wrows ? bexp(wval(L, ld, s + row, c0 + c, Dd, De, pv)) : 0;
+          const int by = row < wrows ? bexp(wval_s(L, ld, s + row, c0 + c, c, wself, woth, wpt)) : 0;
           if (bx) ex = max(ex, bx - u);
           if (by) ey = max(ey, by + u);
         }
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(kSThreads) lf_slice_kernel(FrontTables T, Slot
           if (c < r) {
             u = su[c];
             x = which == 0 ? L[static_cast<int64_t>(c0 + c) * ld + s + row]
-                           : wval(L, ld, s + row, c0 + c, Dd, De, pv);
+                           : wval_s(L, ld, s + row, c0 + c, c, wself, woth, wpt);
           }
           uint32_t d[ND];
           balanced_digits<ND>(x, which == 0 ? u : -u, which == 0 ? el : ew, d);
