@@ -215,3 +215,8 @@ def test_interp_rule_through_the_abi_matches_oracle():
     with pytest.raises(k.KepError):
         kb.interp_update(st, 5, 0.5, 11)                     # count above nu_hi
     assert (st.lo, st.hi, st.nu_lo, st.nu_hi) == (0.0, 1.0, 0, 10)   # unchanged by refused updates
+    # a bracket of two adjacent doubles cannot be split: more than m_max eigenvalues within rounding
+    tight = kb.interp_init(5, 1.0, float(np.nextafter(1.0, 2.0)), 0, 100)
+    with pytest.raises(k.KepError) as ei:
+        kb.interp_point(tight, 5, 20)
+    assert ei.value.code == k.KEP_ERR_CLUSTER
